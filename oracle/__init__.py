@@ -1,0 +1,23 @@
+"""FP64 CPU oracle for efficient Bayesian multi-view deconvolution.
+
+TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's
+CPU-baseline leg may import this package; the product path never does. It
+shares no code with the CUDA path.
+"""
+from .oracle import (  # noqa: F401
+    PLAIN,
+    EFFICIENT,
+    OPT1,
+    OPT2,
+    VARIANTS,
+    build,
+    conv,
+    mirror,
+    kconv,
+    compound,
+    update,
+    update_at,
+    deconvolve,
+    mean_views,
+    num_threads,
+)

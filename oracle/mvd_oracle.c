@@ -1,0 +1,292 @@
+/*
+ * FP64 reference ("oracle") for efficient Bayesian multi-view deconvolution.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library. The CUDA product path never calls
+ * it and shares no code with it.
+ *
+ * Everything here is written from the paper's equations, in plain loops and
+ * FP64, in the order the paper states them:
+ *   - single-view Richardson-Lucy update (Eq. 15) and its mirrored kernel
+ *     (Suppl. Note "Integrating xi and x": integration over x is a
+ *     convolution with P(-x));
+ *   - convolution-algebra form of the multi-view update (Eq. 51);
+ *   - compound kernel of the efficient method (Eq. 220, Eq. 222);
+ *     optimization I (Eq. 230) and optimization II (Eq. 240);
+ *   - sequential, view-by-view (OSEM-style) application of each view's
+ *     update (Suppl. Note "Alternative iteration for faster convergence");
+ *   - flat initial estimate equal to the mean observed intensity (Eq. 15 text).
+ *
+ * Readings where the paper is silent (same on the CUDA side):
+ *   - image convolutions are periodic (circular) on the given grid, i.e. what
+ *     the Convolution Theorem computes;
+ *   - kernel algebra (P_v^* * P_w * P_w^*) is linear convolution of the small
+ *     kernels; the compound kernel lives on P_v's own box and is normalised
+ *     to sum 1;
+ *   - one floor eps: b <- max(b, eps) before the division and
+ *     psi <- max(psi * c, eps) after the multiplication; default
+ *     eps = 1e-4 * psi0;
+ *   - psi0 is the mean over all voxels of all views.
+ *
+ * Layout: volumes are [z][y][x] (x fastest), dims = {X, Y, Z}. Kernels are
+ * [Kz][Ky][Kx] with odd sizes; offset d = (i - (Kx-1)/2, ...) for index i.
+ * Convolution: (f * k)(x) = sum_d k(d) f((x - d) mod dims).
+ */
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include <stdlib.h>
+#include <string.h>
+
+#define MVDO_PLAIN 0
+#define MVDO_EFFICIENT 1
+#define MVDO_OPT1 2
+#define MVDO_OPT2 3
+
+static inline long idx3(int x, int y, int z, int X, int Y) { return (long)x + (long)X * ((long)y + (long)Y * z); }
+
+int mvdo_num_threads(void) {
+#ifdef _OPENMP
+    int n = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        n = omp_get_num_threads();
+    }
+    return n;
+#else
+    return 1;
+#endif
+}
+
+/* Periodic 3D convolution: out(x) = sum_d k(d) in((x - d) mod dims). */
+void mvdo_conv(const double* in, const int dims[3], const double* k, const int kd[3], double* out) {
+    const int X = dims[0], Y = dims[1], Z = dims[2];
+    const int Kx = kd[0], Ky = kd[1], Kz = kd[2];
+    const int hx = (Kx - 1) / 2, hy = (Ky - 1) / 2, hz = (Kz - 1) / 2;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < Z; ++z) {
+        for (int y = 0; y < Y; ++y) {
+            double* o = out + idx3(0, y, z, X, Y);
+            for (int x = 0; x < X; ++x) o[x] = 0.0;
+            for (int kz = 0; kz < Kz; ++kz) {
+                int sz = ((z - (kz - hz)) % Z + Z) % Z;
+                for (int ky = 0; ky < Ky; ++ky) {
+                    int sy = ((y - (ky - hy)) % Y + Y) % Y;
+                    const double* src = in + idx3(0, sy, sz, X, Y);
+                    const double* krow = k + (long)Kx * (ky + (long)Ky * kz);
+                    for (int kx = 0; kx < Kx; ++kx) {
+                        const double w = krow[kx];
+                        const int dx = kx - hx; /* source index x - dx, wrapped */
+                        if (dx >= 0) {
+                            for (int x = 0; x < dx; ++x) o[x] += w * src[x - dx + X];
+                            for (int x = dx; x < X; ++x) o[x] += w * src[x - dx];
+                        } else {
+                            for (int x = 0; x < X + dx; ++x) o[x] += w * src[x - dx];
+                            for (int x = X + dx; x < X; ++x) o[x] += w * src[x - dx - X];
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* Mirrored kernel P^*(d) = P(-d) on the same centred box. */
+void mvdo_mirror(const double* k, const int kd[3], double* out) {
+    const int Kx = kd[0], Ky = kd[1], Kz = kd[2];
+    for (int z = 0; z < Kz; ++z)
+        for (int y = 0; y < Ky; ++y)
+            for (int x = 0; x < Kx; ++x)
+                out[idx3(Kx - 1 - x, Ky - 1 - y, Kz - 1 - z, Kx, Ky)] = k[idx3(x, y, z, Kx, Ky)];
+}
+
+/* Linear convolution of two small kernels, evaluated on a centred output box:
+ * out(d) = sum_e a(e) b(d - e), with b taken as 0 outside its box. */
+void mvdo_kconv(const double* a, const int ad[3], const double* b, const int bd[3],
+                double* out, const int od[3]) {
+    const int ahx = (ad[0] - 1) / 2, ahy = (ad[1] - 1) / 2, ahz = (ad[2] - 1) / 2;
+    const int bhx = (bd[0] - 1) / 2, bhy = (bd[1] - 1) / 2, bhz = (bd[2] - 1) / 2;
+    const int ohx = (od[0] - 1) / 2, ohy = (od[1] - 1) / 2, ohz = (od[2] - 1) / 2;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int oz = 0; oz < od[2]; ++oz) {
+        for (int oy = 0; oy < od[1]; ++oy) {
+            for (int ox = 0; ox < od[0]; ++ox) {
+                const int dx = ox - ohx, dy = oy - ohy, dz = oz - ohz;
+                double s = 0.0;
+                for (int ez = -ahz; ez <= ahz; ++ez) {
+                    const int qz = dz - ez;
+                    if (qz < -bhz || qz > bhz) continue;
+                    for (int ey = -ahy; ey <= ahy; ++ey) {
+                        const int qy = dy - ey;
+                        if (qy < -bhy || qy > bhy) continue;
+                        for (int ex = -ahx; ex <= ahx; ++ex) {
+                            const int qx = dx - ex;
+                            if (qx < -bhx || qx > bhx) continue;
+                            s += a[idx3(ex + ahx, ey + ahy, ez + ahz, ad[0], ad[1])] *
+                                 b[idx3(qx + bhx, qy + bhy, qz + bhz, bd[0], bd[1])];
+                        }
+                    }
+                }
+                out[idx3(ox, oy, oz, od[0], od[1])] = s;
+            }
+        }
+    }
+}
+
+/* Kernel used for the back-projection of view v (the "compound" kernel).
+ *   PLAIN:     P_v^*                                          (Eq. 51)
+ *   EFFICIENT: P_v^* . prod_{w != v} (P_v^* * P_w * P_w^*)     (Eq. 220, Eq. 222)
+ *   OPT1:      P_v^* . prod_{w != v} (P_v^* * P_w)             (Eq. 230)
+ *   OPT2:      P_v^* . prod_{w != v} P_v^*  = (P_v^*)^N          (Eq. 240)
+ * "." is the pointwise product on P_v's box; the result is normalised to sum 1.
+ * Returns 0 on success, -1 if the result sums to 0. */
+int mvdo_compound(int n_views, const double* const* psfs, const int* pdims /* n_views x 3 */,
+                  int v, int variant, double* out) {
+    const int* dv = pdims + 3 * v;
+    const long Tv = (long)dv[0] * dv[1] * dv[2];
+    double* pstar = (double*)malloc(sizeof(double) * Tv);
+    double* cvw = (double*)malloc(sizeof(double) * Tv);
+    mvdo_mirror(psfs[v], dv, pstar);
+    for (long i = 0; i < Tv; ++i) out[i] = pstar[i];
+    if (variant != MVDO_PLAIN) {
+        for (int w = 0; w < n_views; ++w) {
+            if (w == v) continue;
+            const int* dw = pdims + 3 * w;
+            if (variant == MVDO_EFFICIENT) {
+                /* Q_w = P_w * P_w^*  on its full box (2K-1), then C_vw = P_v^* * Q_w on P_v's box */
+                const long Tw = (long)dw[0] * dw[1] * dw[2];
+                int qd[3] = {2 * dw[0] - 1, 2 * dw[1] - 1, 2 * dw[2] - 1};
+                double* pwstar = (double*)malloc(sizeof(double) * Tw);
+                double* q = (double*)malloc(sizeof(double) * (long)qd[0] * qd[1] * qd[2]);
+                mvdo_mirror(psfs[w], dw, pwstar);
+                mvdo_kconv(psfs[w], dw, pwstar, dw, q, qd);
+                mvdo_kconv(pstar, dv, q, qd, cvw, dv);
+                free(pwstar);
+                free(q);
+            } else if (variant == MVDO_OPT1) {
+                mvdo_kconv(pstar, dv, psfs[w], dw, cvw, dv);
+            } else { /* OPT2: P_w treated as constant, so the virtual factor is P_v^* itself */
+                for (long i = 0; i < Tv; ++i) cvw[i] = pstar[i];
+            }
+            for (long i = 0; i < Tv; ++i) out[i] *= cvw[i];
+        }
+    }
+    double s = 0.0;
+    for (long i = 0; i < Tv; ++i) s += out[i];
+    free(pstar);
+    free(cvw);
+    if (!(s > 0.0)) return -1;
+    for (long i = 0; i < Tv; ++i) out[i] /= s;
+    return 0;
+}
+
+/* One view update (a Richardson-Lucy step with kernel P and back-projection kernel K):
+ *   b = psi * P ; r = phi / max(b, eps) ; c = r * K ; psi <- max(psi . c, eps).
+ * b_out / r_out / c_out, when non-NULL, receive the intermediates. */
+void mvdo_update(double* psi, const double* phi, const double* P, const int pd[3],
+                 const double* K, const int kd[3], const int dims[3], double eps,
+                 double* b_out, double* r_out, double* c_out) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double* b = b_out ? b_out : (double*)malloc(sizeof(double) * M);
+    double* r = r_out ? r_out : (double*)malloc(sizeof(double) * M);
+    double* c = c_out ? c_out : (double*)malloc(sizeof(double) * M);
+    mvdo_conv(psi, dims, P, pd, b);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < M; ++i) r[i] = phi[i] / fmax(b[i], eps);
+    mvdo_conv(r, dims, K, kd, c);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < M; ++i) psi[i] = fmax(psi[i] * c[i], eps);
+    if (!b_out) free(b);
+    if (!r_out) free(r);
+    if (!c_out) free(c);
+}
+
+/* Mean over all voxels of all views (the flat initial estimate's value). */
+double mvdo_mean_views(int n_views, const double* const* views, const int dims[3]) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double s = 0.0;
+    for (int v = 0; v < n_views; ++v)
+        for (long i = 0; i < M; ++i) s += views[v][i];
+    return s / ((double)M * n_views);
+}
+
+/* Full deconvolution: compound kernels, flat psi0 (unless init != 0, then psi
+ * holds the start), then n_iter iterations of the schedule (default 0..N-1),
+ * each view's update applied to psi at once.
+ * eps <= 0 selects 1e-4 * psi0. Returns the eps used, or -1 on error. */
+double mvdo_deconvolve(int n_views, const double* const* views, const double* const* psfs,
+                       const int* pdims, const int dims[3], int variant, int n_iter,
+                       const int* schedule, int schedule_len, double eps, int init,
+                       double* psi) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double psi0 = mvdo_mean_views(n_views, views, dims);
+    if (eps <= 0.0) eps = 1e-4 * psi0;
+    if (!init)
+        for (long i = 0; i < M; ++i) psi[i] = psi0;
+    double** comp = (double**)malloc(sizeof(double*) * n_views);
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        comp[v] = (double*)malloc(sizeof(double) * T);
+        if (mvdo_compound(n_views, psfs, pdims, v, variant, comp[v]) != 0) {
+            for (int u = 0; u <= v; ++u) free(comp[u]);
+            free(comp);
+            return -1.0;
+        }
+    }
+    double* b = (double*)malloc(sizeof(double) * M);
+    double* r = (double*)malloc(sizeof(double) * M);
+    double* c = (double*)malloc(sizeof(double) * M);
+    int L = (schedule && schedule_len > 0) ? schedule_len : n_views;
+    for (int it = 0; it < n_iter; ++it) {
+        for (int s = 0; s < L; ++s) {
+            int v = (schedule && schedule_len > 0) ? schedule[s] : s;
+            mvdo_update(psi, views[v], psfs[v], pdims + 3 * v, comp[v], pdims + 3 * v, dims, eps, b,
+                        r, c);
+        }
+    }
+    for (int v = 0; v < n_views; ++v) free(comp[v]);
+    free(comp);
+    free(b);
+    free(r);
+    free(c);
+    return eps;
+}
+
+/* One view update evaluated only at the listed voxels (flat indices):
+ *   out[i] = max(psi(x_i) * c(x_i), eps), with c, r, b computed from the
+ * definitions above on the neighbourhood each sample needs. */
+void mvdo_update_at(const double* psi, const double* phi, const double* P, const int pd[3],
+                    const double* K, const int kd[3], const int dims[3], double eps,
+                    const long* sample, int n_samples, double* out) {
+    const int X = dims[0], Y = dims[1], Z = dims[2];
+    const int phx = (pd[0] - 1) / 2, phy = (pd[1] - 1) / 2, phz = (pd[2] - 1) / 2;
+    const int khx = (kd[0] - 1) / 2, khy = (kd[1] - 1) / 2, khz = (kd[2] - 1) / 2;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int s = 0; s < n_samples; ++s) {
+        const long li = sample[s];
+        const int x = (int)(li % X), y = (int)((li / X) % Y), z = (int)(li / ((long)X * Y));
+        double c = 0.0;
+        for (int kz = 0; kz < kd[2]; ++kz)
+            for (int ky = 0; ky < kd[1]; ++ky)
+                for (int kx = 0; kx < kd[0]; ++kx) {
+                    /* r at u = x - d */
+                    const int ux = ((x - (kx - khx)) % X + X) % X;
+                    const int uy = ((y - (ky - khy)) % Y + Y) % Y;
+                    const int uz = ((z - (kz - khz)) % Z + Z) % Z;
+                    double b = 0.0;
+                    for (int pz = 0; pz < pd[2]; ++pz)
+                        for (int py = 0; py < pd[1]; ++py)
+                            for (int px = 0; px < pd[0]; ++px) {
+                                const int sx = ((ux - (px - phx)) % X + X) % X;
+                                const int sy = ((uy - (py - phy)) % Y + Y) % Y;
+                                const int sz = ((uz - (pz - phz)) % Z + Z) % Z;
+                                b += P[idx3(px, py, pz, pd[0], pd[1])] * psi[idx3(sx, sy, sz, X, Y)];
+                            }
+                    const double r = phi[idx3(ux, uy, uz, X, Y)] / fmax(b, eps);
+                    c += K[idx3(kx, ky, kz, kd[0], kd[1])] * r;
+                }
+        out[s] = fmax(psi[li] * c, eps);
+    }
+}

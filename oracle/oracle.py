@@ -1,0 +1,184 @@
+"""ctypes front end of the FP64 C oracle (``mvd_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring). Every function takes and
+returns float64 numpy arrays shaped ``[z][y][x]`` (kernels ``[Kz][Ky][Kx]``);
+the C file states which equation of the paper each step follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+PLAIN, EFFICIENT, OPT1, OPT2 = 0, 1, 2, 3
+VARIANTS = {"plain": PLAIN, "efficient": EFFICIENT, "opt1": OPT1, "opt2": OPT2}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mvd_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "libmvd_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O3, OpenMP) if the library is missing or stale."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O3", "-fPIC", "-shared", "-fopenmp", "-std=c11", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.mvdo_conv.argtypes = [_D, _I, _D, _I, _D]
+            lib.mvdo_mirror.argtypes = [_D, _I, _D]
+            lib.mvdo_kconv.argtypes = [_D, _I, _D, _I, _D, _I]
+            lib.mvdo_compound.argtypes = [ctypes.c_int, ctypes.POINTER(_D), _I, ctypes.c_int,
+                                          ctypes.c_int, _D]
+            lib.mvdo_compound.restype = ctypes.c_int
+            lib.mvdo_update.argtypes = [_D, _D, _D, _I, _D, _I, _I, ctypes.c_double, _D, _D, _D]
+            lib.mvdo_mean_views.argtypes = [ctypes.c_int, ctypes.POINTER(_D), _I]
+            lib.mvdo_mean_views.restype = ctypes.c_double
+            lib.mvdo_deconvolve.argtypes = [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D), _I,
+                                            _I, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_int, _D]
+            lib.mvdo_deconvolve.restype = ctypes.c_double
+            lib.mvdo_update_at.argtypes = [_D, _D, _D, _I, _D, _I, _I, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_long), ctypes.c_int, _D]
+            lib.mvdo_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _dims_xyz(a: np.ndarray):
+    z, y, x = a.shape
+    return (ctypes.c_int * 3)(x, y, z)
+
+
+def num_threads() -> int:
+    """Number of OpenMP threads the oracle runs on."""
+    return int(_load().mvdo_num_threads())
+
+
+def conv(vol, k) -> np.ndarray:
+    """Periodic convolution ``(vol * k)(x) = sum_d k(d) vol((x-d) mod dims)`` (Eq. 51's ``*``)."""
+    vol, k = _f64(vol), _f64(k)
+    out = np.empty_like(vol)
+    _load().mvdo_conv(_dptr(vol), _dims_xyz(vol), _dptr(k), _dims_xyz(k), _dptr(out))
+    return out
+
+
+def mirror(k) -> np.ndarray:
+    """Mirrored kernel ``P^*(d) = P(-d)`` (Suppl. Note "Integrating xi and x")."""
+    k = _f64(k)
+    out = np.empty_like(k)
+    _load().mvdo_mirror(_dptr(k), _dims_xyz(k), _dptr(out))
+    return out
+
+
+def kconv(a, b, out_shape_zyx) -> np.ndarray:
+    """Linear convolution of two small kernels evaluated on a centred box."""
+    a, b = _f64(a), _f64(b)
+    out = np.empty(out_shape_zyx, dtype=np.float64)
+    _load().mvdo_kconv(_dptr(a), _dims_xyz(a), _dptr(b), _dims_xyz(b), _dptr(out), _dims_xyz(out))
+    return out
+
+
+def _psf_arrays(psfs):
+    ps = [_f64(p) for p in psfs]
+    arr = (_D * len(ps))(*[_dptr(p) for p in ps])
+    pd = (ctypes.c_int * (3 * len(ps)))(*[d for p in ps for d in (p.shape[2], p.shape[1], p.shape[0])])
+    return ps, arr, pd
+
+
+def compound(psfs, v: int, variant="efficient") -> np.ndarray:
+    """Back-projection kernel of view ``v`` (Eq. 222 / Eq. 230 / Eq. 240 / Eq. 51), sum 1."""
+    var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    ps, arr, pd = _psf_arrays(psfs)
+    out = np.empty_like(ps[v])
+    rc = _load().mvdo_compound(len(ps), arr, pd, v, var, _dptr(out))
+    if rc != 0:
+        raise ValueError("compound kernel sums to zero")
+    return out
+
+
+def update(psi, phi, P, K, eps, intermediates=False):
+    """One view update (Eq. 15 with back-projection kernel K); returns the new psi.
+
+    With ``intermediates`` also returns ``(b, r, c)``.
+    """
+    psi = _f64(psi).copy()
+    phi, P, K = _f64(phi), _f64(P), _f64(K)
+    b, r, c = (np.empty_like(psi) for _ in range(3))
+    _load().mvdo_update(_dptr(psi), _dptr(phi), _dptr(P), _dims_xyz(P), _dptr(K), _dims_xyz(K),
+                        _dims_xyz(psi), float(eps), _dptr(b), _dptr(r), _dptr(c))
+    if intermediates:
+        return psi, (b, r, c)
+    return psi
+
+
+def update_at(psi, phi, P, K, eps, flat_indices) -> np.ndarray:
+    """One view update evaluated only at the given flat voxel indices."""
+    psi, phi, P, K = _f64(psi), _f64(phi), _f64(P), _f64(K)
+    idx = np.ascontiguousarray(flat_indices, dtype=np.int64)
+    out = np.empty(idx.shape[0], dtype=np.float64)
+    _load().mvdo_update_at(_dptr(psi), _dptr(phi), _dptr(P), _dims_xyz(P), _dptr(K), _dims_xyz(K),
+                           _dims_xyz(psi), float(eps), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                           int(idx.shape[0]), _dptr(out))
+    return out
+
+
+def mean_views(views) -> float:
+    """Flat initial estimate's value: mean over all voxels of all views."""
+    vs = [_f64(v) for v in views]
+    arr = (_D * len(vs))(*[_dptr(v) for v in vs])
+    return float(_load().mvdo_mean_views(len(vs), arr, _dims_xyz(vs[0])))
+
+
+def deconvolve(views, psfs, n_iter, variant="efficient", schedule=None, eps=0.0, psi_init=None):
+    """Sequential (OSEM-order) efficient Bayesian deconvolution in FP64.
+
+    Returns ``(psi, eps_used)``. ``eps <= 0`` selects ``1e-4 * psi0``.
+    """
+    var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    vs = [_f64(v) for v in views]
+    ps, parr, pd = _psf_arrays(psfs)
+    varr = (_D * len(vs))(*[_dptr(v) for v in vs])
+    if psi_init is None:
+        psi = np.empty_like(vs[0])
+        init = 0
+    else:
+        psi = _f64(psi_init).copy()
+        init = 1
+    if schedule is None:
+        sched, slen = None, 0
+    else:
+        sched = (ctypes.c_int * len(schedule))(*[int(s) for s in schedule])
+        slen = len(schedule)
+    used = _load().mvdo_deconvolve(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), sched,
+                                   slen, float(eps), init, _dptr(psi))
+    if used < 0:
+        raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
+    return psi, used
