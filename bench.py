@@ -1,0 +1,324 @@
+"""Throughput benchmark: voxel-view updates per second of the efficient
+Bayesian multi-view update on GB300, through the library's C ABI.
+
+Default workload: 256x256x128 volume, 4 views at 0/90/180/270 deg about y,
+15x15x41 PSFs (sigma 1.2/4), 3000 ellipsoids, Poisson noise at peak 100
+photons, 20 sequential (OSEM-order) iterations of the efficient method.
+
+One step = one deconvolution of that volume: psi reset to the flat estimate,
+then 20 iterations x 4 view updates (views and kernel spectra resident in
+HBM; the PSFs of a time series are fixed, so kernels are precomputed once).
+value = voxels * views * iterations / step time, in Gvoxel-view/s.
+e2e = the same metric through the public API from pinned host buffers:
+create (H2D of the views) + precompute + iterate + result (D2H) + destroy.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank deconvolves its own independent volume (another
+time point of the same acquisition): weak scaling, no collective on the data
+path; barrier + max over ranks around the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gvoxel-view updates/s"
+UNIT = "Gvoxel-view/s"
+L2_BYTES = 129 * 2 ** 20
+
+# algorithmic bytes per voxel for each update kernel: every input and output
+# array it must touch, once (half spectrum = 8 * (X/2+1) * Y * Z bytes)
+def _kernel_bytes(X, Y, Z):
+    M = X * Y * Z
+    spec = 8 * (X // 2 + 1) * Y * Z
+    return {
+        "x_forward": 4 * M + spec,          # read psi, write S
+        "y": 2 * spec,                      # read S, write S
+        "z_mul": 3 * spec,                  # read S and the kernel spectrum, write S
+        "x_ratio": 2 * spec + 4 * M,        # read S and phi, write S
+        "x_update": spec + 8 * M,           # read S and psi, write psi
+        "direct_ratio": 12 * M,             # read psi and phi, write r
+        "direct_update": 12 * M,            # read r and psi, write psi
+    }
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _workload(rank: int):
+    import synth
+
+    return synth.config2(seed=1002 + 1000 * rank)
+
+
+def _cpu_baseline(w, eps, steps=1):
+    """FP64 oracle on the host cores: one view update of the workload per step."""
+    import oracle
+
+    psfs64 = [p.astype(np.float64) / p.astype(np.float64).sum() for p in w.psfs]
+    K = oracle.compound(psfs64, 0, "efficient")
+    psi = np.full(w.truth.shape, float(np.mean([v.mean(dtype=np.float64) for v in w.views])))
+    phi = w.views[0].astype(np.float64)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.update(psi, phi, psfs64[0], K, eps)
+        times.append(time.perf_counter() - t0)
+    return times, oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = _workload(0)
+    eps = 1e-4 * float(np.mean([v.mean(dtype=np.float64) for v in w.views]))
+    _cpu_baseline(w, eps, steps=args.warmup) if args.warmup > 0 else None
+    times, cores = _cpu_baseline(w, eps, steps=args.steps)
+    total = sum(times)
+    value = w.voxels * args.steps / total / 1e9
+    sample = (f"one view update (view 0) of the {w.dims[0]}x{w.dims[1]}x{w.dims[2]} 4-view workload per step, "
+              f"FP64 direct convolution")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "volume": list(w.dims), "views": w.n_views, "psf_box": [15, 15, 41],
+                   "iterations": w.n_iter, "variant": "efficient"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_1308_0730_gb300 import mvd
+
+    w = _workload(rank)
+    X, Y, Z = w.dims
+    M = w.voxels
+    stream = torch.cuda.Stream()
+    upd_per_step = w.n_views * w.n_iter
+    units_per_step = M * upd_per_step
+
+    # --- device-resident run (value) ---
+    with torch.cuda.stream(stream):
+        dviews = [torch.from_numpy(v).to(f"cuda:{local}", non_blocking=False) for v in w.views]
+    stream.synchronize()
+    d = mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft", device=local)
+
+    def step():
+        d.set_estimate(None)
+        d.iterate(w.n_iter)
+
+    for _ in range(args.warmup):
+        step()
+    d.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = mvd.mvd_launch_count()
+    mvd.mvd_profile_enable(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = mvd.mvd_profile_read()
+    mvd.mvd_profile_enable(False)
+    launches = mvd.mvd_launch_count() - launches0
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    psi_dev = d.result()
+    d.close()
+
+    # --- end to end through the public API from pinned host buffers ---
+    pinned = [torch.from_numpy(v).pin_memory() for v in w.views]
+    hviews = [p.numpy() for p in pinned]
+    out = torch.empty(w.truth.shape, dtype=torch.float32).pin_memory().numpy()
+
+    def e2e_step():
+        with mvd.Deconvolver(hviews, w.psfs, "efficient", stream=stream, path="fft", device=local) as e:
+            e.iterate(w.n_iter)
+            e.result(out)
+
+    e2e_step()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert np.allclose(out, psi_dev, rtol=1e-6, atol=0), "end-to-end result differs from the device run"
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        kb = _kernel_bytes(X, Y, Z)
+        per_kernel = {}
+        for name, (n, tot) in prof.items():
+            if n and name in kb:
+                per_kernel[name] = {"launches": n, "avg_us": 1e3 * tot / n, "share": tot / max(1e-9, sum(
+                    t for (_, t) in prof.values())), "GBps": kb[name] / (tot / n * 1e-3) / 1e9}
+        dom = max(per_kernel, key=lambda k: prof[k][1])
+        achieved = per_kernel[dom]["GBps"]
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tf):
+            with open(tf) as fh:
+                tr = json.load(fh)
+            key = f"{dom}@{X}x{Y}x{Z}"
+            traffic = tr.get(key)
+        value = ws * units_per_step * args.steps / (t_max * 1e-3) / 1e9
+        cpu_times, cores = _cpu_baseline(w, 1e-4 * float(np.mean([v.mean(dtype=np.float64) for v in w.views])))
+        cpu_value = M / cpu_times[0] / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "volume": [X, Y, Z], "views": w.n_views,
+                       "psf_box": [15, 15, 41], "iterations": w.n_iter, "variant": "efficient",
+                       "engine": "fft", "l2": "inputs larger than L2 (views + kernel spectra "
+                       f"{(4 * M * w.n_views + 16 * (X // 2 + 1) * Y * Z * w.n_views) / 2**20:.0f} MiB > 129 MiB)",
+                       "parallelism": f"replicas x{ws}"},
+            "e2e": {"value": ws * units_per_step / e2e_s / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(v.nbytes for v in w.views) + sum(p.nbytes for p in w.psfs)),
+                    "d2h_bytes_per_step": int(out.nbytes)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind},
+            "update_effective_hbm_frac": (12.0 * units_per_step * args.steps / (ms * 1e-3) / 1e9) / peak,
+            "kernels": per_kernel,
+            "clocks": clk.summary(),
+            "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"one view update (view 0) of the {X}x{Y}x{Z} workload, FP64 direct "
+                                       f"convolution, {cpu_times[0]:.1f} s"},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mvd", choices=["mvd", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * mvd.h - C ABI of the GB300 (sm_103a) efficient Bayesian multi-view
+ * deconvolution library (Preibisch et al., "Efficient Bayesian-based
+ * multi-view deconvolution", arXiv:1308.0730).
+ *
+ * The library runs, on one GPU, the sequential (OSEM-order) efficient
+ * Bayesian update of the paper (Suppl. Note "Alternative iteration for faster
+ * convergence", applied to Eq. 220):
+ *
+ *   for each iteration, for each view v of the schedule:
+ *     b   = psi * P_v                     forward blur        (Eq. 51)
+ *     r   = phi_v / max(b, eps)           ratio               (Eq. 15)
+ *     c   = r * P_v^comp                  back-projection     (Eq. 220)
+ *     psi = max(psi . c, eps)             multiplicative step (Eq. 15)
+ *
+ * with P_v^comp the compound kernel of Eq. 222 (or of Eq. 230, Eq. 240, or
+ * the plain mirrored PSF of Eq. 51). "*" is periodic (circular) convolution
+ * on the volume grid, (f * k)(x) = sum_d k(d) f((x - d) mod dims).
+ *
+ * Conventions shared by every entry point
+ *   Layout   FP32 volumes, x fastest: voxel (x,y,z) at index x + X*(y + Y*z).
+ *            dims = {X, Y, Z}. PSFs are FP32 boxes {Kx, Ky, Kz}, each size
+ *            odd, centre at ((Kx-1)/2, (Ky-1)/2, (Kz-1)/2), same layout.
+ *   Memory   Caller buffers are read during the call only and never
+ *            retained. The context owns all device memory it allocates and
+ *            mvd_destroy frees it.
+ *   Order    create -> precompute_kernels -> (set_estimate) -> iterate* ->
+ *            result. A call out of order returns MVD_ERR_STATE.
+ *   Streams  All device work is ordered on the stream given at create
+ *            (NULL = the legacy default stream). Entry points that return
+ *            data to the host synchronise that stream; the others only
+ *            enqueue work (errors of enqueued kernels surface at the next
+ *            synchronising call).
+ *   Errors   Every call returns an mvd_status; nothing aborts, exits or
+ *            throws across the ABI. mvd_last_error() gives a message for the
+ *            last failing call on the calling thread.
+ *   Threads  A context may be used from one thread at a time.
+ */
+#ifndef MVD_H
+#define MVD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mvd_ctx mvd_ctx; /* opaque; owns all device memory of one problem */
+
+typedef enum {
+    MVD_OK = 0,
+    MVD_ERR_ARG = 1,         /* invalid argument value (NULL, negative/NaN view, PSF sum <= 0, ...) */
+    MVD_ERR_SHAPE = 2,       /* inconsistent sizes (even PSF size, PSF larger than the volume, ...) */
+    MVD_ERR_STATE = 3,       /* call out of order */
+    MVD_ERR_OOM = 4,         /* a device allocation failed */
+    MVD_ERR_CUDA = 5,        /* a CUDA runtime call or kernel failed */
+    MVD_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    MVD_ERR_UNSUPPORTED = 7  /* valid request this build does not handle */
+} mvd_status;
+
+/* Back-projection kernel variant (what mvd_precompute_kernels builds). */
+typedef enum {
+    MVD_PLAIN = 0,     /* P_v^*  (Eq. 51; with one view, classic Richardson-Lucy, Eq. 15) */
+    MVD_EFFICIENT = 1, /* P_v^* . prod_{w!=v} (P_v^* * P_w * P_w^*)   (Eq. 222) */
+    MVD_OPT1 = 2,      /* P_v^* . prod_{w!=v} (P_v^* * P_w)           (Eq. 230) */
+    MVD_OPT2 = 3       /* (P_v^*)^N                                    (Eq. 240) */
+} mvd_variant;
+
+/* Convolution engine. AUTO lets the autotuner pick per (dims, PSF boxes). */
+typedef enum { MVD_PATH_AUTO = 0, MVD_PATH_DIRECT = 1, MVD_PATH_FFT = 2 } mvd_path;
+
+typedef struct {
+    float eps;           /* floor of b and psi; <= 0 selects 1e-4 * psi0 */
+    int path;            /* mvd_path */
+    void* stream;        /* cudaStream_t to order all work on; NULL = default stream */
+    int views_on_device; /* 1: `views` are device pointers (copied device-to-device) */
+    int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
+} mvd_options;
+
+/* Fills *opt with eps = 0 (auto), path = AUTO, stream = NULL, host views, device -1. */
+void mvd_default_options(mvd_options* opt);
+
+/*
+ * Creates a context for one deconvolution problem.
+ *   views     n_views pointers to X*Y*Z floats (observed views phi_v on the
+ *             common registered grid, Eq. 51's identity-transform assumption);
+ *             host pointers, or device pointers if opt->views_on_device.
+ *             Values must be finite and >= 0 (Eq. 3), else MVD_ERR_ARG.
+ *   psfs      n_views host pointers to Kx*Ky*Kz floats (P_v); values >= 0 and
+ *             sum > 0, else MVD_ERR_ARG. Each PSF is normalised to sum 1
+ *             (Eq. 3) when copied.
+ *   psf_dims  3*n_views ints {Kx,Ky,Kz} per view; odd and <= dims, else
+ *             MVD_ERR_SHAPE.
+ *   dims      {X, Y, Z}, each >= 1.
+ *   opt       may be NULL (defaults).
+ *   out       receives the context; *out is NULL on failure.
+ * Copies the views to the device (the context owns the copies), computes
+ * psi0 = mean over all voxels of all views (the flat estimate, Eq. 15 text)
+ * and eps, and sets psi = psi0.
+ */
+mvd_status mvd_create(const float* const* views, int n_views, const float* const* psfs,
+                      const int* psf_dims, const int dims[3], const mvd_options* opt,
+                      mvd_ctx** out);
+
+/*
+ * Builds P_v^comp for every view on the device (FP32) for the given
+ * mvd_variant (Eq. 222 / Eq. 230 / Eq. 240 / Eq. 51), normalised to sum 1,
+ * on P_v's own box; chooses the convolution engine (autotuner when the path
+ * is AUTO) and, for the FFT engine, builds the two kernel spectra per view.
+ * May be called again to switch variant.
+ */
+mvd_status mvd_precompute_kernels(mvd_ctx* ctx, int variant);
+
+/* Sets the estimate: psi = psi0 (flat) if psi == NULL, else copies X*Y*Z
+ * floats (> 0) from psi (a device pointer if on_device, else host). */
+mvd_status mvd_set_estimate(mvd_ctx* ctx, const float* psi, int on_device);
+
+/*
+ * Runs n_iter iterations of the sequential update. One iteration applies the
+ * update of every view in `schedule` once, in order (schedule_len entries in
+ * [0, n_views)); schedule == NULL or schedule_len == 0 means 0..n_views-1.
+ * Enqueues work only.
+ */
+mvd_status mvd_iterate(mvd_ctx* ctx, int n_iter, const int* schedule, int schedule_len);
+
+/* Copies psi (X*Y*Z floats) to host memory `out`; n_elems must be >= X*Y*Z.
+ * Synchronises the context's stream. */
+mvd_status mvd_result(mvd_ctx* ctx, float* out, size_t n_elems);
+
+/* Hands out the device pointer of psi (borrowed; valid until the next call
+ * that mutates or destroys the context). Does not synchronise. */
+mvd_status mvd_result_device(mvd_ctx* ctx, const float** dptr);
+
+/* Waits for all work enqueued on the context's stream. */
+mvd_status mvd_synchronize(mvd_ctx* ctx);
+
+/* Frees everything the context owns. NULL is ignored. */
+void mvd_destroy(mvd_ctx* ctx);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* mvd_last_error(void);
+
+/* Introspection. */
+float mvd_get_eps(const mvd_ctx* ctx);  /* floor in use */
+float mvd_get_psi0(const mvd_ctx* ctx); /* flat estimate value */
+int mvd_get_path(const mvd_ctx* ctx);   /* MVD_PATH_DIRECT or MVD_PATH_FFT once precomputed */
+
+/* Copies the compound kernel of view v (Kx*Ky*Kz floats, PSF layout) to host
+ * memory `out` (n_elems >= that size). Synchronises the stream. */
+mvd_status mvd_get_compound_kernel(mvd_ctx* ctx, int v, float* out, size_t n_elems);
+
+/* Number of kernels this library has launched in the process so far. */
+unsigned long long mvd_launch_count(void);
+
+/*
+ * Per-kernel timing for measurement. While enabled, every launch of the
+ * update's kernels is bracketed by two CUDA events recorded on the launching
+ * stream. mvd_profile_read synchronises on the recorded events and returns,
+ * per kernel class, the class name (static string), the number of timed
+ * launches and their summed duration in milliseconds; it returns the number
+ * of classes written (<= max). Enabling again discards earlier records.
+ * Classes: x_forward, y, z_mul, x_ratio, x_update, direct_ratio,
+ * direct_update, setup.
+ */
+void mvd_profile_enable(int on);
+int mvd_profile_read(const char** names, unsigned long long* launches, double* ms, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MVD_H */

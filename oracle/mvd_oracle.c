@@ -212,8 +212,8 @@ double mvdo_mean_views(int n_views, const double* const* views, const int dims[3
     return s / ((double)M * n_views);
 }
 
-/* Full deconvolution: compound kernels, flat psi0 (unless init != 0, then psi
- * holds the start), then n_iter iterations of the schedule (default 0..N-1),
+/* Full deconvolution: PSFs normalised to sum 1, compound kernels, flat psi0
+ * (unless init != 0, then psi holds the start), then n_iter iterations of the schedule (default 0..N-1),
  * each view's update applied to psi at once.
  * eps <= 0 selects 1e-4 * psi0. Returns the eps used, or -1 on error. */
 double mvdo_deconvolve(int n_views, const double* const* views, const double* const* psfs,
@@ -225,13 +225,24 @@ double mvdo_deconvolve(int n_views, const double* const* views, const double* co
     if (eps <= 0.0) eps = 1e-4 * psi0;
     if (!init)
         for (long i = 0; i < M; ++i) psi[i] = psi0;
+    /* every PSF is a probability distribution: normalise to sum 1 (Eq. 3) */
+    double** pn = (double**)malloc(sizeof(double*) * n_views);
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        double s = 0.0;
+        for (long i = 0; i < T; ++i) s += psfs[v][i];
+        pn[v] = (double*)malloc(sizeof(double) * T);
+        for (long i = 0; i < T; ++i) pn[v][i] = psfs[v][i] / s;
+    }
     double** comp = (double**)malloc(sizeof(double*) * n_views);
     for (int v = 0; v < n_views; ++v) {
         const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
         comp[v] = (double*)malloc(sizeof(double) * T);
-        if (mvdo_compound(n_views, psfs, pdims, v, variant, comp[v]) != 0) {
+        if (mvdo_compound(n_views, (const double* const*)pn, pdims, v, variant, comp[v]) != 0) {
             for (int u = 0; u <= v; ++u) free(comp[u]);
+            for (int u = 0; u < n_views; ++u) free(pn[u]);
             free(comp);
+            free(pn);
             return -1.0;
         }
     }
@@ -242,12 +253,13 @@ double mvdo_deconvolve(int n_views, const double* const* views, const double* co
     for (int it = 0; it < n_iter; ++it) {
         for (int s = 0; s < L; ++s) {
             int v = (schedule && schedule_len > 0) ? schedule[s] : s;
-            mvdo_update(psi, views[v], psfs[v], pdims + 3 * v, comp[v], pdims + 3 * v, dims, eps, b,
-                        r, c);
+            mvdo_update(psi, views[v], pn[v], pdims + 3 * v, comp[v], pdims + 3 * v, dims, eps, b, r, c);
         }
     }
     for (int v = 0; v < n_views; ++v) free(comp[v]);
+    for (int v = 0; v < n_views; ++v) free(pn[v]);
     free(comp);
+    free(pn);
     free(b);
     free(r);
     free(c);

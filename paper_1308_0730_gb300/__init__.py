@@ -1,0 +1,26 @@
+"""GB300 (sm_103a) efficient Bayesian multi-view deconvolution.
+
+The compute path is libmvd.so (CUDA, C ABI in include/mvd.h); ``mvd`` is its
+thin Python binding.
+"""
+from .mvd import (  # noqa: F401
+    Deconvolver,
+    MvdError,
+    load,
+    mvd_create,
+    mvd_precompute_kernels,
+    mvd_set_estimate,
+    mvd_iterate,
+    mvd_result,
+    mvd_result_device,
+    mvd_synchronize,
+    mvd_destroy,
+    mvd_last_error,
+    mvd_launch_count,
+    mvd_get_eps,
+    mvd_get_psi0,
+    mvd_get_path,
+    mvd_get_compound_kernel,
+    mvd_profile_enable,
+    mvd_profile_read,
+)

@@ -1,0 +1,146 @@
+// Shared internals of the mvd library: error reporting, launch accounting,
+// the FFT plan type and the context struct.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "mvd.h"
+
+namespace mvd {
+
+// ---------------------------------------------------------------------------
+// errors and accounting
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(unsigned n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Optional per-kernel timing (mvd_profile_*): a pair of CUDA events on the
+// launching stream around each launch of a given class.
+enum KernelClass {
+    KC_X_FORWARD = 0,
+    KC_Y,
+    KC_Z_MUL,
+    KC_X_RATIO,
+    KC_X_UPDATE,
+    KC_DIRECT_RATIO,
+    KC_DIRECT_UPDATE,
+    KC_SETUP,
+    KC_COUNT
+};
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st);
+
+// Converts the last CUDA error (after a launch) into a status.
+mvd_status check_launch(const char* what);
+mvd_status cuda_status(cudaError_t e, const char* what);
+
+#define MVD_TRY(expr)                          \
+    do {                                       \
+        mvd_status _st = (expr);               \
+        if (_st != MVD_OK) return _st;         \
+    } while (0)
+
+#define MVD_CUDA(call)                                           \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return ::mvd::cuda_status(_e, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// FFT plan: one line length L = prod(radix[s]); tw[m] = exp(-2 pi i m / L)
+// (device table, computed in FP64 on the host and rounded to FP32).
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 16;
+
+struct FftPlan {
+    int L;
+    int nst;
+    int radix[kMaxStages];
+    const float2* tw;
+};
+
+// Radix plan for a {2,3,5}-smooth length; false if L has another prime factor.
+bool make_radix_plan(int L, FftPlan* p);
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+struct FftGeom {
+    int X, Y, Z, Xh;
+    long YZ;
+    FftPlan px, py, pz;
+};
+
+// Spectrum layout: S[kx][z][y] (y fastest), kx in [0, Xh), Xh = X/2 + 1.
+mvd_status fft_forward_real(const FftGeom& g, const float* src, float2* S, cudaStream_t st);
+mvd_status fft_y(const FftGeom& g, float2* S, int inverse, cudaStream_t st);
+mvd_status fft_z_mul(const FftGeom& g, float2* S, const float2* K, cudaStream_t st);
+mvd_status fft_z_forward_scaled(const FftGeom& g, float2* S, float scale, cudaStream_t st);
+mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
+mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st);
+mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
+
+// Direct (spatial) periodic convolution with fused epilogues.
+bool direct_supported(const int kd[3]);
+mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, const int kd[3],
+                        const float* phi, float eps, float* r, cudaStream_t st);
+mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
+                         float* psi, float eps, cudaStream_t st);
+mvd_status direct_conv(const int dims[3], const float* in, const float* k, const int kd[3],
+                       float* out, cudaStream_t st);
+
+// Compound-kernel precompute and helpers.
+mvd_status build_compound(int n_views, const float* d_psf, const long* koff_h, const int* kd_h,
+                          int v, int variant, float* d_out, float* d_tmp, double* d_red,
+                          cudaStream_t st);
+mvd_status normalize_kernel(float* d_k, int n, int* d_bad, cudaStream_t st);
+mvd_status place_kernel(const int dims[3], const float* k, const int kd[3], float* vol,
+                        cudaStream_t st);
+mvd_status view_stats(const float* views, long n, double* d_sum, int* d_bad, cudaStream_t st);
+mvd_status fill(float* p, long n, float v, cudaStream_t st);
+mvd_status check_positive(const float* p, long n, int* d_bad, cudaStream_t st);
+
+}  // namespace mvd
+
+// ---------------------------------------------------------------------------
+// the context
+// ---------------------------------------------------------------------------
+struct mvd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int dims[3] = {0, 0, 0};
+    long M = 0;
+    int nv = 0;
+    std::vector<int> kd;     // 3 per view
+    std::vector<long> koff;  // offset of each view's box in the packed kernel arrays
+    long ktotal = 0;
+
+    float* d_views = nullptr;  // nv * M
+    float* d_psi = nullptr;    // M
+    float* d_r = nullptr;      // M (direct-path ratio; scratch for kernel placement)
+    float* d_psf = nullptr;    // packed normalised PSFs
+    float* d_comp = nullptr;   // packed compound kernels
+    float* d_ktmp = nullptr;   // precompute scratch
+    double* d_red = nullptr;   // reduction scratch
+    int* d_flag = nullptr;
+
+    // FFT engine
+    mvd::FftGeom geom{};
+    float2* d_tw = nullptr;  // twiddle tables (x, y, z)
+    float2* d_S = nullptr;   // work spectrum Xh*Y*Z
+    float2* d_K = nullptr;   // 2*nv kernel spectra (P_v, then P_v^comp), each Xh*Y*Z
+
+    int state = 0;  // 1 created, 2 kernels precomputed
+    int variant = -1;
+    int path_opt = MVD_PATH_AUTO;
+    int path = MVD_PATH_AUTO;
+    float psi0 = 0.f, eps = 0.f;
+};

@@ -1,0 +1,184 @@
+// Device-side FFT building blocks: complex helpers, radix-2/3/4/5/8 DFT
+// butterflies and a shared-memory Stockham (self-sorting) driver that runs
+// the same length-L transform on a batch of lines held in shared memory.
+//
+// Stockham stage with radix R after Ns points have been combined (Ns starts
+// at 1 and is multiplied by R after each stage): for butterfly j in [0, L/R)
+// with k = j mod Ns,
+//   v[r] = A[j + r L/R] * exp(s 2 pi i r k / (Ns R)),   r = 0..R-1
+//   v    = DFT_R(v)   (sign s)
+//   B[(j / Ns) Ns R + k + r Ns] = v[r]
+// which leaves the output in natural order after the last stage. s = -1 is
+// the forward transform, s = +1 the (unnormalised) inverse.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mvd {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by s*i (s = -1 forward, +1 inverse)
+template <int S>
+__device__ __forceinline__ float2 mul_si(float2 a) {
+    return S < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// exp(s 2 pi i m / L) from the forward table tw[m] = exp(-2 pi i m / L)
+template <int S>
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int m) {
+    float2 w = __ldg(tw + m);
+    if (S > 0) w.y = -w.y;
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// small DFTs: y[m] = sum_r v[r] exp(s 2 pi i r m / R)
+// ---------------------------------------------------------------------------
+template <int R, int S>
+struct Dft;
+
+template <int S>
+struct Dft<2, S> {
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <int S>
+struct Dft<4, S> {
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        float2 t2 = cadd(v[1], v[3]), t3 = mul_si<S>(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+
+template <int S>
+struct Dft<8, S> {
+    __device__ __forceinline__ static void run(float2* v) {
+        // split into even / odd radix-4 DFTs, then combine with exp(s 2 pi i m / 8)
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, S>::run(e);
+        Dft<4, S>::run(o);
+        const float h = 0.70710678118654752440f;  // sqrt(2)/2
+        // w1 = h (1 + s i), w2 = s i, w3 = h (-1 + s i)
+        float2 o1 = make_float2(h * (o[1].x - S * o[1].y), h * (o[1].y + S * o[1].x));
+        float2 o2 = mul_si<S>(o[2]);
+        float2 o3 = make_float2(h * (-o[3].x - S * o[3].y), h * (-o[3].y + S * o[3].x));
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
+template <int S>
+struct Dft<3, S> {
+    __device__ __forceinline__ static void run(float2* v) {
+        const float c = -0.5f, h = 0.86602540378443864676f;  // cos(2pi/3), sin(2pi/3)
+        float2 t = cadd(v[1], v[2]);
+        float2 u = csub(v[1], v[2]);
+        float2 m = make_float2(v[0].x + c * t.x, v[0].y + c * t.y);
+        float2 j = mul_si<S>(cscale(u, h));
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, j);
+        v[2] = csub(m, j);
+    }
+};
+
+template <int S>
+struct Dft<5, S> {
+    __device__ __forceinline__ static void run(float2* v) {
+        const float c1 = 0.30901699437494742410f;   // cos(2pi/5)
+        const float c2 = -0.80901699437494742410f;  // cos(4pi/5)
+        const float s1 = 0.95105651629515357212f;   // sin(2pi/5)
+        const float s2 = 0.58778525229247312917f;   // sin(4pi/5)
+        float2 t1 = cadd(v[1], v[4]), u1 = csub(v[1], v[4]);
+        float2 t2 = cadd(v[2], v[3]), u2 = csub(v[2], v[3]);
+        float2 a0 = v[0];
+        float2 m1 = make_float2(a0.x + c1 * t1.x + c2 * t2.x, a0.y + c1 * t1.y + c2 * t2.y);
+        float2 m2 = make_float2(a0.x + c2 * t1.x + c1 * t2.x, a0.y + c2 * t1.y + c1 * t2.y);
+        float2 j1 = mul_si<S>(make_float2(s1 * u1.x + s2 * u2.x, s1 * u1.y + s2 * u2.y));
+        float2 j2 = mul_si<S>(make_float2(s2 * u1.x - s1 * u2.x, s2 * u1.y - s1 * u2.y));
+        v[0] = make_float2(a0.x + t1.x + t2.x, a0.y + t1.y + t2.y);
+        v[1] = cadd(m1, j1);
+        v[4] = csub(m1, j1);
+        v[2] = cadd(m2, j2);
+        v[3] = csub(m2, j2);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// one Stockham butterfly (see the file header)
+// ---------------------------------------------------------------------------
+template <int R, int S>
+__device__ __forceinline__ void stockham_bfly(const float2* __restrict__ A, float2* __restrict__ B, int j,
+                                              int Ns, int L, const float2* __restrict__ tw) {
+    const int nb = L / R;
+    const int k = j % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = A[j + r * nb];
+    if (Ns > 1) {
+        const int step = k * (L / (Ns * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<S>(tw, r * step));
+    }
+    Dft<R, S>::run(v);
+    const int d = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) B[d + r * Ns] = v[r];
+}
+
+// Transforms `nlines` lines of length p.L stored at A + line*ls (line stride
+// ls >= L), using B (same shape) as the ping-pong buffer. All threads of the
+// block take part; the call begins and ends with the data synchronised.
+// Returns the buffer (A or B) that holds the result.
+template <int S>
+__device__ float2* fft_lines(float2* A, float2* B, int nlines, int ls, const FftPlan& p) {
+    int Ns = 1;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.radix[s];
+        const int nb = p.L / R;
+        const int total = nlines * nb;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int line = t / nb;
+            const int j = t - line * nb;
+            const float2* a = A + line * ls;
+            float2* b = B + line * ls;
+            switch (R) {
+                case 8: stockham_bfly<8, S>(a, b, j, Ns, p.L, p.tw); break;
+                case 4: stockham_bfly<4, S>(a, b, j, Ns, p.L, p.tw); break;
+                case 2: stockham_bfly<2, S>(a, b, j, Ns, p.L, p.tw); break;
+                case 3: stockham_bfly<3, S>(a, b, j, Ns, p.L, p.tw); break;
+                default: stockham_bfly<5, S>(a, b, j, Ns, p.L, p.tw); break;
+            }
+        }
+        __syncthreads();
+        float2* t = A;
+        A = B;
+        B = t;
+        Ns *= R;
+    }
+    return A;
+}
+
+}  // namespace mvd

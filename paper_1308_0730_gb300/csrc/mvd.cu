@@ -1,0 +1,650 @@
+// C ABI of the mvd library (declared in include/mvd.h): context life cycle,
+// precompute, the sequential update loop and result access.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mvd {
+
+std::atomic<unsigned long long> g_launches{0};
+static thread_local std::string t_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+}
+
+void clear_error() { t_err.clear(); }
+
+mvd_status cuda_status(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MVD_ERR_OOM : MVD_ERR_CUDA;
+}
+
+mvd_status check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, what);
+    return MVD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-kernel event timing
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+std::atomic<int> g_prof_on{0};
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_pool;
+size_t g_pool_used = 0;
+thread_local int t_open_cls = -1;
+thread_local cudaEvent_t t_open_ev = nullptr;
+const char* kClassNames[KC_COUNT] = {"x_forward", "y", "z_mul", "x_ratio", "x_update",
+                                     "direct_ratio", "direct_update", "setup"};
+
+cudaEvent_t next_event() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_pool_used == g_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        g_pool.push_back(e);
+    }
+    return g_pool[g_pool_used++];
+}
+}  // namespace
+
+void prof_begin(int cls, cudaStream_t st) {
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    cudaEvent_t e = next_event();
+    if (!e || cudaEventRecord(e, st) != cudaSuccess) return;
+    t_open_cls = cls;
+    t_open_ev = e;
+}
+
+void prof_end(int cls, cudaStream_t st) {
+    if (!g_prof_on.load(std::memory_order_relaxed) || t_open_cls != cls) return;
+    t_open_cls = -1;
+    cudaEvent_t e = next_event();
+    if (!e || cudaEventRecord(e, st) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back({cls, t_open_ev, e});
+}
+
+bool make_radix_plan(int L, FftPlan* p) {
+    p->L = L;
+    p->nst = 0;
+    int n = L, a = 0, n3 = 0, n5 = 0;
+    while (n % 2 == 0) n /= 2, ++a;
+    while (n % 3 == 0) n /= 3, ++n3;
+    while (n % 5 == 0) n /= 5, ++n5;
+    if (n != 1) return false;
+    auto push = [&](int r) {
+        if (p->nst < kMaxStages) p->radix[p->nst++] = r;
+    };
+    const int q = a / 3, rem = a % 3;
+    if (rem == 0) {
+        for (int i = 0; i < q; ++i) push(8);
+    } else if (rem == 1) {
+        if (q >= 1) {
+            for (int i = 0; i < q - 1; ++i) push(8);
+            push(4);
+            push(4);
+        } else {
+            push(2);
+        }
+    } else {
+        for (int i = 0; i < q; ++i) push(8);
+        push(4);
+    }
+    for (int i = 0; i < n3; ++i) push(3);
+    for (int i = 0; i < n5; ++i) push(5);
+    return p->nst < kMaxStages;
+}
+
+}  // namespace mvd
+
+using namespace mvd;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+mvd_status dev_alloc(T** p, size_t count, const char* what) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        set_error("allocating %s (%zu bytes): %s", what, count * sizeof(T), cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MVD_ERR_OOM : MVD_ERR_CUDA;
+    }
+    return MVD_OK;
+}
+
+template <typename T>
+void dev_free(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void free_fft(mvd_ctx* c) {
+    dev_free(c->d_tw);
+    dev_free(c->d_S);
+    dev_free(c->d_K);
+}
+
+void free_all(mvd_ctx* c) {
+    free_fft(c);
+    dev_free(c->d_views);
+    dev_free(c->d_psi);
+    dev_free(c->d_r);
+    dev_free(c->d_psf);
+    dev_free(c->d_comp);
+    dev_free(c->d_ktmp);
+    dev_free(c->d_red);
+    dev_free(c->d_flag);
+}
+
+bool smooth235(int n) {
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Relative cost of the two engines for one view update (seconds, rough):
+// direct = 2T FMAs per voxel on the FP32 pipe; FFT = ~88 bytes per voxel over
+// HBM plus nine launches. Used when the path is AUTO.
+int choose_path(const mvd_ctx* c) {
+    bool direct_ok = true;
+    long tmax = 0;
+    for (int v = 0; v < c->nv; ++v) {
+        direct_ok = direct_ok && direct_supported(&c->kd[3 * v]);
+        tmax = std::max(tmax, (long)c->kd[3 * v] * c->kd[3 * v + 1] * c->kd[3 * v + 2]);
+    }
+    const bool fft_ok = smooth235(c->dims[0]) && smooth235(c->dims[1]) && smooth235(c->dims[2]);
+    if (!fft_ok) return direct_ok ? MVD_PATH_DIRECT : -1;
+    if (!direct_ok) return MVD_PATH_FFT;
+    const double t_direct = 2.0 * tmax * (double)c->M / 40e12 + 2 * 3e-6;
+    const double t_fft = 88.0 * (double)c->M / 5e12 + 9 * 3e-6;
+    return t_direct <= t_fft ? MVD_PATH_DIRECT : MVD_PATH_FFT;
+}
+
+mvd_status setup_fft(mvd_ctx* c) {
+    FftGeom& g = c->geom;
+    g.X = c->dims[0];
+    g.Y = c->dims[1];
+    g.Z = c->dims[2];
+    g.Xh = g.X / 2 + 1;
+    g.YZ = (long)g.Y * g.Z;
+    if (!make_radix_plan(g.X, &g.px) || !make_radix_plan(g.Y, &g.py) || !make_radix_plan(g.Z, &g.pz)) {
+        set_error("FFT engine needs {2,3,5}-smooth dims, got %d x %d x %d", g.X, g.Y, g.Z);
+        return MVD_ERR_UNSUPPORTED;
+    }
+    const int Ls[3] = {g.X, g.Y, g.Z};
+    std::vector<float2> tw((size_t)g.X + g.Y + g.Z);
+    size_t off = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int m = 0; m < Ls[a]; ++m) {
+            const double ang = -2.0 * M_PI * (double)m / (double)Ls[a];
+            tw[off + m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+        off += Ls[a];
+    }
+    MVD_TRY(dev_alloc(&c->d_tw, tw.size(), "twiddle tables"));
+    MVD_CUDA(cudaMemcpyAsync(c->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+    g.px.tw = c->d_tw;
+    g.py.tw = c->d_tw + g.X;
+    g.pz.tw = c->d_tw + g.X + g.Y;
+    const size_t ns = (size_t)g.Xh * g.YZ;
+    MVD_TRY(dev_alloc(&c->d_S, ns, "work spectrum"));
+    MVD_TRY(dev_alloc(&c->d_K, ns * 2 * c->nv, "kernel spectra"));
+    // spectra of P_v (slot 2v) and of P_v^comp (slot 2v+1), scaled by 1/M
+    const float inv_m = (float)(1.0 / (double)c->M);
+    for (int v = 0; v < c->nv; ++v) {
+        for (int which = 0; which < 2; ++which) {
+            const float* k = (which == 0 ? c->d_psf : c->d_comp) + c->koff[v];
+            float2* dst = c->d_K + ns * (2 * v + which);
+            MVD_TRY(place_kernel(c->dims, k, &c->kd[3 * v], c->d_r, c->stream));
+            MVD_TRY(fft_forward_real(g, c->d_r, dst, c->stream));
+            MVD_TRY(fft_y(g, dst, 0, c->stream));
+            MVD_TRY(fft_z_forward_scaled(g, dst, inv_m, c->stream));
+        }
+    }
+    return MVD_OK;
+}
+
+mvd_status one_update(mvd_ctx* c, int v) {
+    const float* phi = c->d_views + (size_t)v * c->M;
+    const int* kd = &c->kd[3 * v];
+    if (c->path == MVD_PATH_DIRECT) {
+        MVD_TRY(direct_ratio(c->dims, c->d_psi, c->d_psf + c->koff[v], kd, phi, c->eps, c->d_r, c->stream));
+        return direct_update(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_psi, c->eps, c->stream);
+    }
+    const FftGeom& g = c->geom;
+    const size_t ns = (size_t)g.Xh * g.YZ;
+    const float2* Kp = c->d_K + ns * (2 * v);
+    const float2* Kc = c->d_K + ns * (2 * v + 1);
+    MVD_TRY(fft_forward_real(g, c->d_psi, c->d_S, c->stream));
+    MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
+    MVD_TRY(fft_z_mul(g, c->d_S, Kp, c->stream));
+    MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
+    MVD_TRY(fft_x_ratio(g, c->d_S, phi, c->eps, c->stream));
+    MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
+    MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
+    MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
+    return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream);
+}
+
+mvd_status read_flag(mvd_ctx* c, int* flag) {
+    MVD_CUDA(cudaMemcpyAsync(flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MVD_CUDA(cudaStreamSynchronize(c->stream));
+    return MVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mvd_default_options(mvd_options* opt) {
+    if (!opt) return;
+    opt->eps = 0.f;
+    opt->path = MVD_PATH_AUTO;
+    opt->stream = nullptr;
+    opt->views_on_device = 0;
+    opt->device = -1;
+}
+
+const char* mvd_last_error(void) { return t_err.c_str(); }
+
+unsigned long long mvd_launch_count(void) { return g_launches.load(); }
+
+void mvd_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(mvd::g_prof_mu);
+    mvd::g_prof.clear();
+    mvd::g_pool_used = 0;
+    mvd::g_prof_on.store(on ? 1 : 0);
+}
+
+int mvd_profile_read(const char** names, unsigned long long* launches, double* ms, int max) {
+    std::lock_guard<std::mutex> lk(mvd::g_prof_mu);
+    double acc[KC_COUNT] = {0};
+    unsigned long long cnt[KC_COUNT] = {0};
+    for (const auto& r : mvd::g_prof) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            acc[r.cls] += t;
+            cnt[r.cls] += 1;
+        }
+    }
+    int n = 0;
+    for (int c = 0; c < KC_COUNT && n < max; ++c, ++n) {
+        if (names) names[n] = mvd::kClassNames[c];
+        if (launches) launches[n] = cnt[c];
+        if (ms) ms[n] = acc[c];
+    }
+    return n;
+}
+
+mvd_status mvd_create(const float* const* views, int n_views, const float* const* psfs, const int* psf_dims,
+                      const int dims[3], const mvd_options* opt_in, mvd_ctx** out) {
+    clear_error();
+    if (!out) {
+        set_error("mvd_create: out is NULL");
+        return MVD_ERR_ARG;
+    }
+    *out = nullptr;
+    mvd_options opt;
+    mvd_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (!views || !psfs || !psf_dims || !dims || n_views < 1) {
+        set_error("mvd_create: NULL pointer or n_views < 1");
+        return MVD_ERR_ARG;
+    }
+    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1) {
+        set_error("mvd_create: dims must be >= 1");
+        return MVD_ERR_SHAPE;
+    }
+    if (opt.path < MVD_PATH_AUTO || opt.path > MVD_PATH_FFT) {
+        set_error("mvd_create: unknown path %d", opt.path);
+        return MVD_ERR_ARG;
+    }
+    if (!(opt.eps >= 0.f) || std::isinf(opt.eps)) {
+        set_error("mvd_create: eps must be finite and >= 0");
+        return MVD_ERR_ARG;
+    }
+    // PSF shapes and values; normalise to sum 1 (Eq. 3)
+    std::vector<float> psf_h;
+    std::vector<long> koff(n_views);
+    long ktotal = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int* k = psf_dims + 3 * v;
+        for (int a = 0; a < 3; ++a) {
+            if (k[a] < 1 || k[a] % 2 == 0) {
+                set_error("mvd_create: PSF %d size %d on axis %d must be odd and >= 1", v, k[a], a);
+                return MVD_ERR_SHAPE;
+            }
+            if (k[a] > dims[a]) {
+                set_error("mvd_create: PSF %d size %d exceeds the volume (%d) on axis %d", v, k[a], dims[a], a);
+                return MVD_ERR_SHAPE;
+            }
+        }
+        if (!views[v] || !psfs[v]) {
+            set_error("mvd_create: view or PSF %d is NULL", v);
+            return MVD_ERR_ARG;
+        }
+        koff[v] = ktotal;
+        const long T = (long)k[0] * k[1] * k[2];
+        double s = 0.0;
+        for (long i = 0; i < T; ++i) {
+            const float x = psfs[v][i];
+            if (!(x >= 0.f) || std::isinf(x)) {
+                set_error("mvd_create: PSF %d has a negative or non-finite value at %ld", v, i);
+                return MVD_ERR_ARG;
+            }
+            s += x;
+        }
+        if (!(s > 0.0)) {
+            set_error("mvd_create: PSF %d sums to zero", v);
+            return MVD_ERR_ARG;
+        }
+        for (long i = 0; i < T; ++i) psf_h.push_back((float)(psfs[v][i] / s));
+        ktotal += T;
+    }
+
+    DeviceGuard dg(opt.device);
+    if (!dg.ok) {
+        set_error("mvd_create: cannot select device %d", opt.device);
+        return MVD_ERR_CUDA;
+    }
+    mvd_ctx* c = new mvd_ctx();
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)opt.stream;
+    c->dims[0] = dims[0];
+    c->dims[1] = dims[1];
+    c->dims[2] = dims[2];
+    c->M = (long)dims[0] * dims[1] * dims[2];
+    c->nv = n_views;
+    c->kd.assign(psf_dims, psf_dims + 3 * n_views);
+    c->koff = koff;
+    c->ktotal = ktotal;
+    c->path_opt = opt.path;
+
+    auto fail = [&](mvd_status st) {
+        cudaStreamSynchronize(c->stream);
+        free_all(c);
+        delete c;
+        return st;
+    };
+    mvd_status st;
+    if ((st = dev_alloc(&c->d_views, (size_t)n_views * c->M, "views")) != MVD_OK) return fail(st);
+    if ((st = dev_alloc(&c->d_psi, (size_t)c->M, "estimate")) != MVD_OK) return fail(st);
+    if ((st = dev_alloc(&c->d_r, (size_t)c->M, "ratio buffer")) != MVD_OK) return fail(st);
+    if ((st = dev_alloc(&c->d_psf, (size_t)ktotal, "PSFs")) != MVD_OK) return fail(st);
+    if ((st = dev_alloc(&c->d_red, 4, "reduction scratch")) != MVD_OK) return fail(st);
+    if ((st = dev_alloc(&c->d_flag, 4, "flag")) != MVD_OK) return fail(st);
+    const cudaMemcpyKind kind = opt.views_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int v = 0; v < n_views; ++v) {
+        cudaError_t e = cudaMemcpyAsync(c->d_views + (size_t)v * c->M, views[v], c->M * sizeof(float), kind, c->stream);
+        if (e != cudaSuccess) return fail(cuda_status(e, "copying a view"));
+    }
+    {
+        cudaError_t e = cudaMemcpyAsync(c->d_psf, psf_h.data(), ktotal * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return fail(cuda_status(e, "copying PSFs"));
+        e = cudaMemsetAsync(c->d_red, 0, 4 * sizeof(double), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->stream);
+        if (e != cudaSuccess) return fail(cuda_status(e, "clearing scratch"));
+    }
+    if ((st = view_stats(c->d_views, (long)n_views * c->M, c->d_red, c->d_flag, c->stream)) != MVD_OK) return fail(st);
+    double sum = 0.0;
+    int bad = 0;
+    {
+        cudaError_t e = cudaMemcpyAsync(&sum, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return fail(cuda_status(e, "reading view statistics"));
+    }
+    if (bad) {
+        set_error("mvd_create: a view holds a negative or non-finite value");
+        return fail(MVD_ERR_ARG);
+    }
+    c->psi0 = (float)(sum / ((double)c->M * n_views));
+    if (!(c->psi0 > 0.f)) {
+        set_error("mvd_create: all views are zero");
+        return fail(MVD_ERR_ARG);
+    }
+    c->eps = opt.eps > 0.f ? opt.eps : (float)(1e-4 * (sum / ((double)c->M * n_views)));
+    if ((st = fill(c->d_psi, c->M, c->psi0, c->stream)) != MVD_OK) return fail(st);
+    c->state = 1;
+    *out = c;
+    return MVD_OK;
+}
+
+mvd_status mvd_precompute_kernels(mvd_ctx* c, int variant) {
+    clear_error();
+    if (!c) {
+        set_error("mvd_precompute_kernels: NULL context");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 1) {
+        set_error("mvd_precompute_kernels: context not created");
+        return MVD_ERR_STATE;
+    }
+    if (variant < MVD_PLAIN || variant > MVD_OPT2) {
+        set_error("mvd_precompute_kernels: unknown variant %d", variant);
+        return MVD_ERR_ARG;
+    }
+    DeviceGuard dg(c->device);
+    free_fft(c);
+    dev_free(c->d_comp);
+    dev_free(c->d_ktmp);
+    c->state = 1;
+    MVD_TRY(dev_alloc(&c->d_comp, (size_t)c->ktotal, "compound kernels"));
+    size_t qmax = 1;
+    for (int v = 0; v < c->nv; ++v) {
+        const int* k = &c->kd[3 * v];
+        qmax = std::max(qmax, (size_t)(2 * k[0] - 1) * (2 * k[1] - 1) * (2 * k[2] - 1));
+    }
+    MVD_TRY(dev_alloc(&c->d_ktmp, qmax, "precompute scratch"));
+    MVD_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+    for (int v = 0; v < c->nv; ++v) {
+        float* dst = c->d_comp + c->koff[v];
+        MVD_TRY(build_compound(c->nv, c->d_psf, c->koff.data(), c->kd.data(), v, variant, dst, c->d_ktmp,
+                               c->d_red, c->stream));
+        const int* k = &c->kd[3 * v];
+        MVD_TRY(normalize_kernel(dst, k[0] * k[1] * k[2], c->d_flag, c->stream));
+    }
+    int bad = 0;
+    MVD_TRY(read_flag(c, &bad));
+    if (bad) {
+        set_error("mvd_precompute_kernels: a compound kernel sums to zero");
+        return MVD_ERR_ARG;
+    }
+    int path = c->path_opt;
+    const bool fft_ok = smooth235(c->dims[0]) && smooth235(c->dims[1]) && smooth235(c->dims[2]);
+    if (path == MVD_PATH_AUTO) {
+        path = choose_path(c);
+        if (path < 0) {
+            set_error("mvd_precompute_kernels: no engine fits (dims not {2,3,5}-smooth and PSF too large)");
+            return MVD_ERR_UNSUPPORTED;
+        }
+    } else if (path == MVD_PATH_DIRECT) {
+        for (int v = 0; v < c->nv; ++v)
+            if (!direct_supported(&c->kd[3 * v])) {
+                set_error("mvd_precompute_kernels: PSF %d too large for the direct engine", v);
+                return MVD_ERR_UNSUPPORTED;
+            }
+    } else if (!fft_ok) {
+        set_error("mvd_precompute_kernels: FFT engine needs {2,3,5}-smooth dims");
+        return MVD_ERR_UNSUPPORTED;
+    }
+    c->path = path;
+    if (path == MVD_PATH_FFT) MVD_TRY(setup_fft(c));
+    c->variant = variant;
+    c->state = 2;
+    return MVD_OK;
+}
+
+mvd_status mvd_set_estimate(mvd_ctx* c, const float* psi, int on_device) {
+    clear_error();
+    if (!c) {
+        set_error("mvd_set_estimate: NULL context");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 1) {
+        set_error("mvd_set_estimate: context not created");
+        return MVD_ERR_STATE;
+    }
+    DeviceGuard dg(c->device);
+    if (!psi) return fill(c->d_psi, c->M, c->psi0, c->stream);
+    MVD_CUDA(cudaMemcpyAsync(c->d_psi, psi, c->M * sizeof(float),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    MVD_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+    MVD_TRY(check_positive(c->d_psi, c->M, c->d_flag, c->stream));
+    int bad = 0;
+    MVD_TRY(read_flag(c, &bad));
+    if (bad) {
+        set_error("mvd_set_estimate: the estimate must be finite and > 0");
+        fill(c->d_psi, c->M, c->psi0, c->stream);
+        return MVD_ERR_ARG;
+    }
+    return MVD_OK;
+}
+
+mvd_status mvd_iterate(mvd_ctx* c, int n_iter, const int* schedule, int schedule_len) {
+    clear_error();
+    if (!c) {
+        set_error("mvd_iterate: NULL context");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 2) {
+        set_error("mvd_iterate: kernels not precomputed");
+        return MVD_ERR_STATE;
+    }
+    if (n_iter < 0 || schedule_len < 0 || (schedule_len > 0 && !schedule)) {
+        set_error("mvd_iterate: bad iteration count or schedule");
+        return MVD_ERR_ARG;
+    }
+    const int L = schedule_len > 0 ? schedule_len : c->nv;
+    for (int s = 0; s < L; ++s) {
+        const int v = schedule_len > 0 ? schedule[s] : s;
+        if (v < 0 || v >= c->nv) {
+            set_error("mvd_iterate: schedule entry %d = %d out of range", s, v);
+            return MVD_ERR_ARG;
+        }
+    }
+    DeviceGuard dg(c->device);
+    for (int it = 0; it < n_iter; ++it)
+        for (int s = 0; s < L; ++s) MVD_TRY(one_update(c, schedule_len > 0 ? schedule[s] : s));
+    return MVD_OK;
+}
+
+mvd_status mvd_result(mvd_ctx* c, float* out, size_t n_elems) {
+    clear_error();
+    if (!c || !out) {
+        set_error("mvd_result: NULL argument");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 1) {
+        set_error("mvd_result: context not created");
+        return MVD_ERR_STATE;
+    }
+    if (n_elems < (size_t)c->M) {
+        set_error("mvd_result: buffer holds %zu elements, need %ld", n_elems, c->M);
+        return MVD_ERR_SHAPE;
+    }
+    DeviceGuard dg(c->device);
+    MVD_CUDA(cudaMemcpyAsync(out, c->d_psi, c->M * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    MVD_CUDA(cudaStreamSynchronize(c->stream));
+    return MVD_OK;
+}
+
+mvd_status mvd_result_device(mvd_ctx* c, const float** dptr) {
+    clear_error();
+    if (!c || !dptr) {
+        set_error("mvd_result_device: NULL argument");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 1) {
+        set_error("mvd_result_device: context not created");
+        return MVD_ERR_STATE;
+    }
+    *dptr = c->d_psi;
+    return MVD_OK;
+}
+
+mvd_status mvd_synchronize(mvd_ctx* c) {
+    clear_error();
+    if (!c) {
+        set_error("mvd_synchronize: NULL context");
+        return MVD_ERR_ARG;
+    }
+    DeviceGuard dg(c->device);
+    MVD_CUDA(cudaStreamSynchronize(c->stream));
+    return MVD_OK;
+}
+
+void mvd_destroy(mvd_ctx* c) {
+    if (!c) return;
+    DeviceGuard dg(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+float mvd_get_eps(const mvd_ctx* c) { return c ? c->eps : 0.f; }
+float mvd_get_psi0(const mvd_ctx* c) { return c ? c->psi0 : 0.f; }
+int mvd_get_path(const mvd_ctx* c) { return c ? c->path : -1; }
+
+mvd_status mvd_get_compound_kernel(mvd_ctx* c, int v, float* out, size_t n_elems) {
+    clear_error();
+    if (!c || !out) {
+        set_error("mvd_get_compound_kernel: NULL argument");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 2) {
+        set_error("mvd_get_compound_kernel: kernels not precomputed");
+        return MVD_ERR_STATE;
+    }
+    if (v < 0 || v >= c->nv) {
+        set_error("mvd_get_compound_kernel: view %d out of range", v);
+        return MVD_ERR_ARG;
+    }
+    const int* k = &c->kd[3 * v];
+    const size_t T = (size_t)k[0] * k[1] * k[2];
+    if (n_elems < T) {
+        set_error("mvd_get_compound_kernel: buffer too small");
+        return MVD_ERR_SHAPE;
+    }
+    DeviceGuard dg(c->device);
+    MVD_CUDA(cudaMemcpyAsync(out, c->d_comp + c->koff[v], T * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    MVD_CUDA(cudaStreamSynchronize(c->stream));
+    return MVD_OK;
+}
+
+}  // extern "C"

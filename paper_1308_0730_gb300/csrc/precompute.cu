@@ -1,0 +1,222 @@
+// Device-side set-up work: compound kernels (Eq. 222 / Eq. 230 / Eq. 240),
+// kernel placement on the periodic grid, view statistics (psi0 and input
+// validation) and small helpers.
+//
+// Kernels are functions on Z^3 supported on a centred odd box; kernel algebra
+// (P_v^* * P_w * P_w^*) is linear convolution of those small functions. The
+// compound kernel of view v is zero outside P_v^*'s box, so every factor is
+// evaluated on that box only.
+#include "common.cuh"
+
+namespace mvd {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Box {
+    int kx, ky, kz;  // sizes
+    __device__ __forceinline__ int hx() const { return (kx - 1) / 2; }
+    __device__ __forceinline__ int hy() const { return (ky - 1) / 2; }
+    __device__ __forceinline__ int hz() const { return (kz - 1) / 2; }
+    __device__ __forceinline__ int size() const { return kx * ky * kz; }
+    // value at offset (dx,dy,dz) from the centre
+    __device__ __forceinline__ float at(const float* k, int dx, int dy, int dz) const {
+        return __ldg(k + (dx + hx()) + kx * ((dy + hy()) + ky * (dz + hz())));
+    }
+};
+
+__device__ __forceinline__ void offset_of(const Box& b, int i, int& dx, int& dy, int& dz) {
+    dx = i % b.kx - b.hx();
+    const int r = i / b.kx;
+    dy = r % b.ky - b.hy();
+    dz = r / b.ky - b.hz();
+}
+
+// Q(d) = sum_e P(e) P(e - d)   (P * P^*), on the box of size 2K-1
+__global__ void k_autocorr(const float* P, Box b, float* Q, Box q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= q.size()) return;
+    int dx, dy, dz;
+    offset_of(q, i, dx, dy, dz);
+    float s = 0.f;
+    // e and e - d both inside b
+    const int zlo = max(-b.hz(), dz - b.hz()), zhi = min(b.hz(), dz + b.hz());
+    const int ylo = max(-b.hy(), dy - b.hy()), yhi = min(b.hy(), dy + b.hy());
+    const int xlo = max(-b.hx(), dx - b.hx()), xhi = min(b.hx(), dx + b.hx());
+    for (int ez = zlo; ez <= zhi; ++ez)
+        for (int ey = ylo; ey <= yhi; ++ey)
+            for (int ex = xlo; ex <= xhi; ++ex) s = fmaf(b.at(P, ex, ey, ez), b.at(P, ex - dx, ey - dy, ez - dz), s);
+    Q[i] = s;
+}
+
+// out(d) = P^*(d) = P(-d)
+__global__ void k_mirror(const float* P, Box b, float* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.size()) return;
+    int dx, dy, dz;
+    offset_of(b, i, dx, dy, dz);
+    out[i] = b.at(P, -dx, -dy, -dz);
+}
+
+// out(d) *= sum_e P^*(e) G(d - e)  for d on P's box  (P^*(e) = P(-e))
+__global__ void k_mul_conv(const float* P, Box b, const float* G, Box g, float* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.size()) return;
+    int dx, dy, dz;
+    offset_of(b, i, dx, dy, dz);
+    const int zlo = max(-b.hz(), dz - g.hz()), zhi = min(b.hz(), dz + g.hz());
+    const int ylo = max(-b.hy(), dy - g.hy()), yhi = min(b.hy(), dy + g.hy());
+    const int xlo = max(-b.hx(), dx - g.hx()), xhi = min(b.hx(), dx + g.hx());
+    float s = 0.f;
+    for (int ez = zlo; ez <= zhi; ++ez)
+        for (int ey = ylo; ey <= yhi; ++ey)
+            for (int ex = xlo; ex <= xhi; ++ex) s = fmaf(b.at(P, -ex, -ey, -ez), g.at(G, dx - ex, dy - ey, dz - ez), s);
+    out[i] *= s;
+}
+
+// out(d) *= P^*(d)
+__global__ void k_mul_mirror(const float* P, Box b, float* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.size()) return;
+    int dx, dy, dz;
+    offset_of(b, i, dx, dy, dz);
+    out[i] *= b.at(P, -dx, -dy, -dz);
+}
+
+// one block: out /= sum(out) (sum in FP64); flag if the sum is not > 0
+__global__ void k_normalize(float* out, int n, int* bad) {
+    __shared__ double part[1024];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += out[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double tot = part[0];
+    if (!(tot > 0.0)) {
+        if (threadIdx.x == 0) *bad = 1;
+        return;
+    }
+    const float inv = (float)(1.0 / tot);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] *= inv;
+}
+
+__global__ void k_place(const float* k, Box b, int X, int Y, int Z, float* vol) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.size()) return;
+    int dx, dy, dz;
+    offset_of(b, i, dx, dy, dz);
+    const int x = (dx % X + X) % X, y = (dy % Y + Y) % Y, z = (dz % Z + Z) % Z;
+    vol[(long)x + (long)X * (y + (long)Y * z)] = __ldg(k + i);
+}
+
+// sum of all values (FP64) and a flag for negative or non-finite values
+__global__ void k_stats(const float* v, long n, double* sum, int* bad) {
+    __shared__ double part[kThreads];
+    double s = 0.0;
+    int b = 0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float x = v[i];
+        if (!(x >= 0.f) || isinf(x)) b = 1;
+        s += x;
+    }
+    part[threadIdx.x] = s;
+    if (b) atomicOr(bad, 1);
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(sum, part[0]);
+}
+
+__global__ void k_check_positive(const float* v, long n, int* bad) {
+    int b = 0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float x = v[i];
+        if (!(x > 0.f) || isinf(x)) b = 1;
+    }
+    if (b) atomicOr(bad, 1);
+}
+
+__global__ void k_fill(float* p, long n, float v) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = v;
+}
+
+inline Box box_of(const int* kd) { return Box{kd[0], kd[1], kd[2]}; }
+inline int blocks_for(long n) { return (int)((n + kThreads - 1) / kThreads); }
+inline int grid_stride_blocks(long n) {
+    long b = (n + kThreads - 1) / kThreads;
+    return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
+}
+
+}  // namespace
+
+mvd_status build_compound(int n_views, const float* d_psf, const long* koff, const int* kd, int v,
+                          int variant, float* d_out, float* d_tmp, double* /*d_red*/,
+                          cudaStream_t st) {
+    const Box bv = box_of(kd + 3 * v);
+    const float* Pv = d_psf + koff[v];
+    k_mirror<<<blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, d_out);
+    count_launch();
+    MVD_TRY(check_launch("compound mirror"));
+    if (variant != MVD_PLAIN) {
+        for (int w = 0; w < n_views; ++w) {
+            if (w == v) continue;
+            const Box bw = box_of(kd + 3 * w);
+            const float* Pw = d_psf + koff[w];
+            if (variant == MVD_EFFICIENT) {
+                const Box bq{2 * bw.kx - 1, 2 * bw.ky - 1, 2 * bw.kz - 1};
+                k_autocorr<<<blocks_for((long)bq.kx * bq.ky * bq.kz), kThreads, 0, st>>>(Pw, bw, d_tmp, bq);
+                count_launch();
+                MVD_TRY(check_launch("compound autocorrelation"));
+                k_mul_conv<<<blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, d_tmp, bq, d_out);
+            } else if (variant == MVD_OPT1) {
+                k_mul_conv<<<blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, Pw, bw, d_out);
+            } else {
+                k_mul_mirror<<<blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, d_out);
+            }
+            count_launch();
+            MVD_TRY(check_launch("compound product"));
+        }
+    }
+    return MVD_OK;
+}
+
+mvd_status normalize_kernel(float* d_k, int n, int* d_bad, cudaStream_t st) {
+    k_normalize<<<1, 1024, 0, st>>>(d_k, n, d_bad);
+    count_launch();
+    return check_launch("normalise kernel");
+}
+
+mvd_status place_kernel(const int dims[3], const float* k, const int kd[3], float* vol, cudaStream_t st) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    MVD_CUDA(cudaMemsetAsync(vol, 0, M * sizeof(float), st));
+    const Box b = box_of(kd);
+    k_place<<<blocks_for(b.kx * b.ky * b.kz), kThreads, 0, st>>>(k, b, dims[0], dims[1], dims[2], vol);
+    count_launch();
+    return check_launch("place kernel");
+}
+
+mvd_status view_stats(const float* views, long n, double* d_sum, int* d_bad, cudaStream_t st) {
+    k_stats<<<grid_stride_blocks(n), kThreads, 0, st>>>(views, n, d_sum, d_bad);
+    count_launch();
+    return check_launch("view statistics");
+}
+
+mvd_status check_positive(const float* p, long n, int* d_bad, cudaStream_t st) {
+    k_check_positive<<<grid_stride_blocks(n), kThreads, 0, st>>>(p, n, d_bad);
+    count_launch();
+    return check_launch("check estimate");
+}
+
+mvd_status fill(float* p, long n, float v, cudaStream_t st) {
+    k_fill<<<grid_stride_blocks(n), kThreads, 0, st>>>(p, n, v);
+    count_launch();
+    return check_launch("fill");
+}
+
+}  // namespace mvd

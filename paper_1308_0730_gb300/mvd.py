@@ -1,0 +1,287 @@
+"""Thin Python binding of libmvd.so (the C ABI in include/mvd.h).
+
+Argument marshalling only: every step of the deconvolution runs in the
+library's CUDA kernels. Host inputs are numpy float32 arrays; device inputs
+are CUDA tensors (anything with ``data_ptr()``), passed as raw pointers.
+There is no CPU fallback: if the library is missing, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmvd.so")
+
+MVD_OK, MVD_ERR_ARG, MVD_ERR_SHAPE, MVD_ERR_STATE, MVD_ERR_OOM, MVD_ERR_CUDA, MVD_ERR_TIMEOUT, \
+    MVD_ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = ["MVD_OK", "MVD_ERR_ARG", "MVD_ERR_SHAPE", "MVD_ERR_STATE", "MVD_ERR_OOM", "MVD_ERR_CUDA",
+                "MVD_ERR_TIMEOUT", "MVD_ERR_UNSUPPORTED"]
+MVD_PLAIN, MVD_EFFICIENT, MVD_OPT1, MVD_OPT2 = range(4)
+VARIANTS = {"plain": MVD_PLAIN, "efficient": MVD_EFFICIENT, "opt1": MVD_OPT1, "opt2": MVD_OPT2}
+MVD_PATH_AUTO, MVD_PATH_DIRECT, MVD_PATH_FFT = range(3)
+PATHS = {"auto": MVD_PATH_AUTO, "direct": MVD_PATH_DIRECT, "fft": MVD_PATH_FFT}
+
+# every symbol include/mvd.h declares
+EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_set_estimate", "mvd_iterate",
+           "mvd_result", "mvd_result_device", "mvd_synchronize", "mvd_destroy", "mvd_last_error",
+           "mvd_get_eps", "mvd_get_psi0", "mvd_get_path", "mvd_get_compound_kernel", "mvd_launch_count",
+           "mvd_profile_enable", "mvd_profile_read"]
+
+
+class MvdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("path", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("views_on_device", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+_lib = None
+_FP = ctypes.POINTER(ctypes.c_float)
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libmvd.so (built by ``paper_1308_0730_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, ci, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    lib.mvd_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.mvd_default_options.restype = None
+    lib.mvd_create.argtypes = [ctypes.POINTER(vp), ci, ctypes.POINTER(vp), ctypes.POINTER(ci),
+                               ctypes.POINTER(ci), ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    lib.mvd_precompute_kernels.argtypes = [vp, ci]
+    lib.mvd_set_estimate.argtypes = [vp, vp, ci]
+    lib.mvd_iterate.argtypes = [vp, ci, ctypes.POINTER(ci), ci]
+    lib.mvd_result.argtypes = [vp, _FP, sz]
+    lib.mvd_result_device.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.mvd_synchronize.argtypes = [vp]
+    lib.mvd_destroy.argtypes = [vp]
+    lib.mvd_destroy.restype = None
+    lib.mvd_last_error.restype = ctypes.c_char_p
+    lib.mvd_get_eps.argtypes = [vp]
+    lib.mvd_get_eps.restype = ctypes.c_float
+    lib.mvd_get_psi0.argtypes = [vp]
+    lib.mvd_get_psi0.restype = ctypes.c_float
+    lib.mvd_get_path.argtypes = [vp]
+    lib.mvd_get_path.restype = ci
+    lib.mvd_get_compound_kernel.argtypes = [vp, ci, _FP, sz]
+    lib.mvd_launch_count.restype = ctypes.c_ulonglong
+    lib.mvd_profile_enable.argtypes = [ci]
+    lib.mvd_profile_enable.restype = None
+    lib.mvd_profile_read.argtypes = [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_ulonglong),
+                                     ctypes.POINTER(ctypes.c_double), ci]
+    lib.mvd_profile_read.restype = ci
+    for name in ("mvd_create", "mvd_precompute_kernels", "mvd_set_estimate", "mvd_iterate", "mvd_result",
+                 "mvd_result_device", "mvd_synchronize", "mvd_get_compound_kernel"):
+        getattr(lib, name).restype = ci
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != MVD_OK:
+        raise MvdError(status, (_lib.mvd_last_error() or b"").decode())
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)
+
+
+def _host_f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def mvd_last_error() -> str:
+    return (load().mvd_last_error() or b"").decode()
+
+
+def mvd_launch_count() -> int:
+    return int(load().mvd_launch_count())
+
+
+def mvd_profile_enable(on: bool = True):
+    load().mvd_profile_enable(1 if on else 0)
+
+
+def mvd_profile_read() -> dict:
+    """{class name: (timed launches, total ms)} of the launches recorded since enabling."""
+    n = 16
+    names = (ctypes.c_char_p * n)()
+    cnt = (ctypes.c_ulonglong * n)()
+    ms = (ctypes.c_double * n)()
+    k = load().mvd_profile_read(names, cnt, ms, n)
+    return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(k)}
+
+
+def mvd_create(views, psfs, dims=None, eps: float = 0.0, path="auto", stream=None, device: int = -1):
+    """Creates a context (see mvd_create in include/mvd.h); returns its handle.
+
+    ``views``: list of float32 arrays ``[Z][Y][X]`` (numpy on the host, or CUDA
+    tensors on the device, contiguous). ``psfs``: list of float32 host arrays
+    ``[Kz][Ky][Kx]``. ``stream``: a ``torch.cuda.Stream`` or a raw handle.
+    """
+    lib = load()
+    on_dev = _is_device(views[0])
+    keep = []
+    if on_dev:
+        ptrs = [ctypes.c_void_p(int(v.data_ptr())) for v in views]
+        shape = tuple(views[0].shape)
+    else:
+        hv = [_host_f32(v) for v in views]
+        keep += hv
+        ptrs = [ctypes.c_void_p(v.ctypes.data) for v in hv]
+        shape = hv[0].shape
+    if dims is None:
+        dims = (shape[2], shape[1], shape[0])
+    hp = [_host_f32(p) for p in psfs]
+    keep += hp
+    pd = [d for p in hp for d in (p.shape[2], p.shape[1], p.shape[0])]
+    opt = Options()
+    lib.mvd_default_options(ctypes.byref(opt))
+    opt.eps = float(eps)
+    opt.path = PATHS[path] if isinstance(path, str) else int(path)
+    if stream is not None:
+        opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    opt.views_on_device = 1 if on_dev else 0
+    opt.device = int(device)
+    h = ctypes.c_void_p()
+    _check(lib.mvd_create((ctypes.c_void_p * len(ptrs))(*ptrs), len(ptrs),
+                          (ctypes.c_void_p * len(hp))(*[ctypes.c_void_p(p.ctypes.data) for p in hp]),
+                          (ctypes.c_int * len(pd))(*pd), (ctypes.c_int * 3)(*[int(d) for d in dims]),
+                          ctypes.byref(opt), ctypes.byref(h)))
+    return h
+
+
+def mvd_precompute_kernels(ctx, variant="efficient"):
+    _check(load().mvd_precompute_kernels(ctx, VARIANTS[variant] if isinstance(variant, str) else int(variant)))
+
+
+def mvd_set_estimate(ctx, psi=None):
+    lib = load()
+    if psi is None:
+        _check(lib.mvd_set_estimate(ctx, None, 0))
+    elif _is_device(psi):
+        _check(lib.mvd_set_estimate(ctx, ctypes.c_void_p(int(psi.data_ptr())), 1))
+    else:
+        h = _host_f32(psi)
+        _check(lib.mvd_set_estimate(ctx, ctypes.c_void_p(h.ctypes.data), 0))
+
+
+def mvd_iterate(ctx, n_iter: int, schedule=None):
+    lib = load()
+    if schedule is None or len(schedule) == 0:
+        _check(lib.mvd_iterate(ctx, int(n_iter), None, 0))
+    else:
+        s = (ctypes.c_int * len(schedule))(*[int(v) for v in schedule])
+        _check(lib.mvd_iterate(ctx, int(n_iter), s, len(schedule)))
+
+
+def mvd_result(ctx, out: np.ndarray):
+    """Copies psi into the float32 host array ``out`` (synchronises)."""
+    assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
+    _check(load().mvd_result(ctx, out.ctypes.data_as(_FP), out.size))
+    return out
+
+
+def mvd_result_device(ctx) -> int:
+    p = ctypes.c_void_p()
+    _check(load().mvd_result_device(ctx, ctypes.byref(p)))
+    return int(p.value or 0)
+
+
+def mvd_synchronize(ctx):
+    _check(load().mvd_synchronize(ctx))
+
+
+def mvd_destroy(ctx):
+    if ctx:
+        load().mvd_destroy(ctx)
+
+
+def mvd_get_eps(ctx) -> float:
+    return float(load().mvd_get_eps(ctx))
+
+
+def mvd_get_psi0(ctx) -> float:
+    return float(load().mvd_get_psi0(ctx))
+
+
+def mvd_get_path(ctx) -> int:
+    return int(load().mvd_get_path(ctx))
+
+
+def mvd_get_compound_kernel(ctx, v: int, shape_zyx) -> np.ndarray:
+    out = np.empty(shape_zyx, dtype=np.float32)
+    _check(load().mvd_get_compound_kernel(ctx, int(v), out.ctypes.data_as(_FP), out.size))
+    return out
+
+
+class Deconvolver:
+    """Owns one context: ``with Deconvolver(views, psfs) as d: d.iterate(10); psi = d.result()``."""
+
+    def __init__(self, views, psfs, variant="efficient", eps=0.0, path="auto", stream=None, device=-1):
+        self.shape = tuple(views[0].shape)
+        self.psf_shapes = [tuple(p.shape) for p in psfs]
+        self.ctx = mvd_create(views, psfs, eps=eps, path=path, stream=stream, device=device)
+        try:
+            mvd_precompute_kernels(self.ctx, variant)
+        except Exception:
+            self.close()
+            raise
+
+    def iterate(self, n_iter, schedule=None):
+        mvd_iterate(self.ctx, n_iter, schedule)
+
+    def set_estimate(self, psi=None):
+        mvd_set_estimate(self.ctx, psi)
+
+    def result(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float32)
+        return mvd_result(self.ctx, out)
+
+    def compound_kernel(self, v):
+        return mvd_get_compound_kernel(self.ctx, v, self.psf_shapes[v])
+
+    @property
+    def eps(self):
+        return mvd_get_eps(self.ctx)
+
+    @property
+    def psi0(self):
+        return mvd_get_psi0(self.ctx)
+
+    @property
+    def path(self):
+        return {MVD_PATH_DIRECT: "direct", MVD_PATH_FFT: "fft"}.get(mvd_get_path(self.ctx), "none")
+
+    def synchronize(self):
+        mvd_synchronize(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mvd_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,107 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and rejects invalid arguments during host-side validation
+(before any device work)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from paper_1308_0730_gb300 import mvd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return mvd.load()
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mvd_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared_symbols()
+    assert "mvd_create" in declared and "mvd_iterate" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) <= set(mvd.EXPORTS) | set(declared)
+    for name in mvd.EXPORTS:
+        assert name in declared, f"binding lists {name} but the header does not declare it"
+
+
+def test_default_options(lib):
+    o = mvd.Options()
+    lib.mvd_default_options(ctypes.byref(o))
+    assert o.eps == 0.0 and o.path == 0 and o.stream is None and o.views_on_device == 0 and o.device == -1
+
+
+def _good():
+    views = [np.ones((8, 8, 8), np.float32)] * 2
+    psfs = [np.ones((3, 3, 3), np.float32)] * 2
+    return views, psfs
+
+
+@pytest.mark.parametrize("case,status", [
+    ("even_psf", mvd.MVD_ERR_SHAPE),
+    ("psf_too_big", mvd.MVD_ERR_SHAPE),
+    ("negative_psf", mvd.MVD_ERR_ARG),
+    ("zero_psf", mvd.MVD_ERR_ARG),
+    ("nan_psf", mvd.MVD_ERR_ARG),
+    ("no_views", mvd.MVD_ERR_ARG),
+    ("bad_path", mvd.MVD_ERR_ARG),
+    ("bad_eps", mvd.MVD_ERR_ARG),
+])
+def test_create_rejects_invalid_arguments(lib, case, status):
+    views, psfs = _good()
+    kw = {}
+    if case == "even_psf":
+        psfs = [np.ones((3, 4, 3), np.float32)] * 2
+    elif case == "psf_too_big":
+        psfs = [np.ones((9, 3, 3), np.float32)] * 2
+    elif case == "negative_psf":
+        p = np.ones((3, 3, 3), np.float32)
+        p[1, 1, 1] = -1
+        psfs = [p, p]
+    elif case == "zero_psf":
+        psfs = [np.zeros((3, 3, 3), np.float32)] * 2
+    elif case == "nan_psf":
+        p = np.ones((3, 3, 3), np.float32)
+        p[0, 0, 0] = np.nan
+        psfs = [p, p]
+    elif case == "no_views":
+        views, psfs = [], []
+    elif case == "bad_path":
+        kw["path"] = 7
+    elif case == "bad_eps":
+        kw["eps"] = float("nan")
+    if case == "no_views":
+        h = ctypes.c_void_p()
+        opt = mvd.Options()
+        lib.mvd_default_options(ctypes.byref(opt))
+        st = lib.mvd_create(None, 0, None, None, (ctypes.c_int * 3)(8, 8, 8), ctypes.byref(opt), ctypes.byref(h))
+        assert st == status and not h.value
+        return
+    with pytest.raises(mvd.MvdError) as ei:
+        mvd.mvd_create(views, psfs, **kw)
+    assert ei.value.status == status
+    assert mvd.mvd_last_error()
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.mvd_iterate(None, 1, None, 0) == mvd.MVD_ERR_ARG
+    assert lib.mvd_precompute_kernels(None, 1) == mvd.MVD_ERR_ARG
+    assert lib.mvd_synchronize(None) == mvd.MVD_ERR_ARG
+    lib.mvd_destroy(None)
+    assert lib.mvd_get_path(None) == -1
+    assert isinstance(mvd.mvd_launch_count(), int)

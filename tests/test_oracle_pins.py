@@ -247,7 +247,7 @@ def test_noise_free_truth_is_fixed_point(variant):
     """phi_v = psi* * P_v exactly => ratio 1 => back-projection of ones is 1 => psi* fixed."""
     w = synth.small_case(11, dims=(12, 10, 14), n_views=3, asymmetric=True)
     truth = w.truth.astype(np.float64)
-    psfs = [p.astype(np.float64) for p in w.psfs]
+    psfs = [p.astype(np.float64) / p.astype(np.float64).sum() for p in w.psfs]
     views = [_fft_blur(truth, p) for p in psfs]
     psi, eps = oracle.deconvolve(views, psfs, 2, variant, psi_init=truth, eps=1e-9)
     assert np.max(np.abs(psi - truth) / truth) < 1e-11
@@ -335,3 +335,11 @@ def test_deconvolution_improves_correlation_with_truth():
     r_in = np.corrcoef(w.views[0].ravel(), w.truth.ravel())[0, 1]
     r_out = np.corrcoef(psi.ravel(), w.truth.ravel())[0, 1]
     assert r_out > r_in + 0.05
+
+
+def test_psf_scale_is_irrelevant():
+    """PSFs are probability distributions (Eq. 3): scaling a PSF must not change the result."""
+    w = synth.small_case(19, dims=(10, 9, 8), n_views=2, asymmetric=True)
+    a, _ = oracle.deconvolve(w.views, w.psfs, 2, "efficient")
+    b, _ = oracle.deconvolve(w.views, [w.psfs[0] * 4.0, w.psfs[1] * 0.25], 2, "efficient")  # exact scales
+    assert np.allclose(a, b, rtol=1e-12)
