@@ -165,6 +165,32 @@ unsigned long long mvd_launch_count(void);
 void mvd_profile_enable(int on);
 int mvd_profile_read(const char** names, unsigned long long* launches, double* ms, int max);
 
+/*
+ * Allocation-free view update. The paper has no counterpart: this entry point
+ * serves callers that cannot call cudaMalloc, such as applications whose
+ * device memory belongs to a caching allocator that must see every
+ * allocation (a raw cudaMalloc or cudaFree also synchronises the device), or
+ * acquisition loops that allocate at start-up only. It runs one view update
+ * with the direct engine and allocates nothing:
+ *   psi = max(psi . ((phi / max(psi * psf, eps)) * comp), eps)
+ * All pointers are device pointers the caller owns: psi (X*Y*Z floats,
+ * updated in place), phi (X*Y*Z floats), psf and comp (Kx*Ky*Kz floats each,
+ * PSF layout; used as given, so pass a normalised PSF and its compound
+ * kernel, e.g. from mvd_get_compound_kernel). dims = {X,Y,Z}, kdims =
+ * {Kx,Ky,Kz} (odd, <= dims), eps > 0, stream = cudaStream_t or NULL.
+ * Limit: X*Y*Z <= 2^21 voxels (8 MiB of ratio scratch); larger volumes
+ * return MVD_ERR_SHAPE, PSF boxes the direct engine cannot stage return
+ * MVD_ERR_UNSUPPORTED.
+ * The ratio scratch is one file-scope device array per GPU, held until the
+ * process exits and shared by every call: calls whose work overlaps on the
+ * GPU (other streams, other host threads) race on it. Order them on one
+ * stream. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. Enqueues work only.
+ */
+mvd_status mvd_update_direct_noalloc(float* psi, const float* phi, const float* psf, const float* comp,
+                                     const int dims[3], const int kdims[3], float eps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

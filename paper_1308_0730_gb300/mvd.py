@@ -28,7 +28,7 @@ PATHS = {"auto": MVD_PATH_AUTO, "direct": MVD_PATH_DIRECT, "fft": MVD_PATH_FFT}
 EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_set_estimate", "mvd_iterate",
            "mvd_result", "mvd_result_device", "mvd_synchronize", "mvd_destroy", "mvd_last_error",
            "mvd_get_eps", "mvd_get_psi0", "mvd_get_path", "mvd_get_compound_kernel", "mvd_launch_count",
-           "mvd_profile_enable", "mvd_profile_read"]
+           "mvd_profile_enable", "mvd_profile_read", "mvd_update_direct_noalloc"]
 
 
 class MvdError(RuntimeError):
@@ -82,6 +82,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_profile_read.argtypes = [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_ulonglong),
                                      ctypes.POINTER(ctypes.c_double), ci]
     lib.mvd_profile_read.restype = ci
+    lib.mvd_update_direct_noalloc.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ci), ctypes.POINTER(ci),
+                                              ctypes.c_float, vp]
+    lib.mvd_update_direct_noalloc.restype = ci
     for name in ("mvd_create", "mvd_precompute_kernels", "mvd_set_estimate", "mvd_iterate", "mvd_result",
                  "mvd_result_device", "mvd_synchronize", "mvd_get_compound_kernel"):
         getattr(lib, name).restype = ci
@@ -225,6 +228,20 @@ def mvd_get_compound_kernel(ctx, v: int, shape_zyx) -> np.ndarray:
     out = np.empty(shape_zyx, dtype=np.float32)
     _check(load().mvd_get_compound_kernel(ctx, int(v), out.ctypes.data_as(_FP), out.size))
     return out
+
+
+def mvd_update_direct_noalloc(psi, phi, psf, comp, eps: float, stream=None):
+    """One view update without any device allocation (see include/mvd.h).
+
+    ``psi`` (updated in place), ``phi``, ``psf`` and ``comp`` are contiguous
+    float32 CUDA tensors; ``psi``/``phi`` shaped ``[Z][Y][X]``, ``psf``/``comp``
+    shaped ``[Kz][Ky][Kx]``.
+    """
+    dims = (ctypes.c_int * 3)(int(psi.shape[2]), int(psi.shape[1]), int(psi.shape[0]))
+    kd = (ctypes.c_int * 3)(int(psf.shape[2]), int(psf.shape[1]), int(psf.shape[0]))
+    st = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    ptr = lambda t: ctypes.c_void_p(int(t.data_ptr()))  # noqa: E731
+    _check(load().mvd_update_direct_noalloc(ptr(psi), ptr(phi), ptr(psf), ptr(comp), dims, kd, float(eps), st))
 
 
 class Deconvolver:
