@@ -211,7 +211,6 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = mvd.mvd_launch_count()
-    mvd.mvd_profile_enable(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -222,9 +221,20 @@ def run_gpu(args):
         ev1.synchronize()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    launches = mvd.mvd_launch_count() - launches0
+    # per-kernel durations: the same K steps again with CUDA events around
+    # every launch on the launching stream (kernels launched one by one)
+    mvd.mvd_profile_enable(True)
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev3.record(stream)
+    ev3.synchronize()
     prof = mvd.mvd_profile_read()
     mvd.mvd_profile_enable(False)
-    launches = mvd.mvd_launch_count() - launches0
+    ms_profiled = ev2.elapsed_time(ev3)
     t_max = ms
     if dist is not None:
         t = torch.tensor([ms], device=f"cuda:{local}")
@@ -296,6 +306,7 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind},
             "update_effective_hbm_frac": (12.0 * units_per_step * args.steps / (ms * 1e-3) / 1e9) / peak,
             "kernels": per_kernel,
+            "profiled_ms_per_step": ms_profiled / args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"one view update (view 0) of the {X}x{Y}x{Z} workload, FP64 direct "

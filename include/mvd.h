@@ -119,7 +119,11 @@ mvd_status mvd_set_estimate(mvd_ctx* ctx, const float* psi, int on_device);
  * Runs n_iter iterations of the sequential update. One iteration applies the
  * update of every view in `schedule` once, in order (schedule_len entries in
  * [0, n_views)); schedule == NULL or schedule_len == 0 means 0..n_views-1.
- * Enqueues work only.
+ * Enqueues work only. On a non-NULL stream, one iteration of a given
+ * schedule is captured once as a CUDA graph (kept by the context until the
+ * next mvd_precompute_kernels or mvd_destroy) and replayed per iteration;
+ * while per-kernel timing is enabled, or with MVD_NO_GRAPH=1 in the
+ * environment, kernels are launched one by one instead.
  */
 mvd_status mvd_iterate(mvd_ctx* ctx, int n_iter, const int* schedule, int schedule_len);
 

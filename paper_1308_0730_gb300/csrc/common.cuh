@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -77,6 +78,7 @@ struct FftGeom {
     int X, Y, Z, Xh;
     long YZ;
     FftPlan px, py, pz;
+    bool fast;  // use the register-resident kernels where the length allows
 };
 
 // Spectrum layout: S[kx][z][y] (y fastest), kx in [0, Xh), Xh = X/2 + 1.
@@ -87,6 +89,17 @@ mvd_status fft_z_forward_scaled(const FftGeom& g, float2* S, float scale, cudaSt
 mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
 mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st);
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
+
+// register-resident variants for power-of-two lengths (fft_fast.cu)
+bool fft_fast_supported(int L);
+bool fft_fast_z_supported(int L);
+mvd_status fft_forward_real_fast(const FftGeom& g, const float* src, float2* S, cudaStream_t st);
+mvd_status fft_y_fast(const FftGeom& g, float2* S, int inverse, cudaStream_t st);
+mvd_status fft_z_mul_fast(const FftGeom& g, float2* S, const float2* K, cudaStream_t st);
+mvd_status fft_z_forward_scaled_fast(const FftGeom& g, float2* S, float scale, cudaStream_t st);
+mvd_status fft_x_ratio_fast(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
+mvd_status fft_x_update_fast(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st);
+mvd_status fft_inverse_real_fast(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
 
 // Direct (spatial) periodic convolution with fused epilogues.
 bool direct_supported(const int kd[3]);
@@ -137,6 +150,13 @@ struct mvd_ctx {
     float2* d_tw = nullptr;  // twiddle tables (x, y, z)
     float2* d_S = nullptr;   // work spectrum Xh*Y*Z
     float2* d_K = nullptr;   // 2*nv kernel spectra (P_v, then P_v^comp), each Xh*Y*Z
+
+    // one instantiated graph per schedule (one iteration each)
+    struct Graph {
+        cudaGraphExec_t exec;
+        unsigned nodes;
+    };
+    std::map<std::vector<int>, Graph> graphs;
 
     int state = 0;  // 1 created, 2 kernels precomputed
     int variant = -1;

@@ -292,14 +292,14 @@ mvd_status launch_x(K kern, const XArgs& a, cudaStream_t st, const char* name, i
 
 }  // namespace
 
-mvd_status fft_forward_real(const FftGeom& g, const float* src, float2* S, cudaStream_t st) {
+mvd_status fft_forward_real_generic(const FftGeom& g, const float* src, float2* S, cudaStream_t st) {
     XArgs a = make_x(g);
     a.src = src;
     a.S = S;
     return launch_x(k_x_forward, a, st, "fft x forward", KC_X_FORWARD);
 }
 
-mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st) {
+mvd_status fft_x_ratio_generic(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st) {
     XArgs a = make_x(g);
     a.S = S;
     a.phi = phi;
@@ -307,7 +307,7 @@ mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps,
     return launch_x(k_x_ratio, a, st, "fft x ratio", KC_X_RATIO);
 }
 
-mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st) {
+mvd_status fft_x_update_generic(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st) {
     XArgs a = make_x(g);
     a.S = const_cast<float2*>(S);
     a.psi = psi;
@@ -315,14 +315,14 @@ mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps
     return launch_x(k_x_inverse<true>, a, st, "fft x update", KC_X_UPDATE);
 }
 
-mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
+mvd_status fft_inverse_real_generic(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
     XArgs a = make_x(g);
     a.S = const_cast<float2*>(S);
     a.psi = dst;
     return launch_x(k_x_inverse<false>, a, st, "fft x inverse", KC_SETUP);
 }
 
-mvd_status fft_y(const FftGeom& g, float2* S, int inverse, cudaStream_t st) {
+mvd_status fft_y_generic(const FftGeom& g, float2* S, int inverse, cudaStream_t st) {
     LineArgs a{};
     a.L = g.Y;
     a.ls = g.Y + 1;
@@ -366,12 +366,46 @@ static mvd_status launch_z(const FftGeom& g, float2* S, const float2* K, float s
     return check_launch("fft z");
 }
 
-mvd_status fft_z_mul(const FftGeom& g, float2* S, const float2* K, cudaStream_t st) {
+mvd_status fft_z_mul_generic(const FftGeom& g, float2* S, const float2* K, cudaStream_t st) {
     return launch_z(g, S, K, 1.f, true, st);
 }
 
-mvd_status fft_z_forward_scaled(const FftGeom& g, float2* S, float scale, cudaStream_t st) {
+mvd_status fft_z_forward_scaled_generic(const FftGeom& g, float2* S, float scale, cudaStream_t st) {
     return launch_z(g, S, nullptr, scale, false, st);
+}
+
+// ---------------------------------------------------------------------------
+// public passes: the register-resident kernels when the axis length is a
+// supported power of two (and the generic engine is not forced), else the
+// generic shared-memory Stockham kernels above
+// ---------------------------------------------------------------------------
+mvd_status fft_forward_real(const FftGeom& g, const float* src, float2* S, cudaStream_t st) {
+    if (g.fast && fft_fast_supported(g.X)) return fft_forward_real_fast(g, src, S, st);
+    return fft_forward_real_generic(g, src, S, st);
+}
+mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st) {
+    if (g.fast && fft_fast_supported(g.X)) return fft_x_ratio_fast(g, S, phi, eps, st);
+    return fft_x_ratio_generic(g, S, phi, eps, st);
+}
+mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st) {
+    if (g.fast && fft_fast_supported(g.X)) return fft_x_update_fast(g, S, psi, eps, st);
+    return fft_x_update_generic(g, S, psi, eps, st);
+}
+mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
+    if (g.fast && fft_fast_supported(g.X)) return fft_inverse_real_fast(g, S, dst, st);
+    return fft_inverse_real_generic(g, S, dst, st);
+}
+mvd_status fft_y(const FftGeom& g, float2* S, int inverse, cudaStream_t st) {
+    if (g.fast && fft_fast_supported(g.Y)) return fft_y_fast(g, S, inverse, st);
+    return fft_y_generic(g, S, inverse, st);
+}
+mvd_status fft_z_mul(const FftGeom& g, float2* S, const float2* K, cudaStream_t st) {
+    if (g.fast && fft_fast_z_supported(g.Z)) return fft_z_mul_fast(g, S, K, st);
+    return fft_z_mul_generic(g, S, K, st);
+}
+mvd_status fft_z_forward_scaled(const FftGeom& g, float2* S, float scale, cudaStream_t st) {
+    if (g.fast && fft_fast_z_supported(g.Z)) return fft_z_forward_scaled_fast(g, S, scale, st);
+    return fft_z_forward_scaled_generic(g, S, scale, st);
 }
 
 }  // namespace mvd

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -153,13 +154,20 @@ void dev_free(T*& p) {
     p = nullptr;
 }
 
+void drop_graphs(mvd_ctx* c) {
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+}
+
 void free_fft(mvd_ctx* c) {
+    drop_graphs(c);
     dev_free(c->d_tw);
     dev_free(c->d_S);
     dev_free(c->d_K);
 }
 
 void free_all(mvd_ctx* c) {
+    drop_graphs(c);
     free_fft(c);
     dev_free(c->d_views);
     dev_free(c->d_psi);
@@ -202,6 +210,9 @@ mvd_status setup_fft(mvd_ctx* c) {
     g.Z = c->dims[2];
     g.Xh = g.X / 2 + 1;
     g.YZ = (long)g.Y * g.Z;
+    // MVD_FFT_GENERIC=1 forces the generic kernels (used to test both engines)
+    const char* gen = std::getenv("MVD_FFT_GENERIC");
+    g.fast = !(gen && gen[0] == '1');
     if (!make_radix_plan(g.X, &g.px) || !make_radix_plan(g.Y, &g.py) || !make_radix_plan(g.Z, &g.pz)) {
         set_error("FFT engine needs {2,3,5}-smooth dims, got %d x %d x %d", g.X, g.Y, g.Z);
         return MVD_ERR_UNSUPPORTED;
@@ -460,6 +471,7 @@ mvd_status mvd_precompute_kernels(mvd_ctx* c, int variant) {
         return MVD_ERR_ARG;
     }
     DeviceGuard dg(c->device);
+    drop_graphs(c);
     free_fft(c);
     dev_free(c->d_comp);
     dev_free(c->d_ktmp);
@@ -559,8 +571,50 @@ mvd_status mvd_iterate(mvd_ctx* c, int n_iter, const int* schedule, int schedule
         }
     }
     DeviceGuard dg(c->device);
-    for (int it = 0; it < n_iter; ++it)
-        for (int s = 0; s < L; ++s) MVD_TRY(one_update(c, schedule_len > 0 ? schedule[s] : s));
+    std::vector<int> sched(L);
+    for (int s = 0; s < L; ++s) sched[s] = schedule_len > 0 ? schedule[s] : s;
+    // One iteration of the schedule is captured once as a CUDA graph and
+    // replayed: the host launches one graph per iteration instead of 9
+    // kernels per view update. Not on the legacy default stream (it cannot be
+    // captured), not while per-kernel timing is on, and not with MVD_NO_GRAPH=1.
+    const char* ng = std::getenv("MVD_NO_GRAPH");
+    const bool use_graph = n_iter > 0 && c->stream != nullptr && !g_prof_on.load() && !(ng && ng[0] == '1');
+    if (use_graph) {
+        cudaGraphExec_t exec = nullptr;
+        unsigned nodes = 0;
+        auto it = c->graphs.find(sched);
+        if (it != c->graphs.end()) {
+            exec = it->second.exec;
+            nodes = it->second.nodes;
+        } else {
+            cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_status(e, "mvd_iterate: begin capture");
+            const unsigned long long before = g_launches.load();
+            mvd_status st = MVD_OK;
+            for (int s = 0; s < L && st == MVD_OK; ++s) st = one_update(c, sched[s]);
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(c->stream, &graph);
+            nodes = (unsigned)(g_launches.load() - before);
+            g_launches.fetch_sub(nodes);  // captured, not launched
+            if (st != MVD_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (e != cudaSuccess) return cuda_status(e, "mvd_iterate: end capture");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_status(e, "mvd_iterate: instantiate graph");
+            c->graphs[sched] = {exec, nodes};
+        }
+        for (int i = 0; i < n_iter; ++i) {
+            cudaError_t e = cudaGraphLaunch(exec, c->stream);
+            if (e != cudaSuccess) return cuda_status(e, "mvd_iterate: graph launch");
+            count_launch(nodes);
+        }
+        return MVD_OK;
+    }
+    for (int i = 0; i < n_iter; ++i)
+        for (int s = 0; s < L; ++s) MVD_TRY(one_update(c, sched[s]));
     return MVD_OK;
 }
 

@@ -255,3 +255,48 @@ def test_device_views_and_stream(mvd):
         d.iterate(3)
         got = d.result().astype(np.float64)
     assert rel_err(got, want) < PARITY_TOL, err_report(got, want)
+
+
+# ---------------------------------------------------------------------------
+# every power-of-two length of the register-resident passes, on each axis,
+# with the generic passes forced as a second engine
+# ---------------------------------------------------------------------------
+
+POW2_CASES = [(16, 16, 16), (32, 64, 128), (256, 16, 32), (64, 512, 16), (16, 32, 1024), (2048, 16, 16),
+              (16, 2048, 16), (16, 16, 2048), (48, 128, 96)]
+
+
+@pytest.mark.parametrize("engine", ["fast", "generic"])
+@pytest.mark.parametrize("dims", POW2_CASES)
+def test_fft_lengths(mvd, monkeypatch, dims, engine):
+    if engine == "generic":
+        monkeypatch.setenv("MVD_FFT_GENERIC", "1")
+    w = synth.small_case(200 + sum(dims), dims=dims, n_views=2, boxes=[(3, 5, 3), (5, 3, 7)], n_iter=2,
+                         asymmetric=True)
+    want, _ = oracle.deconvolve(w.views, w.psfs, 2, "efficient")
+    got, used, _ = _run_gpu(mvd, w, path="fft", n_iter=2)
+    assert used == "fft"
+    assert rel_err(got, want) < PARITY_TOL, err_report(got, want)
+
+
+def test_graph_replay_matches_plain_launches(mvd, monkeypatch):
+    """On a non-default stream one iteration is captured as a CUDA graph and replayed; the
+    result must equal the one-by-one launches bit for bit, and match the oracle."""
+    import torch
+
+    w = synth.small_case(41, dims=(64, 48, 32), n_views=3, boxes=[(7, 5, 9), (5, 9, 7), (9, 7, 5)], n_iter=3,
+                         asymmetric=True)
+    want, _ = oracle.deconvolve(w.views, w.psfs, 3, "efficient", schedule=[2, 0, 1])
+    out = {}
+    for mode in ("graph", "plain"):
+        if mode == "plain":
+            monkeypatch.setenv("MVD_NO_GRAPH", "1")
+        s = torch.cuda.Stream()
+        for path in ("fft", "direct"):
+            with mvd.Deconvolver(w.views, w.psfs, "efficient", stream=s, path=path) as d:
+                d.iterate(2, [2, 0, 1])
+                d.iterate(1, [2, 0, 1])
+                out[mode, path] = d.result()
+    for path in ("fft", "direct"):
+        assert np.array_equal(out["graph", path], out["plain", path]), path
+        assert rel_err(out["graph", path], want) < PARITY_TOL, err_report(out["graph", path], want)
