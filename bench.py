@@ -41,7 +41,7 @@ L2_BYTES = 129 * 2 ** 20
 # array it must touch, once (half spectrum = 8 * (X/2+1) * Y * Z bytes)
 def _kernel_bytes(X, Y, Z):
     M = X * Y * Z
-    spec = 8 * (X // 2 + 1) * Y * Z
+    spec = 8 * (X // 2 + 1) * Y * Z  # FP32 half spectrum; double-float is 2 * spec
     return {
         "x_forward": 4 * M + spec,          # read psi, write S
         "y": 2 * spec,                      # read S, write S
@@ -50,6 +50,10 @@ def _kernel_bytes(X, Y, Z):
         "x_update": spec + 8 * M,           # read S and psi, write psi
         "direct_ratio": 12 * M,             # read psi and phi, write r
         "direct_update": 12 * M,            # read r and psi, write psi
+        "dd_x_forward": 4 * M + 2 * spec,   # read psi, write S2
+        "dd_y": 4 * spec,                   # read S2, write S2
+        "dd_z_mul": 6 * spec,               # read S2 and the double-float PSF spectrum, write S2
+        "dd_x_ratio": 2 * spec + 4 * M + spec,  # read S2 and phi, write S
     }
 
 
@@ -243,6 +247,26 @@ def run_gpu(args):
     psi_dev = d.result()
     d.close()
 
+    # the same steps with every pass in FP32 (MVD_FAST), for comparison
+    fast = mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft", device=local, precision="fast")
+
+    def fast_step():
+        fast.set_estimate(None)
+        fast.iterate(w.n_iter)
+
+    for _ in range(args.warmup):
+        fast_step()
+    ev4 = torch.cuda.Event(enable_timing=True)
+    ev5 = torch.cuda.Event(enable_timing=True)
+    ev4.record(stream)
+    for _ in range(args.steps):
+        fast_step()
+    ev5.record(stream)
+    ev5.synchronize()
+    ms_fast = ev4.elapsed_time(ev5)
+    psi_fast = fast.result()
+    fast.close()
+
     # --- end to end through the public API from pinned host buffers ---
     pinned = [torch.from_numpy(v).pin_memory() for v in w.views]
     hviews = [p.numpy() for p in pinned]
@@ -307,6 +331,12 @@ def run_gpu(args):
             "update_effective_hbm_frac": (12.0 * units_per_step * args.steps / (ms * 1e-3) / 1e9) / peak,
             "kernels": per_kernel,
             "profiled_ms_per_step": ms_profiled / args.steps,
+            "precision": "forward blur in double-float (pairs of FP32), back-projection FP32",
+            "fast_fp32": {"value": ws * units_per_step * args.steps / (ms_fast * 1e-3) / 1e9, "unit": UNIT,
+                          "ms_per_step": ms_fast / args.steps,
+                          "max_rel_diff_vs_precise": float(np.max(np.abs(psi_fast.astype(np.float64) - psi_dev)
+                                                                  / np.maximum(np.abs(psi_dev.astype(np.float64)),
+                                                                               1e-3 * np.abs(psi_dev).max())))},
             "clocks": clk.summary(),
             "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"one view update (view 0) of the {X}x{Y}x{Z} workload, FP64 direct "
@@ -319,15 +349,108 @@ def run_gpu(args):
     return 0
 
 
+def run_batched(args):
+    """48 volumes of uneven size and view count (15 iterations each): one persistent
+    batched launch vs the same volumes deconvolved one after another."""
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    from paper_1308_0730_gb300 import mvd
+
+    t0 = time.perf_counter()
+    ws = synth.config4()
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    ds = []
+    for w in ws:
+        with torch.cuda.stream(stream):
+            dv = [torch.from_numpy(v).cuda() for v in w.views]
+        stream.synchronize()
+        ds.append(mvd.Deconvolver(dv, w.psfs, "efficient", path="fft", stream=stream))
+    n_iter = ws[0].n_iter
+    units = sum(w.voxels * w.n_views * n_iter for w in ws)
+
+    def reset():
+        for d in ds:
+            d.set_estimate(None)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # plain: one volume after another (each replays its own per-iteration graph)
+    for _ in range(max(1, args.warmup)):
+        reset()
+        for d in ds:
+            d.iterate(n_iter)
+    plain_ms = []
+    for _ in range(args.steps):
+        reset()
+        ev0.record(stream)
+        for d in ds:
+            d.iterate(n_iter)
+        ev1.record(stream)
+        ev1.synchronize()
+        plain_ms.append(ev0.elapsed_time(ev1))
+    plain_res = [d.result() for d in ds]
+    b = mvd.mvd_batch_create(ds, n_iter)
+    for _ in range(max(1, args.warmup)):
+        reset()
+        mvd.mvd_batch_run(b)
+        mvd.mvd_batch_wait(b)
+    batch_ms = []
+    launches0 = mvd.mvd_launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            reset()
+            ev0.record(stream)
+            mvd.mvd_batch_run(b)
+            ev1.record(stream)
+            ev1.synchronize()
+            batch_ms.append(ev0.elapsed_time(ev1))
+    mvd.mvd_batch_wait(b)
+    batch_res = [d.result() for d in ds]
+    tasks = mvd.mvd_batch_tasks(b)
+    mvd.mvd_batch_destroy(b)
+    for d in ds:
+        d.close()
+    errs = []
+    for p, q in zip(plain_res, batch_res):
+        p64 = p.astype(np.float64)
+        tau = 1e-3 * np.abs(p64).max()
+        errs.append(float(np.max(np.abs(q - p64) / np.maximum(np.abs(p64), tau))))
+    pm, bm = statistics.median(plain_ms), statistics.median(batch_ms)
+    line = {
+        "metric": METRIC, "value": units / (bm * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": bm, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch of {len(ws)} volumes (48^3 to 320x320x192, 2-6 views, 15 iterations)",
+                   "voxels": int(sum(w.voxels for w in ws)), "voxel_view_updates": int(units),
+                   "engine": "fft (generic passes)", "l2": "inputs larger than L2"},
+        "batched_vs_plain": {"batched_ms": bm, "plain_ms": pm, "speedup": pm / bm,
+                             "plain_value": units / (pm * 1e-3) / 1e9, "tasks_per_run": tasks,
+                             "max_rel_err_batched_vs_plain": max(errs)},
+        "gpu_launches_per_step": (mvd.mvd_launch_count() - launches0) / args.steps,
+        "generation_s": gen_s,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mvd", choices=["mvd", "reference"])
+    ap.add_argument("--batched", action="store_true",
+                    help="time the 48-volume batched workload against per-volume runs instead")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched:
+        return run_batched(args)
     return run_gpu(args)
 
 

@@ -69,15 +69,27 @@ typedef enum {
 /* Convolution engine. AUTO lets the autotuner pick per (dims, PSF boxes). */
 typedef enum { MVD_PATH_AUTO = 0, MVD_PATH_DIRECT = 1, MVD_PATH_FFT = 2 } mvd_path;
 
+/* Arithmetic of the FFT engine's forward blur b = psi * P_v.
+ *   MVD_PRECISE: double-float (pairs of FP32, about 48 significant bits) for
+ *     the forward blur, FP32 for the back-projection. FP32 FFT rounding is
+ *     absolute (it scales with the whole volume's norm), so in FP32 the dim
+ *     voxels of b carry large relative errors that the ratio phi / b and the
+ *     iteration amplify; double-float removes them.
+ *   MVD_FAST: everything in FP32 (faster; after tens of iterations dim voxels
+ *     differ from an exact computation by about 1e-3 relative). */
+typedef enum { MVD_PRECISE = 0, MVD_FAST = 1 } mvd_precision;
+
 typedef struct {
     float eps;           /* floor of b and psi; <= 0 selects 1e-4 * psi0 */
     int path;            /* mvd_path */
     void* stream;        /* cudaStream_t to order all work on; NULL = default stream */
     int views_on_device; /* 1: `views` are device pointers (copied device-to-device) */
     int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
+    int precision;       /* mvd_precision (FFT engine) */
 } mvd_options;
 
-/* Fills *opt with eps = 0 (auto), path = AUTO, stream = NULL, host views, device -1. */
+/* Fills *opt with eps = 0 (auto), path = AUTO, stream = NULL, host views,
+ * device -1, precision = MVD_PRECISE. */
 void mvd_default_options(mvd_options* opt);
 
 /*
@@ -168,6 +180,31 @@ unsigned long long mvd_launch_count(void);
  */
 void mvd_profile_enable(int on);
 int mvd_profile_read(const char** names, unsigned long long* launches, double* ms, int max);
+
+/*
+ * Batched form: many independent problems of uneven size and view count
+ * (time points, tiles of a large specimen; the paper processes such units
+ * independently, Suppl. Table 1 and main text) advanced together by one
+ * persistent kernel launch, captured in a CUDA graph.
+ *   ctxs    n contexts, each created and precomputed with the FFT engine,
+ *           all on one device and one stream (else MVD_ERR_ARG /
+ *           MVD_ERR_STATE / MVD_ERR_UNSUPPORTED). The batch keeps pointers
+ *           into them: destroy the batch before any of its contexts, and do
+ *           not re-precompute a context while a batch uses it.
+ *   n_iter  iterations of each context's default schedule (views 0..N-1)
+ *           per mvd_batch_run.
+ * mvd_batch_run enqueues the job on the shared stream (each context's psi
+ * advances by n_iter iterations from its current value); mvd_batch_wait
+ * synchronises and returns MVD_ERR_TIMEOUT if a block gave up waiting for a
+ * dependency (a bounded wait; MVD_BATCH_POLL_LIMIT sets the poll count).
+ * mvd_batch_tasks gives the number of tiles in one run.
+ */
+typedef struct mvd_batch mvd_batch;
+mvd_status mvd_batch_create(mvd_ctx* const* ctxs, int n, int n_iter, mvd_batch** out);
+mvd_status mvd_batch_run(mvd_batch* batch);
+mvd_status mvd_batch_wait(mvd_batch* batch);
+long long mvd_batch_tasks(const mvd_batch* batch);
+void mvd_batch_destroy(mvd_batch* batch);
 
 /*
  * Allocation-free view update. The paper has no counterpart: this entry point

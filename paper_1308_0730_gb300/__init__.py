@@ -23,4 +23,9 @@ from .mvd import (  # noqa: F401
     mvd_get_compound_kernel,
     mvd_profile_enable,
     mvd_profile_read,
+    mvd_batch_create,
+    mvd_batch_run,
+    mvd_batch_wait,
+    mvd_batch_tasks,
+    mvd_batch_destroy,
 )

@@ -33,6 +33,10 @@ enum KernelClass {
     KC_X_UPDATE,
     KC_DIRECT_RATIO,
     KC_DIRECT_UPDATE,
+    KC_DD_X_FORWARD,
+    KC_DD_Y,
+    KC_DD_Z_MUL,
+    KC_DD_X_RATIO,
     KC_SETUP,
     KC_COUNT
 };
@@ -74,11 +78,14 @@ bool make_radix_plan(int L, FftPlan* p);
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
+struct cdd;  // complex double-float (dd.cuh)
+
 struct FftGeom {
     int X, Y, Z, Xh;
     long YZ;
     FftPlan px, py, pz;
-    bool fast;  // use the register-resident kernels where the length allows
+    bool fast;                       // use the register-resident kernels where the length allows
+    const cdd *tw2x, *tw2y, *tw2z;  // double-float twiddle tables (precise forward blur)
 };
 
 // Spectrum layout: S[kx][z][y] (y fastest), kx in [0, Xh), Xh = X/2 + 1.
@@ -89,6 +96,13 @@ mvd_status fft_z_forward_scaled(const FftGeom& g, float2* S, float scale, cudaSt
 mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
 mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st);
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
+
+// double-float forward blur (fft_dd.cu): spectrum of complex double-float
+mvd_status dd_forward_real(const FftGeom& g, const float* src, cdd* S2, cudaStream_t st);
+mvd_status dd_y(const FftGeom& g, cdd* S2, int inverse, cudaStream_t st);
+mvd_status dd_z_mul(const FftGeom& g, cdd* S2, const cdd* K2, cudaStream_t st);
+mvd_status dd_z_forward_scaled(const FftGeom& g, cdd* S2, double scale, cudaStream_t st);
+mvd_status dd_x_ratio(const FftGeom& g, const cdd* S2, const float* phi, float eps, float2* S, cudaStream_t st);
 
 // register-resident variants for power-of-two lengths (fft_fast.cu)
 bool fft_fast_supported(int L);
@@ -147,9 +161,15 @@ struct mvd_ctx {
 
     // FFT engine
     mvd::FftGeom geom{};
+    int precise = 1;         // forward blur in double-float (MVD_PRECISE)
     float2* d_tw = nullptr;  // twiddle tables (x, y, z)
     float2* d_S = nullptr;   // work spectrum Xh*Y*Z
-    float2* d_K = nullptr;   // 2*nv kernel spectra (P_v, then P_v^comp), each Xh*Y*Z
+    // FP32 kernel spectra, each Xh*Y*Z: fast mode 2*nv (P_v, P_v^comp per
+    // view), precise mode nv (P_v^comp only)
+    float2* d_K = nullptr;
+    mvd::cdd* d_tw2 = nullptr;  // double-float twiddle tables (x, y, z)
+    mvd::cdd* d_S2 = nullptr;   // double-float work spectrum (precise mode)
+    mvd::cdd* d_KP2 = nullptr;  // nv double-float spectra of P_v (precise mode)
 
     // one instantiated graph per schedule (one iteration each)
     struct Graph {

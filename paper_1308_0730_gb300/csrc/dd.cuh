@@ -1,0 +1,229 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant bits, built from
+// the error-free transformations of Knuth (TwoSum), Dekker (FastTwoSum) and
+// the FMA-based exact product (TwoProd). Used for the forward blur
+// b = psi * P_v, whose FP32 FFT rounding (absolute, scaled by the whole
+// volume's norm) would swamp dim voxels of b.
+//
+// These steps rely on IEEE round-to-nearest FP32 adds without
+// reassociation; the library is never built with fast-math.
+#pragma once
+
+#include "fft.cuh"
+
+namespace mvd {
+
+struct dd {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dd dd_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ dd dd_fast_two_sum(float a, float b) {  // needs |a| >= |b| (or a == 0)
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dd dd_add(dd x, dd y) {
+    const dd s = dd_two_sum(x.hi, y.hi);
+    return dd_fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ dd dd_sub(dd x, dd y) { return dd_add(x, dd{-y.hi, -y.lo}); }
+__device__ __forceinline__ dd dd_mul(dd x, dd y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return dd_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dd dd_from(float a) { return {a, 0.f}; }
+
+// complex double-float, 16 bytes (loads and stores as float4)
+struct __align__(16) cdd {
+    dd re, im;
+};
+
+__device__ __forceinline__ cdd cadd(cdd a, cdd b) { return {dd_add(a.re, b.re), dd_add(a.im, b.im)}; }
+__device__ __forceinline__ cdd csub(cdd a, cdd b) { return {dd_sub(a.re, b.re), dd_sub(a.im, b.im)}; }
+__device__ __forceinline__ cdd cmul(cdd a, cdd b) {
+    return {dd_sub(dd_mul(a.re, b.re), dd_mul(a.im, b.im)), dd_add(dd_mul(a.re, b.im), dd_mul(a.im, b.re))};
+}
+__device__ __forceinline__ cdd cconj(cdd a) { return {a.re, dd{-a.im.hi, -a.im.lo}}; }
+__device__ __forceinline__ cdd chalf(cdd a) {  // exact
+    return {dd{0.5f * a.re.hi, 0.5f * a.re.lo}, dd{0.5f * a.im.hi, 0.5f * a.im.lo}};
+}
+template <int S>
+__device__ __forceinline__ cdd mul_si(cdd a) {  // exact
+    return S < 0 ? cdd{a.im, dd{-a.re.hi, -a.re.lo}} : cdd{dd{-a.im.hi, -a.im.lo}, a.re};
+}
+__device__ __forceinline__ cdd czero_dd() { return {dd{0.f, 0.f}, dd{0.f, 0.f}}; }
+__device__ __forceinline__ cdd cdd_load(const cdd* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {dd{v.x, v.y}, dd{v.z, v.w}};
+}
+__device__ __forceinline__ cdd cdd_load_cg(const cdd* p) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+    return {dd{v.x, v.y}, dd{v.z, v.w}};
+}
+__device__ __forceinline__ cdd cdd_load_nc(const cdd* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {dd{v.x, v.y}, dd{v.z, v.w}};
+}
+__device__ __forceinline__ void cdd_store(cdd* p, cdd a) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
+}
+
+// constant (cos, S sin) pairs as double-float: hi = fl32(c), lo = fl32(c - hi)
+#define MVD_DD(c) dd{(float)(c), (float)((c) - (double)(float)(c))}
+
+// exp(s 2 pi i m / L) from the forward table tw[m] = exp(-2 pi i m / L)
+template <int S>
+__device__ __forceinline__ cdd twiddle_dd(const cdd* __restrict__ tw, int m) {
+    cdd w = cdd_load_nc(tw + m);
+    if (S > 0) w.im = dd{-w.im.hi, -w.im.lo};
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// small DFTs in double-float: y[m] = sum_r v[r] exp(s 2 pi i r m / R)
+// ---------------------------------------------------------------------------
+template <int R, int S>
+struct DftDD;
+
+template <int S>
+struct DftDD<2, S> {
+    __device__ __forceinline__ static void run(cdd* v) {
+        const cdd a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <int S>
+struct DftDD<4, S> {
+    __device__ __forceinline__ static void run(cdd* v) {
+        const cdd t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const cdd t2 = cadd(v[1], v[3]), t3 = mul_si<S>(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+
+template <int S>
+struct DftDD<8, S> {
+    __device__ __forceinline__ static void run(cdd* v) {
+        cdd e[4] = {v[0], v[2], v[4], v[6]};
+        cdd o[4] = {v[1], v[3], v[5], v[7]};
+        DftDD<4, S>::run(e);
+        DftDD<4, S>::run(o);
+        const double h = 0.70710678118654752440;  // sqrt(2)/2
+        const cdd w1{MVD_DD(h), MVD_DD(S * h)};
+        const cdd w3{MVD_DD(-h), MVD_DD(S * h)};
+        const cdd o1 = cmul(o[1], w1), o2 = mul_si<S>(o[2]), o3 = cmul(o[3], w3);
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
+template <int S>
+struct DftDD<3, S> {
+    __device__ __forceinline__ static void run(cdd* v) {
+        const double c = -0.5, h = 0.86602540378443864676;  // cos(2pi/3), sin(2pi/3)
+        const cdd t = cadd(v[1], v[2]);
+        const cdd u = csub(v[1], v[2]);
+        const dd cd = MVD_DD(c), hd = MVD_DD(h);
+        const cdd m = cadd(v[0], cdd{dd_mul(cd, t.re), dd_mul(cd, t.im)});
+        const cdd j = mul_si<S>(cdd{dd_mul(hd, u.re), dd_mul(hd, u.im)});
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, j);
+        v[2] = csub(m, j);
+    }
+};
+
+template <int S>
+struct DftDD<5, S> {
+    __device__ __forceinline__ static void run(cdd* v) {
+        const dd c1 = MVD_DD(0.30901699437494742410), c2 = MVD_DD(-0.80901699437494742410);
+        const dd s1 = MVD_DD(0.95105651629515357212), s2 = MVD_DD(0.58778525229247312917);
+        const cdd t1 = cadd(v[1], v[4]), u1 = csub(v[1], v[4]);
+        const cdd t2 = cadd(v[2], v[3]), u2 = csub(v[2], v[3]);
+        const cdd a0 = v[0];
+        auto sc = [](dd k, cdd x) { return cdd{dd_mul(k, x.re), dd_mul(k, x.im)}; };
+        const cdd m1 = cadd(a0, cadd(sc(c1, t1), sc(c2, t2)));
+        const cdd m2 = cadd(a0, cadd(sc(c2, t1), sc(c1, t2)));
+        const cdd j1 = mul_si<S>(cadd(sc(s1, u1), sc(s2, u2)));
+        const cdd j2 = mul_si<S>(csub(sc(s2, u1), sc(s1, u2)));
+        v[0] = cadd(a0, cadd(t1, t2));
+        v[1] = cadd(m1, j1);
+        v[4] = csub(m1, j1);
+        v[2] = cadd(m2, j2);
+        v[3] = csub(m2, j2);
+    }
+};
+
+// one Stockham butterfly and the multi-line driver, as in fft.cuh
+template <int R, int S>
+__device__ __forceinline__ void stockham_bfly_dd(const cdd* __restrict__ A, cdd* __restrict__ B, int j, int Ns,
+                                                 int L, const cdd* __restrict__ tw) {
+    const int nb = L / R;
+    const int k = j % Ns;
+    cdd v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = A[j + r * nb];
+    if (Ns > 1) {
+        const int step = k * (L / (Ns * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle_dd<S>(tw, r * step));
+    }
+    DftDD<R, S>::run(v);
+    const int d = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) B[d + r * Ns] = v[r];
+}
+
+template <int R, int S>
+__device__ __forceinline__ void stockham_stage_dd(const cdd* __restrict__ A, cdd* __restrict__ B, int nlines, int ls,
+                                                  int L, int Ns, const cdd* __restrict__ tw) {
+    const int nb = L / R;
+    const int total = nlines * nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int line = t / nb;
+        const int j = t - line * nb;
+        stockham_bfly_dd<R, S>(A + line * ls, B + line * ls, j, Ns, L, tw);
+    }
+}
+
+// plan radices as FftPlan, twiddles from a double-float table of length L
+template <int S>
+__device__ cdd* fft_lines_dd(cdd* A, cdd* B, int nlines, int ls, const FftPlan& p, const cdd* tw) {
+    int Ns = 1;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.radix[s];
+        switch (R) {
+            case 8: stockham_stage_dd<8, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 4: stockham_stage_dd<4, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 2: stockham_stage_dd<2, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 3: stockham_stage_dd<3, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            default: stockham_stage_dd<5, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+        }
+        __syncthreads();
+        cdd* t = A;
+        A = B;
+        B = t;
+        Ns *= R;
+    }
+    return A;
+}
+
+}  // namespace mvd

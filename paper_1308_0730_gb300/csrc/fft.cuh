@@ -148,6 +148,20 @@ __device__ __forceinline__ void stockham_bfly(const float2* __restrict__ A, floa
     for (int r = 0; r < R; ++r) B[d + r * Ns] = v[r];
 }
 
+// All butterflies of one stage (radix R, Ns combined so far) over `nlines`
+// lines, spread over the block's threads.
+template <int R, int S>
+__device__ __forceinline__ void stockham_stage(const float2* __restrict__ A, float2* __restrict__ B, int nlines,
+                                               int ls, int L, int Ns, const float2* __restrict__ tw) {
+    const int nb = L / R;
+    const int total = nlines * nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int line = t / nb;
+        const int j = t - line * nb;
+        stockham_bfly<R, S>(A + line * ls, B + line * ls, j, Ns, L, tw);
+    }
+}
+
 // Transforms `nlines` lines of length p.L stored at A + line*ls (line stride
 // ls >= L), using B (same shape) as the ping-pong buffer. All threads of the
 // block take part; the call begins and ends with the data synchronised.
@@ -157,20 +171,12 @@ __device__ float2* fft_lines(float2* A, float2* B, int nlines, int ls, const Fft
     int Ns = 1;
     for (int s = 0; s < p.nst; ++s) {
         const int R = p.radix[s];
-        const int nb = p.L / R;
-        const int total = nlines * nb;
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            const int line = t / nb;
-            const int j = t - line * nb;
-            const float2* a = A + line * ls;
-            float2* b = B + line * ls;
-            switch (R) {
-                case 8: stockham_bfly<8, S>(a, b, j, Ns, p.L, p.tw); break;
-                case 4: stockham_bfly<4, S>(a, b, j, Ns, p.L, p.tw); break;
-                case 2: stockham_bfly<2, S>(a, b, j, Ns, p.L, p.tw); break;
-                case 3: stockham_bfly<3, S>(a, b, j, Ns, p.L, p.tw); break;
-                default: stockham_bfly<5, S>(a, b, j, Ns, p.L, p.tw); break;
-            }
+        switch (R) {
+            case 8: stockham_stage<8, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
+            case 4: stockham_stage<4, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
+            case 2: stockham_stage<2, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
+            case 3: stockham_stage<3, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
+            default: stockham_stage<5, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
         }
         __syncthreads();
         float2* t = A;
@@ -179,6 +185,23 @@ __device__ float2* fft_lines(float2* A, float2* B, int nlines, int ls, const Fft
         Ns *= R;
     }
     return A;
+}
+
+// Global loads of data that other blocks of the same launch may have written
+// (the persistent batch kernel) must bypass L1: CO selects L2-only loads.
+template <bool CO>
+__device__ __forceinline__ float2 ld2(const float2* p) {
+    if constexpr (CO)
+        return __ldcg(p);
+    else
+        return *p;
+}
+template <bool CO>
+__device__ __forceinline__ float ld1(const float* p) {
+    if constexpr (CO)
+        return __ldcg(p);
+    else
+        return *p;
 }
 
 }  // namespace mvd

@@ -1,0 +1,261 @@
+// Forward blur b = psi * P_v in double-float (tile-level device functions,
+// generic mixed-radix plans). Same layout as the FP32 passes: spectrum
+// S2[kx][z][y] of complex double-float (16 bytes), two real x-lines per
+// complex line. The last pass leaves double-float: it rounds b to FP32, forms
+// the ratio and hands the FP32 forward x transform of (r - 1) to the FP32
+// back-projection passes.
+//
+// CO = true makes loads of data written inside the same launch L2 loads (the
+// persistent batch kernel).
+#pragma once
+
+#include "dd.cuh"
+#include "fft_generic.cuh"
+
+namespace mvd {
+
+// half the lines of the FP32 tiles (elements are twice as large)
+__host__ __device__ inline int dd_x_pairs(int X) {
+    const int p = gen_x_pairs(X) / 2;
+    return p < 1 ? 1 : p;
+}
+__host__ __device__ inline int dd_y_lines(int Y) {
+    const int p = gen_y_lines(Y) / 2;
+    return p < 1 ? 1 : p;
+}
+__host__ __device__ inline int dd_z_cols(int Z, int Y) {
+    const int q = gen_z_cols(Z, Y) / 2;
+    return q < 1 ? 1 : q;
+}
+__host__ __device__ inline long dd_x_tiles(int X, long YZ) { return gen_div_up(YZ, 2 * dd_x_pairs(X)); }
+__host__ __device__ inline long dd_y_tiles(int Y, int Xh, int Z) { return gen_div_up((long)Xh * Z, dd_y_lines(Y)); }
+__host__ __device__ inline long dd_z_tiles(int Z, int Y, int Xh) { return (long)Xh * gen_div_up(Y, dd_z_cols(Z, Y)); }
+__host__ __device__ inline size_t dd_x_smem(int X) { return (size_t)2 * dd_x_pairs(X) * (X + 1) * sizeof(cdd); }
+__host__ __device__ inline size_t dd_y_smem(int Y) { return (size_t)2 * dd_y_lines(Y) * (Y + 1) * sizeof(cdd); }
+__host__ __device__ inline size_t dd_z_smem(int Z, int Y) { return (size_t)2 * dd_z_cols(Z, Y) * (Z + 1) * sizeof(cdd); }
+
+struct DdX {
+    int X, Xh, P, ls;
+    long YZ;
+    FftPlan plan;           // radices of X
+    const cdd* tw2;         // double-float twiddles of X
+    const float2* tw;       // FP32 twiddles of X (the FP32 forward transform of r - 1)
+    const float* src;       // real rows
+    cdd* S2;                // double-float spectrum
+    const float* phi;       // observed view
+    float2* S;              // FP32 spectrum of r - 1
+    float eps;
+};
+
+__host__ __device__ inline DdX dd_x_args(int X, long YZ, const FftPlan& plan, const cdd* tw2) {
+    DdX a{};
+    a.X = X;
+    a.Xh = X / 2 + 1;
+    a.P = dd_x_pairs(X);
+    a.ls = X + 1;
+    a.YZ = YZ;
+    a.plan = plan;
+    a.tw2 = tw2;
+    return a;
+}
+
+template <bool CO>
+__device__ void dd_x_forward_tile(const DdX& a, long tile, cdd* sm) {
+    cdd* A = sm;
+    cdd* B = sm + a.P * a.ls;
+    const long rho0 = tile * 2 * a.P;
+    const int nrows = (int)min((long)2 * a.P, a.YZ - rho0);
+    const int n2 = a.P * a.X;
+    // pair p = rows (p, P+p): complex line a + i b, exact in double-float
+    for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+        const int p = t / a.X, n = t - p * a.X;
+        const float va = p < nrows ? ld1<CO>(a.src + (rho0 + p) * a.X + n) : 0.f;
+        const float vb = a.P + p < nrows ? ld1<CO>(a.src + (rho0 + a.P + p) * a.X + n) : 0.f;
+        A[p * a.ls + n] = cdd{dd_from(va), dd_from(vb)};
+    }
+    __syncthreads();
+    const cdd* F = fft_lines_dd<-1>(A, B, a.P, a.ls, a.plan, a.tw2);
+    const int P2 = 2 * a.P;
+    for (int t = threadIdx.x; t < a.Xh * P2; t += blockDim.x) {
+        const int k = t / P2, row = t - k * P2;
+        if (row >= nrows) continue;
+        const int p = row < a.P ? row : row - a.P;
+        const cdd zk = F[p * a.ls + k];
+        const cdd zm = cconj(F[p * a.ls + (k == 0 ? 0 : a.X - k)]);
+        cdd val;
+        if (row < a.P) {
+            val = chalf(cadd(zk, zm));
+        } else {  // (zk - zm) / (2i)
+            const cdd d = chalf(csub(zk, zm));
+            val = cdd{d.im, dd{-d.re.hi, -d.re.lo}};
+        }
+        cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, val);
+    }
+}
+
+// double-float spectrum -> inverse x -> b (rounded to FP32) -> r - 1 with
+// r = phi / max(b, eps) -> FP32 forward x -> FP32 spectrum
+template <bool CO>
+__device__ void dd_x_ratio_tile(const DdX& a, long tile, cdd* sm) {
+    cdd* A = sm;
+    cdd* B = sm + a.P * a.ls;
+    const long rho0 = tile * 2 * a.P;
+    const int nrows = (int)min((long)2 * a.P, a.YZ - rho0);
+    const int P2 = 2 * a.P;
+    for (int t = threadIdx.x; t < a.Xh * P2; t += blockDim.x) {
+        const int k = t / P2, row = t - k * P2;
+        cdd v = czero_dd();
+        if (row < nrows) v = CO ? cdd_load_cg(a.S2 + (long)k * a.YZ + rho0 + row) : cdd_load(a.S2 + (long)k * a.YZ + rho0 + row);
+        if (row < a.P)
+            A[row * a.ls + k] = v;
+        else
+            B[(row - a.P) * a.ls + k] = v;
+    }
+    __syncthreads();
+    const int half = (a.X + 1) / 2;
+    for (int t = threadIdx.x; t < a.P * a.Xh; t += blockDim.x) {
+        const int p = t / a.Xh, k = t - p * a.Xh;
+        const cdd av = A[p * a.ls + k], bv = B[p * a.ls + k];
+        // A + iB and, at -k, conj(A) + i conj(B)
+        A[p * a.ls + k] = cdd{dd_sub(av.re, bv.im), dd_add(av.im, bv.re)};
+        if (k >= 1 && k < half) A[p * a.ls + (a.X - k)] = cdd{dd_add(av.re, bv.im), dd_sub(bv.re, av.im)};
+    }
+    __syncthreads();
+    cdd* R = fft_lines_dd<+1>(A, B, a.P, a.ls, a.plan, a.tw2);
+    // FP32 buffers in the other half of shared memory
+    float2* F0 = reinterpret_cast<float2*>(R == A ? B : A);
+    float2* F1 = F0 + a.P * a.ls;
+    const int n2 = a.P * a.X;
+    for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+        const int p = t / a.X, n = t - p * a.X;
+        const cdd z = R[p * a.ls + n];
+        const float ba = z.re.hi + z.re.lo, bb = z.im.hi + z.im.lo;
+        float ra = 0.f, rb = 0.f;
+        if (p < nrows) ra = __ldg(a.phi + (rho0 + p) * a.X + n) / fmaxf(ba, a.eps) - 1.f;
+        if (a.P + p < nrows) rb = __ldg(a.phi + (rho0 + a.P + p) * a.X + n) / fmaxf(bb, a.eps) - 1.f;
+        F0[p * a.ls + n] = make_float2(ra, rb);
+    }
+    __syncthreads();
+    const float2* F = fft_lines<-1>(F0, F1, a.P, a.ls, a.plan);
+    // unpack into the FP32 spectrum (as gen_unpack_store, with this tile's P)
+    for (int t = threadIdx.x; t < a.Xh * P2; t += blockDim.x) {
+        const int k = t / P2, row = t - k * P2;
+        if (row >= nrows) continue;
+        const int p = row < a.P ? row : row - a.P;
+        const float2 zk = F[p * a.ls + k];
+        const float2 zm = cconj(F[p * a.ls + (k == 0 ? 0 : a.X - k)]);
+        float2 val;
+        if (row < a.P) {
+            val = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
+        } else {
+            const float2 d = csub(zk, zm);
+            val = make_float2(0.5f * d.y, -0.5f * d.x);
+        }
+        a.S[(long)k * a.YZ + rho0 + row] = val;
+    }
+}
+
+struct DdY {
+    int L, ls, P;
+    long nlines;
+    FftPlan plan;
+    const cdd* tw2;
+    cdd* S2;
+};
+
+__host__ __device__ inline DdY dd_y_args(int Y, int Xh, int Z, const FftPlan& plan, const cdd* tw2, cdd* S2) {
+    DdY a{};
+    a.L = Y;
+    a.ls = Y + 1;
+    a.P = dd_y_lines(Y);
+    a.nlines = (long)Xh * Z;
+    a.plan = plan;
+    a.tw2 = tw2;
+    a.S2 = S2;
+    return a;
+}
+
+template <bool CO, int S>
+__device__ void dd_y_tile(const DdY& a, long tile, cdd* sm) {
+    cdd* A = sm;
+    cdd* B = sm + a.P * a.ls;
+    const long l0 = tile * a.P;
+    const int nl = (int)min((long)a.P, a.nlines - l0);
+    for (int t = threadIdx.x; t < a.P * a.L; t += blockDim.x) {
+        const int line = t / a.L, y = t - line * a.L;
+        cdd v = czero_dd();
+        if (line < nl) v = CO ? cdd_load_cg(a.S2 + (l0 + line) * a.L + y) : cdd_load(a.S2 + (l0 + line) * a.L + y);
+        A[line * a.ls + y] = v;
+    }
+    __syncthreads();
+    const cdd* R = fft_lines_dd<S>(A, B, a.P, a.ls, a.plan, a.tw2);
+    for (int t = threadIdx.x; t < nl * a.L; t += blockDim.x) {
+        const int line = t / a.L, y = t - line * a.L;
+        cdd_store(a.S2 + (l0 + line) * a.L + y, R[line * a.ls + y]);
+    }
+}
+
+struct DdZ {
+    int Z, Y, Q, ls, ntiles_y;
+    long YZ;
+    FftPlan plan;
+    const cdd* tw2;
+    cdd* S2;
+    const cdd* K2;  // double-float kernel spectrum (MUL)
+    dd scale;       // forward-only scale
+};
+
+__host__ __device__ inline DdZ dd_z_args(int Z, int Y, long YZ, const FftPlan& plan, const cdd* tw2, cdd* S2,
+                                         const cdd* K2, dd scale) {
+    DdZ a{};
+    a.Z = Z;
+    a.Y = Y;
+    a.Q = dd_z_cols(Z, Y);
+    a.ls = Z + 1;
+    a.ntiles_y = (int)gen_div_up(Y, a.Q);
+    a.YZ = YZ;
+    a.plan = plan;
+    a.tw2 = tw2;
+    a.S2 = S2;
+    a.K2 = K2;
+    a.scale = scale;
+    return a;
+}
+
+template <bool CO, bool MUL>
+__device__ void dd_z_tile(const DdZ& a, long tile, cdd* sm) {
+    cdd* A = sm;
+    cdd* B = sm + a.Q * a.ls;
+    const int kx = (int)(tile / a.ntiles_y);
+    const int y0 = (int)(tile - (long)kx * a.ntiles_y) * a.Q;
+    const int nq = min(a.Q, a.Y - y0);
+    const long base = (long)kx * a.YZ + y0;
+    const int n = a.Z * a.Q;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int z = t / a.Q, q = t - z * a.Q;
+        cdd v = czero_dd();
+        if (q < nq) v = CO ? cdd_load_cg(a.S2 + base + (long)z * a.Y + q) : cdd_load(a.S2 + base + (long)z * a.Y + q);
+        A[q * a.ls + z] = v;
+    }
+    __syncthreads();
+    cdd* F = fft_lines_dd<-1>(A, B, a.Q, a.ls, a.plan, a.tw2);
+    cdd* O = F == A ? B : A;
+    if (MUL) {
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int z = t / a.Q, q = t - z * a.Q;
+            if (q < nq) F[q * a.ls + z] = cmul(F[q * a.ls + z], cdd_load_nc(a.K2 + base + (long)z * a.Y + q));
+        }
+        __syncthreads();
+        F = fft_lines_dd<+1>(F, O, a.Q, a.ls, a.plan, a.tw2);
+    }
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int z = t / a.Q, q = t - z * a.Q;
+        if (q < nq) {
+            cdd v = F[q * a.ls + z];
+            if (!MUL) v = cdd{dd_mul(v.re, a.scale), dd_mul(v.im, a.scale)};
+            cdd_store(a.S2 + base + (long)z * a.Y + q, v);
+        }
+    }
+}
+
+}  // namespace mvd

@@ -5,7 +5,7 @@
 // the axis length allows.
 #include <type_traits>
 
-#include "fft_fast.cuh"
+#include "fft_fast_tiles.cuh"
 
 namespace mvd {
 
@@ -15,217 +15,35 @@ constexpr int kThreads = 256;
 
 inline int div_up(long a, long b) { return (int)((a + b - 1) / b); }
 
-// ---------------------------------------------------------------------------
-// y pass: Xh*Z contiguous lines of length Y; lines of one warp are adjacent
-// ---------------------------------------------------------------------------
 template <int L, int S>
 __global__ void __launch_bounds__(kThreads) k_y_fast(float2* __restrict__ spec, long nlines,
                                                      const float2* __restrict__ tw) {
-    using F = LineFFT<L, S, true>;
-    constexpr int TPL = F::TPL;
-    constexpr int LPC = kThreads / TPL;
     extern __shared__ float2 sm[];
-    const int li = threadIdx.x / TPL, t = threadIdx.x - li * TPL;
-    const long line = (long)blockIdx.x * LPC + li;
-    const bool ok = line < nlines;
-    float2* g = spec + line * L;
-    float2 v[kE];
-#pragma unroll
-    for (int q = 0; q < kE; ++q) v[q] = ok ? g[t + TPL * q] : make_float2(0.f, 0.f);
-    F::run(v, sm + li * line_stride(L), t, tw);
-    if (ok) {
-#pragma unroll
-        for (int q = 0; q < kE; ++q) g[t + TPL * q] = v[q];
-    }
+    fast_y_tile<L, S, false>(spec, nlines, tw, blockIdx.x, sm);
 }
 
-// ---------------------------------------------------------------------------
-// z pass: Q lines (consecutive y) of one kx plane; thread = q + Q * t so each
-// warp reads rows of consecutive y
-// ---------------------------------------------------------------------------
 template <int L>
 __host__ __device__ constexpr int z_q() {
-    return (kThreads / (L / kE)) >= 8 ? kThreads / (L / kE) : 8;
+    return fast_z_cols(L);
 }
 
 template <int L, bool MUL>
 __global__ void __launch_bounds__(512) k_z_fast(float2* __restrict__ spec, const float2* __restrict__ K, int Y,
                                                  long YZ, int ntiles_y, float scale, const float2* __restrict__ tw) {
-    constexpr int TPL = L / kE;
-    constexpr int Q = z_q<L>();
     extern __shared__ float2 sm[];
-    const int q = threadIdx.x % Q, t = threadIdx.x / Q;
-    const int kx = blockIdx.x / ntiles_y;
-    const int y0 = (blockIdx.x - kx * ntiles_y) * Q;
-    const bool ok = y0 + q < Y;
-    const long base = (long)kx * YZ + y0 + q;
-    float2* line_sm = sm + q * line_stride(L);
-    float2 v[kE];
-#pragma unroll
-    for (int i = 0; i < kE; ++i) v[i] = ok ? spec[base + (long)(t + TPL * i) * Y] : make_float2(0.f, 0.f);
-    LineFFT<L, -1, false>::run(v, line_sm, t, tw);
-    if (MUL) {
-#pragma unroll
-        for (int i = 0; i < kE; ++i) {
-            const float2 k = ok ? __ldg(K + base + (long)(t + TPL * i) * Y) : make_float2(0.f, 0.f);
-            v[i] = cmul(v[i], k);
-        }
-        __syncthreads();  // the exchange buffer is reused by the inverse transform
-        LineFFT<L, +1, false>::run(v, line_sm, t, tw);
-    } else {
-#pragma unroll
-        for (int i = 0; i < kE; ++i) v[i] = cscale(v[i], scale);
-    }
-    if (ok) {
-#pragma unroll
-        for (int i = 0; i < kE; ++i) spec[base + (long)(t + TPL * i) * Y] = v[i];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// x passes: P pairs of rows per block (rows rho0+p and rho0+P+p form pair p)
-// ---------------------------------------------------------------------------
-struct XFast {
-    const float* src;
-    float2* spec;
-    const float* phi;
-    float* psi;
-    long YZ;
-    float eps;
-    const float2* tw;
-};
-
-// write the packed forward spectra (natural order in registers) as the two
-// half spectra of each pair, coalesced over rows
-template <int L>
-__device__ __forceinline__ void x_store_halves(const XFast& a, float2 (&v)[kE], float2* sm, int p, int t, long rho0,
-                                               int nrows) {
-    constexpr int TPL = L / kE, P = kThreads / TPL, LS = line_stride(L), XH = L / 2 + 1;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kE; ++q) sm[p * LS + pad16(t + TPL * q)] = v[q];
-    __syncthreads();
-    constexpr int NTOT = XH * 2 * P, NIT = (NTOT + kThreads - 1) / kThreads;
-#pragma unroll
-    for (int i = 0; i < NIT; ++i) {
-        const int idx = threadIdx.x + i * kThreads;
-        const int k = idx / (2 * P), row = idx - k * 2 * P;
-        if (idx >= NTOT || row >= nrows) continue;
-        const int pp = row < P ? row : row - P;
-        const float2 zk = sm[pp * LS + pad16(k)];
-        const float2 zm = cconj(sm[pp * LS + pad16(k == 0 ? 0 : L - k)]);
-        float2 val;
-        if (row < P) {
-            val = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
-        } else {
-            const float2 d = csub(zk, zm);
-            val = make_float2(0.5f * d.y, -0.5f * d.x);
-        }
-        a.spec[(long)k * a.YZ + rho0 + row] = val;
-    }
-}
-
-// read both half spectra of each pair and build Z = A + i B (natural order)
-template <int L>
-__device__ __forceinline__ void x_load_packed(const XFast& a, float2 (&v)[kE], float2* sm, int p, int t, long rho0,
-                                              int nrows) {
-    constexpr int TPL = L / kE, P = kThreads / TPL, LS = line_stride(L), XH = L / 2 + 1;
-    constexpr int NTOT = XH * 2 * P, NIT = (NTOT + kThreads - 1) / kThreads;
-    // rows < P -> line p (A), rows >= P -> line P + p (B); all loads of a
-    // thread are issued before the first shared-memory store
-    float2 tmp[NIT];
-#pragma unroll
-    for (int i = 0; i < NIT; ++i) {
-        const int idx = threadIdx.x + i * kThreads;
-        const int k = idx / (2 * P), row = idx - k * 2 * P;
-        tmp[i] = (idx < NTOT && row < nrows) ? a.spec[(long)k * a.YZ + rho0 + row] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int i = 0; i < NIT; ++i) {
-        const int idx = threadIdx.x + i * kThreads;
-        const int k = idx / (2 * P), row = idx - k * 2 * P;
-        if (idx < NTOT) sm[row * LS + pad16(k)] = tmp[i];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kE; ++q) {
-        const int k = t + TPL * q;
-        if (k <= L / 2) {
-            const float2 A = sm[p * LS + pad16(k)], B = sm[(P + p) * LS + pad16(k)];
-            v[q] = make_float2(A.x - B.y, A.y + B.x);
-        } else {
-            const float2 A = sm[p * LS + pad16(L - k)], B = sm[(P + p) * LS + pad16(L - k)];
-            v[q] = make_float2(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
-        }
-    }
-    __syncthreads();
+    fast_z_tile<L, MUL, false>(spec, K, Y, YZ, ntiles_y, scale, tw, blockIdx.x, sm);
 }
 
 template <int L>
 __global__ void __launch_bounds__(kThreads) k_x_forward_fast(XFast a) {
-    constexpr int TPL = L / kE, P = kThreads / TPL, LS = line_stride(L);
     extern __shared__ float2 sm[];
-    const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
-    const long rho0 = (long)blockIdx.x * 2 * P;
-    const int nrows = (int)min((long)2 * P, a.YZ - rho0);
-    const bool oka = p < nrows, okb = P + p < nrows;
-    const float* ra = a.src + (rho0 + p) * L;
-    const float* rb = a.src + (rho0 + P + p) * L;
-    float2 v[kE];
-#pragma unroll
-    for (int q = 0; q < kE; ++q) {
-        const int n = t + TPL * q;
-        v[q] = make_float2(oka ? __ldg(ra + n) : 0.f, okb ? __ldg(rb + n) : 0.f);
-    }
-    LineFFT<L, -1, true>::run(v, sm + p * LS, t, a.tw);
-    x_store_halves<L>(a, v, sm, p, t, rho0, nrows);
+    fast_x_forward_tile<L, false>(a, blockIdx.x, sm);
 }
 
 template <int L, int MODE>  // MODE 0: ratio -> forward ; 1: psi update ; 2: plain real output
 __global__ void __launch_bounds__(kThreads) k_x_inverse_fast(XFast a) {
-    constexpr int TPL = L / kE, P = kThreads / TPL, LS = line_stride(L);
     extern __shared__ float2 sm[];
-    const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
-    const long rho0 = (long)blockIdx.x * 2 * P;
-    const int nrows = (int)min((long)2 * P, a.YZ - rho0);
-    const bool oka = p < nrows, okb = P + p < nrows;
-    float2 v[kE];
-    x_load_packed<L>(a, v, sm, p, t, rho0, nrows);
-    const long ra = (rho0 + p) * L, rb = (rho0 + P + p) * L;
-    // the epilogue's operand rows (phi for the ratio, psi for the update) are
-    // fetched now so that their loads overlap the inverse transform
-    float2 w[kE];
-    if (MODE < 2) {
-        const float* src = MODE == 0 ? a.phi : a.psi;
-#pragma unroll
-        for (int q = 0; q < kE; ++q) {
-            const int n = t + TPL * q;
-            w[q] = make_float2(oka ? src[ra + n] : 0.f, okb ? src[rb + n] : 0.f);
-        }
-    }
-    LineFFT<L, +1, true>::run(v, sm + p * LS, t, a.tw);
-    if (MODE == 0) {
-#pragma unroll
-        for (int q = 0; q < kE; ++q) {
-            const float xa = oka ? w[q].x / fmaxf(v[q].x, a.eps) : 0.f;
-            const float xb = okb ? w[q].y / fmaxf(v[q].y, a.eps) : 0.f;
-            v[q] = make_float2(xa, xb);
-        }
-        LineFFT<L, -1, true>::run(v, sm + p * LS, t, a.tw);
-        x_store_halves<L>(a, v, sm, p, t, rho0, nrows);
-    } else {
-#pragma unroll
-        for (int q = 0; q < kE; ++q) {
-            const int n = t + TPL * q;
-            if (MODE == 1) {
-                if (oka) a.psi[ra + n] = fmaxf(w[q].x * v[q].x, a.eps);
-                if (okb) a.psi[rb + n] = fmaxf(w[q].y * v[q].y, a.eps);
-            } else {
-                if (oka) a.psi[ra + n] = v[q].x;
-                if (okb) a.psi[rb + n] = v[q].y;
-            }
-        }
-    }
+    fast_x_inverse_tile<L, MODE, false>(a, blockIdx.x, sm);
 }
 
 // ---------------------------------------------------------------------------

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dd.cuh"
 
 namespace mvd {
 
@@ -53,8 +54,9 @@ std::vector<cudaEvent_t> g_pool;
 size_t g_pool_used = 0;
 thread_local int t_open_cls = -1;
 thread_local cudaEvent_t t_open_ev = nullptr;
-const char* kClassNames[KC_COUNT] = {"x_forward", "y", "z_mul", "x_ratio", "x_update",
-                                     "direct_ratio", "direct_update", "setup"};
+const char* kClassNames[KC_COUNT] = {"x_forward", "y",        "z_mul",        "x_ratio",
+                                     "x_update",  "direct_ratio", "direct_update", "dd_x_forward",
+                                     "dd_y",      "dd_z_mul", "dd_x_ratio",   "setup"};
 
 cudaEvent_t next_event() {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -164,6 +166,9 @@ void free_fft(mvd_ctx* c) {
     dev_free(c->d_tw);
     dev_free(c->d_S);
     dev_free(c->d_K);
+    dev_free(c->d_tw2);
+    dev_free(c->d_S2);
+    dev_free(c->d_KP2);
 }
 
 void free_all(mvd_ctx* c) {
@@ -234,14 +239,45 @@ mvd_status setup_fft(mvd_ctx* c) {
     g.pz.tw = c->d_tw + g.X + g.Y;
     const size_t ns = (size_t)g.Xh * g.YZ;
     MVD_TRY(dev_alloc(&c->d_S, ns, "work spectrum"));
-    MVD_TRY(dev_alloc(&c->d_K, ns * 2 * c->nv, "kernel spectra"));
-    // spectra of P_v (slot 2v) and of P_v^comp (slot 2v+1), scaled by 1/M
+    const int nk = c->precise ? c->nv : 2 * c->nv;
+    MVD_TRY(dev_alloc(&c->d_K, ns * nk, "kernel spectra"));
     const float inv_m = (float)(1.0 / (double)c->M);
+    if (c->precise) {
+        // double-float twiddles: hi = fl32(w), lo = fl32(w - hi), w in FP64
+        std::vector<float4> tw2((size_t)g.X + g.Y + g.Z);
+        size_t o = 0;
+        for (int a = 0; a < 3; ++a) {
+            for (int m = 0; m < Ls[a]; ++m) {
+                const double ang = -2.0 * M_PI * (double)m / (double)Ls[a];
+                const double cr = std::cos(ang), ci = std::sin(ang);
+                const float rh = (float)cr, ih = (float)ci;
+                tw2[o + m] = make_float4(rh, (float)(cr - rh), ih, (float)(ci - ih));
+            }
+            o += Ls[a];
+        }
+        MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_tw2), tw2.size(), "double-float twiddle tables"));
+        MVD_CUDA(cudaMemcpyAsync(c->d_tw2, tw2.data(), tw2.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                                 c->stream));
+        g.tw2x = c->d_tw2;
+        g.tw2y = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + g.X);
+        g.tw2z = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + g.X + g.Y);
+        MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_S2), ns, "double-float work spectrum"));
+        MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_KP2), ns * c->nv, "double-float PSF spectra"));
+    }
+    // kernel spectra, scaled by 1/M: fast mode slot 2v = P_v, 2v+1 = P_v^comp;
+    // precise mode slot v = P_v^comp (FP32) and the double-float P_v
     for (int v = 0; v < c->nv; ++v) {
         for (int which = 0; which < 2; ++which) {
             const float* k = (which == 0 ? c->d_psf : c->d_comp) + c->koff[v];
-            float2* dst = c->d_K + ns * (2 * v + which);
             MVD_TRY(place_kernel(c->dims, k, &c->kd[3 * v], c->d_r, c->stream));
+            if (c->precise && which == 0) {
+                cdd* dst = reinterpret_cast<cdd*>(reinterpret_cast<float4*>(c->d_KP2) + ns * v);
+                MVD_TRY(dd_forward_real(g, c->d_r, dst, c->stream));
+                MVD_TRY(dd_y(g, dst, 0, c->stream));
+                MVD_TRY(dd_z_forward_scaled(g, dst, 1.0 / (double)c->M, c->stream));
+                continue;
+            }
+            float2* dst = c->d_K + ns * (c->precise ? v : 2 * v + which);
             MVD_TRY(fft_forward_real(g, c->d_r, dst, c->stream));
             MVD_TRY(fft_y(g, dst, 0, c->stream));
             MVD_TRY(fft_z_forward_scaled(g, dst, inv_m, c->stream));
@@ -259,6 +295,20 @@ mvd_status one_update(mvd_ctx* c, int v) {
     }
     const FftGeom& g = c->geom;
     const size_t ns = (size_t)g.Xh * g.YZ;
+    if (c->precise) {
+        cdd* S2 = c->d_S2;
+        const cdd* Kp2 = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_KP2) + ns * v);
+        const float2* Kc = c->d_K + ns * v;
+        MVD_TRY(dd_forward_real(g, c->d_psi, S2, c->stream));
+        MVD_TRY(dd_y(g, S2, 0, c->stream));
+        MVD_TRY(dd_z_mul(g, S2, Kp2, c->stream));
+        MVD_TRY(dd_y(g, S2, 1, c->stream));
+        MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->d_S, c->stream));
+        MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
+        MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
+        MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
+        return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream);
+    }
     const float2* Kp = c->d_K + ns * (2 * v);
     const float2* Kc = c->d_K + ns * (2 * v + 1);
     MVD_TRY(fft_forward_real(g, c->d_psi, c->d_S, c->stream));
@@ -289,6 +339,7 @@ void mvd_default_options(mvd_options* opt) {
     opt->stream = nullptr;
     opt->views_on_device = 0;
     opt->device = -1;
+    opt->precision = MVD_PRECISE;
 }
 
 const char* mvd_last_error(void) { return t_err.c_str(); }
@@ -340,6 +391,10 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1) {
         set_error("mvd_create: dims must be >= 1");
         return MVD_ERR_SHAPE;
+    }
+    if (opt.precision != MVD_PRECISE && opt.precision != MVD_FAST) {
+        set_error("mvd_create: unknown precision %d", opt.precision);
+        return MVD_ERR_ARG;
     }
     if (opt.path < MVD_PATH_AUTO || opt.path > MVD_PATH_FFT) {
         set_error("mvd_create: unknown path %d", opt.path);
@@ -405,6 +460,7 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     c->koff = koff;
     c->ktotal = ktotal;
     c->path_opt = opt.path;
+    c->precise = opt.precision == MVD_PRECISE ? 1 : 0;
 
     auto fail = [&](mvd_status st) {
         cudaStreamSynchronize(c->stream);

@@ -28,7 +28,8 @@ PATHS = {"auto": MVD_PATH_AUTO, "direct": MVD_PATH_DIRECT, "fft": MVD_PATH_FFT}
 EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_set_estimate", "mvd_iterate",
            "mvd_result", "mvd_result_device", "mvd_synchronize", "mvd_destroy", "mvd_last_error",
            "mvd_get_eps", "mvd_get_psi0", "mvd_get_path", "mvd_get_compound_kernel", "mvd_launch_count",
-           "mvd_profile_enable", "mvd_profile_read", "mvd_update_direct_noalloc"]
+           "mvd_profile_enable", "mvd_profile_read", "mvd_update_direct_noalloc", "mvd_batch_create",
+           "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy"]
 
 
 class MvdError(RuntimeError):
@@ -38,9 +39,13 @@ class MvdError(RuntimeError):
         self.status = status
 
 
+MVD_PRECISE, MVD_FAST = 0, 1
+PRECISIONS = {"precise": MVD_PRECISE, "fast": MVD_FAST}
+
+
 class Options(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("path", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("views_on_device", ctypes.c_int), ("device", ctypes.c_int)]
+                ("views_on_device", ctypes.c_int), ("device", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 _lib = None
@@ -85,6 +90,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_update_direct_noalloc.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ci), ctypes.POINTER(ci),
                                               ctypes.c_float, vp]
     lib.mvd_update_direct_noalloc.restype = ci
+    lib.mvd_batch_create.argtypes = [ctypes.POINTER(vp), ci, ci, ctypes.POINTER(vp)]
+    lib.mvd_batch_create.restype = ci
+    lib.mvd_batch_run.argtypes = [vp]
+    lib.mvd_batch_run.restype = ci
+    lib.mvd_batch_wait.argtypes = [vp]
+    lib.mvd_batch_wait.restype = ci
+    lib.mvd_batch_tasks.argtypes = [vp]
+    lib.mvd_batch_tasks.restype = ctypes.c_longlong
+    lib.mvd_batch_destroy.argtypes = [vp]
+    lib.mvd_batch_destroy.restype = None
     for name in ("mvd_create", "mvd_precompute_kernels", "mvd_set_estimate", "mvd_iterate", "mvd_result",
                  "mvd_result_device", "mvd_synchronize", "mvd_get_compound_kernel"):
         getattr(lib, name).restype = ci
@@ -127,7 +142,8 @@ def mvd_profile_read() -> dict:
     return {names[i].decode(): (int(cnt[i]), float(ms[i])) for i in range(k)}
 
 
-def mvd_create(views, psfs, dims=None, eps: float = 0.0, path="auto", stream=None, device: int = -1):
+def mvd_create(views, psfs, dims=None, eps: float = 0.0, path="auto", stream=None, device: int = -1,
+               precision="precise"):
     """Creates a context (see mvd_create in include/mvd.h); returns its handle.
 
     ``views``: list of float32 arrays ``[Z][Y][X]`` (numpy on the host, or CUDA
@@ -158,6 +174,7 @@ def mvd_create(views, psfs, dims=None, eps: float = 0.0, path="auto", stream=Non
         opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     opt.views_on_device = 1 if on_dev else 0
     opt.device = int(device)
+    opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     h = ctypes.c_void_p()
     _check(lib.mvd_create((ctypes.c_void_p * len(ptrs))(*ptrs), len(ptrs),
                           (ctypes.c_void_p * len(hp))(*[ctypes.c_void_p(p.ctypes.data) for p in hp]),
@@ -244,13 +261,39 @@ def mvd_update_direct_noalloc(psi, phi, psf, comp, eps: float, stream=None):
     _check(load().mvd_update_direct_noalloc(ptr(psi), ptr(phi), ptr(psf), ptr(comp), dims, kd, float(eps), st))
 
 
+def mvd_batch_create(ctxs, n_iter: int):
+    """Batch over context handles (all FFT-engine, one device, one stream)."""
+    arr = (ctypes.c_void_p * len(ctxs))(*[c if isinstance(c, ctypes.c_void_p) else c.ctx for c in ctxs])
+    h = ctypes.c_void_p()
+    _check(load().mvd_batch_create(arr, len(ctxs), int(n_iter), ctypes.byref(h)))
+    return h
+
+
+def mvd_batch_run(batch):
+    _check(load().mvd_batch_run(batch))
+
+
+def mvd_batch_wait(batch):
+    _check(load().mvd_batch_wait(batch))
+
+
+def mvd_batch_tasks(batch) -> int:
+    return int(load().mvd_batch_tasks(batch))
+
+
+def mvd_batch_destroy(batch):
+    if batch:
+        load().mvd_batch_destroy(batch)
+
+
 class Deconvolver:
     """Owns one context: ``with Deconvolver(views, psfs) as d: d.iterate(10); psi = d.result()``."""
 
-    def __init__(self, views, psfs, variant="efficient", eps=0.0, path="auto", stream=None, device=-1):
+    def __init__(self, views, psfs, variant="efficient", eps=0.0, path="auto", stream=None, device=-1,
+                 precision="precise"):
         self.shape = tuple(views[0].shape)
         self.psf_shapes = [tuple(p.shape) for p in psfs]
-        self.ctx = mvd_create(views, psfs, eps=eps, path=path, stream=stream, device=device)
+        self.ctx = mvd_create(views, psfs, eps=eps, path=path, stream=stream, device=device, precision=precision)
         try:
             mvd_precompute_kernels(self.ctx, variant)
         except Exception:

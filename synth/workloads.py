@@ -224,8 +224,15 @@ def blur_circular(vol: np.ndarray, psf: np.ndarray) -> np.ndarray:
     return np.maximum(out, 0.0)
 
 
+def _as_stored(p):
+    """The PSF as the deconvolution receives it: rounded to FP32. Imaging with
+    these values (not the FP64 samples, whose last bits depend on the platform's
+    exp) keeps the generated inputs identical across platforms."""
+    return np.asarray(p, dtype=np.float32).astype(np.float64)
+
+
 def _observe(rng, truth, psfs):
-    blurred = [blur_circular(truth, p) for p in psfs]
+    blurred = [blur_circular(truth, _as_stored(p)) for p in psfs]
     views = [rng.poisson(b).astype(np.float32) for b in blurred]
     return views
 
@@ -244,7 +251,7 @@ def _spim_psfs(n_views, sigma_xy, sigma_ax, box, angles=None):
 
 
 def _scale_to_peak(truth, psfs, peak):
-    m = max(blur_circular(truth, p).max() for p in psfs)
+    m = max(blur_circular(truth, _as_stored(p)).max() for p in psfs)
     return truth * (peak / m)
 
 
@@ -287,17 +294,36 @@ def config3(seed: int = 1003, dims=(1024, 1024, 512), n_objects=150_000) -> Work
                    angles=angles)
 
 
-def config4(seed: int = 1004, n_volumes: int = 48):
-    """48 independent volumes: log-uniform sizes, 2-6 views, peak 50-300 photons."""
+def config4_layout(seed: int = 1004, n_volumes: int = 48):
+    """Sizes, view counts and peak photon counts of the batched volumes.
+
+    Each axis is drawn log-uniformly (x, y in [48, 320], z in [48, 192]) and
+    rounded to the nearest {2,3,5}-smooth integer; views U{2..6}; peak
+    U(50, 300) photons.
+    """
     rng = np.random.default_rng(seed)
     out = []
-    for b in range(n_volumes):
+    for _ in range(n_volumes):
         X = smooth235(int(round(math.exp(rng.uniform(math.log(48), math.log(320))))))
         Y = smooth235(int(round(math.exp(rng.uniform(math.log(48), math.log(320))))))
         Z = smooth235(int(round(math.exp(rng.uniform(math.log(48), math.log(192))))))
-        n_views = int(rng.integers(2, 7))
-        peak = float(rng.uniform(50.0, 300.0))
-        dims = (X, Y, Z)
+        out.append(((X, Y, Z), int(rng.integers(2, 7)), float(rng.uniform(50.0, 300.0))))
+    return out
+
+
+def config4(seed: int = 1004, n_volumes: int = 48, only=None):
+    """48 independent volumes: log-uniform sizes, 2-6 views, peak 50-300 photons.
+
+    ``only``: indices of the volumes to generate (default all); volume b's
+    objects and noise use ``default_rng([seed, b])`` so any subset is
+    reproducible on its own.
+    """
+    out = []
+    for b, (dims, n_views, peak) in enumerate(config4_layout(seed, n_volumes)):
+        if only is not None and b not in only:
+            continue
+        rng = np.random.default_rng([seed, b])
+        X, Y, Z = dims
         # object density as in the 256x256x128 case (3000 per 8.4e6 voxels)
         n_obj = max(8, int(round(3000 * X * Y * Z / (256 * 256 * 128))))
         truth = ellipsoids_truth(rng, dims, n_obj, (3.0, 6.0), (0.5, 1.0))

@@ -44,6 +44,7 @@ def test_default_options(lib):
     o = mvd.Options()
     lib.mvd_default_options(ctypes.byref(o))
     assert o.eps == 0.0 and o.path == 0 and o.stream is None and o.views_on_device == 0 and o.device == -1
+    assert o.precision == mvd.MVD_PRECISE
 
 
 def _good():

@@ -1,0 +1,149 @@
+"""Batched form: many volumes of uneven size and view count in one persistent
+launch, against per-volume runs and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._util import PARITY_TOL, err_report, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1308_0730_gb300 import mvd
+
+    mvd.load()
+    return torch, mvd
+
+
+SPECS = [  # dims, boxes (one per view)
+    ((48, 40, 36), [(5, 7, 9), (9, 7, 5), (7, 5, 5)]),
+    ((30, 64, 27), [(7, 5, 9), (5, 9, 7)]),
+    ((24, 20, 45), [(5, 5, 11), (11, 5, 5), (5, 11, 5), (7, 7, 7)]),
+    ((75, 18, 32), [(9, 5, 5), (5, 5, 9)]),
+    ((16, 16, 16), [(3, 5, 7), (7, 5, 3), (5, 3, 5)]),
+]
+
+
+def _workloads(seed=500, n_iter=3):
+    return [synth.small_case(seed + i, dims=d, n_views=len(b), boxes=b, n_iter=n_iter, asymmetric=True)
+            for i, (d, b) in enumerate(SPECS)]
+
+
+def test_batch_matches_per_volume_runs_and_oracle(env):
+    torch, mvd = env
+    ws = _workloads()
+    s = torch.cuda.Stream()
+    plain = []
+    for w in ws:
+        with mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", stream=s) as d:
+            d.iterate(w.n_iter)
+            plain.append(d.result())
+    ds = [mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", stream=s) for w in ws]
+    try:
+        b = mvd.mvd_batch_create(ds, ws[0].n_iter)
+        try:
+            assert mvd.mvd_batch_tasks(b) > 0
+            mvd.mvd_batch_run(b)
+            mvd.mvd_batch_wait(b)
+            got = [d.result() for d in ds]
+            # a second run continues from the current estimates
+            mvd.mvd_batch_run(b)
+            mvd.mvd_batch_wait(b)
+            got2 = [d.result() for d in ds]
+        finally:
+            mvd.mvd_batch_destroy(b)
+    finally:
+        for d in ds:
+            d.close()
+    for w, g, p in zip(ws, got, plain):
+        assert rel_err(g, p) < PARITY_TOL, f"{w.name}: {err_report(g, p)}"
+    for i in (0, 3, 4):
+        w = ws[i]
+        want, _ = oracle.deconvolve(w.views, w.psfs, w.n_iter, "efficient")
+        assert rel_err(got[i], want) < PARITY_TOL, f"{w.name}: {err_report(got[i], want)}"
+        want2, _ = oracle.deconvolve(w.views, w.psfs, 2 * w.n_iter, "efficient")
+        assert rel_err(got2[i], want2) < PARITY_TOL, f"{w.name} (second run): {err_report(got2[i], want2)}"
+
+
+def test_batch_rejects_bad_contexts(env):
+    torch, mvd = env
+    ws = _workloads()[:2]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with mvd.Deconvolver(ws[0].views, ws[0].psfs, path="fft", stream=s1) as a, \
+            mvd.Deconvolver(ws[1].views, ws[1].psfs, path="fft", stream=s2) as b, \
+            mvd.Deconvolver(ws[1].views, ws[1].psfs, path="direct", stream=s1) as c:
+        with pytest.raises(mvd.MvdError) as ei:
+            mvd.mvd_batch_create([a, b], 1)
+        assert ei.value.status == mvd.MVD_ERR_ARG
+        with pytest.raises(mvd.MvdError) as ei:
+            mvd.mvd_batch_create([a, c], 1)
+        assert ei.value.status == mvd.MVD_ERR_UNSUPPORTED
+
+
+def test_batch_wait_times_out_and_context_stays_usable(env, monkeypatch):
+    """A dependency that nothing satisfies (test hook) makes one block's bounded wait run
+    out: the batch reports MVD_ERR_TIMEOUT, and the contexts keep working afterwards."""
+    torch, mvd = env
+    ws = _workloads()[:3]
+    s = torch.cuda.Stream()
+    monkeypatch.setenv("MVD_BATCH_STALL_ENTRY", "4")
+    monkeypatch.setenv("MVD_BATCH_POLL_LIMIT", "20000")
+    ds = [mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", stream=s) for w in ws]
+    try:
+        b = mvd.mvd_batch_create(ds, 1)
+        try:
+            mvd.mvd_batch_run(b)
+            with pytest.raises(mvd.MvdError) as ei:
+                mvd.mvd_batch_wait(b)
+            assert ei.value.status == mvd.MVD_ERR_TIMEOUT
+        finally:
+            mvd.mvd_batch_destroy(b)
+        w = ws[0]
+        ds[0].set_estimate(None)
+        ds[0].iterate(2)
+        got = ds[0].result()
+        want, _ = oracle.deconvolve(w.views, w.psfs, 2, "efficient")
+        assert rel_err(got, want) < PARITY_TOL
+    finally:
+        for d in ds:
+            d.close()
+
+
+def test_batched_volumes_of_the_48_volume_workload_match_oracle(env):
+    """Three of the 48 batched volumes (all-generic 48x60x60 with 5 views; 100x128x54 with 5
+    views and 128x72x81 with 2 views, which have power-of-two axes), 15 iterations, against the
+    FP64 oracle at 1e-4: per volume and inside one batch."""
+    torch, mvd = env
+    ws = synth.config4(only=[0, 36, 19])
+    s = torch.cuda.Stream()
+    ds = [mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", stream=s) for w in ws]
+    try:
+        plain = []
+        for d, w in zip(ds, ws):
+            d.iterate(w.n_iter)
+            plain.append(d.result())
+            d.set_estimate(None)
+        b = mvd.mvd_batch_create(ds, ws[0].n_iter)
+        try:
+            mvd.mvd_batch_run(b)
+            mvd.mvd_batch_wait(b)
+        finally:
+            mvd.mvd_batch_destroy(b)
+        batched = [d.result() for d in ds]
+    finally:
+        for d in ds:
+            d.close()
+    for w, p, q in zip(ws, plain, batched):
+        want, _ = oracle.deconvolve(w.views, w.psfs, w.n_iter, "efficient")
+        assert rel_err(p, want) < PARITY_TOL, f"{w.name} per volume: {err_report(p, want)}"
+        assert rel_err(q, want) < PARITY_TOL, f"{w.name} batched: {err_report(q, want)}"

@@ -300,3 +300,32 @@ def test_graph_replay_matches_plain_launches(mvd, monkeypatch):
     for path in ("fft", "direct"):
         assert np.array_equal(out["graph", path], out["plain", path]), path
         assert rel_err(out["graph", path], want) < PARITY_TOL, err_report(out["graph", path], want)
+
+
+def test_mid_volume_full_run_against_stored_oracle(mvd, cfg2):
+    """256x256x128, 4 views, 20 iterations, compared with the FP64 oracle's final estimate at
+    4096 seeded voxels (tests/golden/oracle_samples_mid.txt, written by
+    tests/golden/make_oracle_samples.py from the oracle alone)."""
+    from tests.golden.make_oracle_samples import input_digest, read
+
+    digest, eps, max_abs, idx, want = read("mid")
+    w = cfg2
+    assert input_digest(w) == digest, "the input generator produced different inputs on this machine"
+    got, used, geps = _run_gpu(mvd, w, path="fft")
+    assert abs(geps - eps) <= 1e-6 * eps
+    g = got.ravel()[idx]
+    tau = 1e-3 * max_abs
+    err = float(np.max(np.abs(g - want) / np.maximum(np.abs(want), tau)))
+    assert err < PARITY_TOL, f"max rel err {err:.3e} at sampled voxels"
+
+
+def test_fast_fp32_mode(mvd):
+    """MVD_FAST (everything in FP32): few iterations stay at 1e-4; the documented cost of FP32
+    is slow growth of dim-voxel error with the iteration count."""
+    w = synth.small_case(61, dims=(48, 40, 36), n_views=3, boxes=[(7, 5, 9), (9, 7, 5), (5, 9, 7)], n_iter=2,
+                         asymmetric=True)
+    want, _ = oracle.deconvolve(w.views, w.psfs, 2, "efficient")
+    with mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", precision="fast") as d:
+        d.iterate(2)
+        got = d.result()
+    assert rel_err(got, want) < PARITY_TOL, err_report(got, want)
