@@ -39,9 +39,17 @@ L2_BYTES = 129 * 2 ** 20
 
 # algorithmic bytes per voxel for each update kernel: every input and output
 # array it must touch, once (half spectrum = 8 * (X/2+1) * Y * Z bytes)
-def _kernel_bytes(X, Y, Z):
+def _kernel_bytes(X, Y, Z, precise=True):
     M = X * Y * Z
     spec = 8 * (X // 2 + 1) * Y * Z  # FP32 half spectrum; double-float is 2 * spec
+    if precise:  # the update reads the double-float spectrum
+        return {
+            "dd_x_forward": 4 * M + 2 * spec,       # read psi, write S2
+            "dd_y": 4 * spec,                       # read S2, write S2
+            "dd_z_mul": 6 * spec,                   # read S2 and a double-float kernel spectrum, write S2
+            "dd_x_ratio": 4 * spec + 4 * M,         # read S2 and phi, write S2
+            "x_update": 2 * spec + 8 * M,           # read S2, read and write psi
+        }
     return {
         "x_forward": 4 * M + spec,          # read psi, write S
         "y": 2 * spec,                      # read S, write S
@@ -50,10 +58,6 @@ def _kernel_bytes(X, Y, Z):
         "x_update": spec + 8 * M,           # read S and psi, write psi
         "direct_ratio": 12 * M,             # read psi and phi, write r
         "direct_update": 12 * M,            # read r and psi, write psi
-        "dd_x_forward": 4 * M + 2 * spec,   # read psi, write S2
-        "dd_y": 4 * spec,                   # read S2, write S2
-        "dd_z_mul": 6 * spec,               # read S2 and the double-float PSF spectrum, write S2
-        "dd_x_ratio": 2 * spec + 4 * M + spec,  # read S2 and phi, write S
     }
 
 
@@ -331,7 +335,7 @@ def run_gpu(args):
             "update_effective_hbm_frac": (12.0 * units_per_step * args.steps / (ms * 1e-3) / 1e9) / peak,
             "kernels": per_kernel,
             "profiled_ms_per_step": ms_profiled / args.steps,
-            "precision": "forward blur in double-float (pairs of FP32), back-projection FP32",
+            "precision": "double-float (pairs of FP32) for the forward blur and the back-projection's y and z passes; FP32 x passes of the back-projection",
             "fast_fp32": {"value": ws * units_per_step * args.steps / (ms_fast * 1e-3) / 1e9, "unit": UNIT,
                           "ms_per_step": ms_fast / args.steps,
                           "max_rel_diff_vs_precise": float(np.max(np.abs(psi_fast.astype(np.float64) - psi_dev)

@@ -85,6 +85,7 @@ __device__ __forceinline__ void with_len(int L, F&& f) {
     }
 }
 
+// precise mode: every pass but the update runs in double-float
 __device__ void run_tile_dd(const VolDesc& d, int pass, int view, long tile, cdd* sm) {
     const size_t ns = (size_t)d.Xh * d.YZ;
     switch (pass) {
@@ -96,23 +97,25 @@ __device__ void run_tile_dd(const VolDesc& d, int pass, int view, long tile, cdd
             break;
         }
         case YF1:
+        case YF2:
             dd_y_tile<true, -1>(dd_y_args(d.Y, d.Xh, d.Z, d.py, d.tw2y, d.S2), tile, sm);
             break;
         case YI1:
+        case YI2:
             dd_y_tile<true, +1>(dd_y_args(d.Y, d.Xh, d.Z, d.py, d.tw2y, d.S2), tile, sm);
             break;
-        case Z1: {
-            const cdd* K2 = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(d.KP2) + ns * view);
+        case Z1:
+        case Z2: {
+            const cdd* K2 = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(d.KP2) +
+                                                         ns * (2 * view + (pass == Z2 ? 1 : 0)));
             dd_z_tile<true, true>(dd_z_args(d.Z, d.Y, d.YZ, d.pz, d.tw2z, d.S2, K2, dd{1.f, 0.f}), tile, sm);
             break;
         }
         default: {  // XR
             DdX a = dd_x_args(d.X, d.YZ, d.px, d.tw2x);
-            a.tw = d.px.tw;
             a.S2 = d.S2;
             a.phi = d.views + (size_t)view * d.M;
             a.eps = d.eps;
-            a.S = d.S;
             dd_x_ratio_tile<true>(a, tile, sm);
             break;
         }
@@ -121,7 +124,7 @@ __device__ void run_tile_dd(const VolDesc& d, int pass, int view, long tile, cdd
 
 __device__ void run_tile(const VolDesc& d, int pass, int view, long tile, float2* sm) {
     const size_t ns = (size_t)d.Xh * d.YZ;
-    if (d.precise && pass <= XR) {
+    if (d.precise && pass != XU) {
         run_tile_dd(d, pass, view, tile, reinterpret_cast<cdd*>(sm));
         return;
     }
@@ -161,7 +164,7 @@ __device__ void run_tile(const VolDesc& d, int pass, int view, long tile, float2
         }
         case Z1:
         case Z2: {
-            const float2* K = d.K + ns * (d.precise ? view : 2 * view + (pass == Z2 ? 1 : 0));
+            const float2* K = d.K + ns * (2 * view + (pass == Z2 ? 1 : 0));
             if (d.fz) {
                 with_len(d.Z, [&](auto Lc) {
                     constexpr int L = decltype(Lc)::value;
@@ -186,13 +189,15 @@ __device__ void run_tile(const VolDesc& d, int pass, int view, long tile, float2
             }
             break;
         }
-        default: {
+        default: {  // XU (in precise mode from the double-float spectrum)
+            const cdd* S2 = d.precise ? d.S2 : nullptr;
             if (d.fx) {
-                const XFast a{nullptr, d.S, nullptr, d.psi, d.YZ, d.eps, d.px.tw};
+                const XFast a{nullptr, d.S, nullptr, d.psi, d.YZ, d.eps, d.px.tw, S2};
                 with_len(d.X, [&](auto Lc) { fast_x_inverse_tile<decltype(Lc)::value, 1, true>(a, tile, sm); });
             } else {
                 GenX a = gen_x_args(d.X, d.YZ, d.px);
                 a.S = d.S;
+                a.S2in = S2;
                 a.psi = d.psi;
                 a.eps = d.eps;
                 gen_x_inverse_tile<true, true>(a, tile, sm);
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(kGenThreads, 2) k_batch(BatchArgs a) {
 
 // tiles of one pass, and elements each tile transforms
 void pass_tiles(const VolDesc& d, int pass, long* ntiles, long* elems) {
-    if (d.precise && pass <= XR) {
+    if (d.precise && pass != XU) {
         switch (pass) {
             case XF:
             case XR:
@@ -260,6 +265,7 @@ void pass_tiles(const VolDesc& d, int pass, long* ntiles, long* elems) {
                 *elems = 2L * dd_x_pairs(d.X) * d.X * 4;  // double-float work counts about 4x
                 return;
             case Z1:
+            case Z2:
                 *ntiles = dd_z_tiles(d.Z, d.Y, d.Xh);
                 *elems = (long)dd_z_cols(d.Z, d.Y) * d.Z * 4;
                 return;

@@ -102,7 +102,9 @@ mvd_status dd_forward_real(const FftGeom& g, const float* src, cdd* S2, cudaStre
 mvd_status dd_y(const FftGeom& g, cdd* S2, int inverse, cudaStream_t st);
 mvd_status dd_z_mul(const FftGeom& g, cdd* S2, const cdd* K2, cudaStream_t st);
 mvd_status dd_z_forward_scaled(const FftGeom& g, cdd* S2, double scale, cudaStream_t st);
-mvd_status dd_x_ratio(const FftGeom& g, const cdd* S2, const float* phi, float eps, float2* S, cudaStream_t st);
+mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cudaStream_t st);
+// update pass reading the double-float spectrum (rounded to FP32)
+mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st);
 
 // register-resident variants for power-of-two lengths (fft_fast.cu)
 bool fft_fast_supported(int L);
@@ -114,6 +116,7 @@ mvd_status fft_z_forward_scaled_fast(const FftGeom& g, float2* S, float scale, c
 mvd_status fft_x_ratio_fast(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
 mvd_status fft_x_update_fast(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st);
 mvd_status fft_inverse_real_fast(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
+mvd_status fft_x_update_dd_fast(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st);
 
 // Direct (spatial) periodic convolution with fused epilogues.
 bool direct_supported(const int kd[3]);
@@ -164,12 +167,12 @@ struct mvd_ctx {
     int precise = 1;         // forward blur in double-float (MVD_PRECISE)
     float2* d_tw = nullptr;  // twiddle tables (x, y, z)
     float2* d_S = nullptr;   // work spectrum Xh*Y*Z
-    // FP32 kernel spectra, each Xh*Y*Z: fast mode 2*nv (P_v, P_v^comp per
-    // view), precise mode nv (P_v^comp only)
+    // kernel spectra, each Xh*Y*Z, slot 2v = P_v and 2v+1 = P_v^comp: FP32
+    // in fast mode (d_K), double-float in precise mode (d_KP2)
     float2* d_K = nullptr;
     mvd::cdd* d_tw2 = nullptr;  // double-float twiddle tables (x, y, z)
     mvd::cdd* d_S2 = nullptr;   // double-float work spectrum (precise mode)
-    mvd::cdd* d_KP2 = nullptr;  // nv double-float spectra of P_v (precise mode)
+    mvd::cdd* d_KP2 = nullptr;  // 2*nv double-float kernel spectra (precise mode)
 
     // one instantiated graph per schedule (one iteration each)
     struct Graph {

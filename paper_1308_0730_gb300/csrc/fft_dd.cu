@@ -1,6 +1,9 @@
 // Kernels and launchers of the double-float forward-blur passes (tile
 // functions in fft_dd.cuh).
+#include <type_traits>
+
 #include "fft_dd.cuh"
+#include "fft_dd_fast.cuh"
 
 namespace mvd {
 
@@ -28,6 +31,65 @@ __global__ void __launch_bounds__(kGenThreads) k_dd_z(DdZ a) {
     dd_z_tile<false, MUL>(a, blockIdx.x, smd);
 }
 
+// register-resident double-float passes (power-of-two lengths)
+template <int L, int S>
+__global__ void __launch_bounds__(kDdThreads) k_ddf_y(cdd* S2, long nlines, const cdd* tw2) {
+    extern __shared__ cdd smd[];
+    ddf_y_tile<L, S, false>(S2, nlines, tw2, blockIdx.x, smd);
+}
+
+template <int L, bool MUL>
+__global__ void __launch_bounds__(512) k_ddf_z(cdd* S2, const cdd* K2, int Y, long YZ, int ntiles_y, dd scale,
+                                               const cdd* tw2) {
+    extern __shared__ cdd smd[];
+    ddf_z_tile<L, MUL, false>(S2, K2, Y, YZ, ntiles_y, scale, tw2, blockIdx.x, smd);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kDdThreads) k_ddf_x_forward(DdXFast a) {
+    extern __shared__ cdd smd[];
+    ddf_x_forward_tile<L, false>(a, blockIdx.x, smd);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kDdThreads) k_ddf_x_ratio(DdXFast a) {
+    extern __shared__ cdd smd[];
+    ddf_x_ratio_tile<L, false>(a, blockIdx.x, smd);
+}
+
+template <typename F>
+bool with_dd_len(int L, F&& f) {
+    switch (L) {
+        case 32: f(std::integral_constant<int, 32>{}); return true;
+        case 64: f(std::integral_constant<int, 64>{}); return true;
+        case 128: f(std::integral_constant<int, 128>{}); return true;
+        case 256: f(std::integral_constant<int, 256>{}); return true;
+        case 512: f(std::integral_constant<int, 512>{}); return true;
+        case 1024: f(std::integral_constant<int, 1024>{}); return true;
+        default: return false;
+    }
+}
+
+template <typename K, typename... Args>
+mvd_status launch_raw(K kern, long grid, int threads, size_t smem, cudaStream_t st, const char* name, int cls,
+                      Args... args) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e, name);
+    prof_begin(cls, st);
+    kern<<<(unsigned)grid, threads, smem, st>>>(args...);
+    prof_end(cls, st);
+    count_launch();
+    return check_launch(name);
+}
+
+DdXFast ddf_args(const FftGeom& g) {
+    DdXFast a{};
+    a.YZ = g.YZ;
+    a.tw2 = g.tw2x;
+    a.plan = g.px;
+    return a;
+}
+
 template <typename K, typename A>
 mvd_status launch(K kern, const A& a, long grid, size_t smem, cudaStream_t st, const char* name, int cls) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -42,34 +104,83 @@ mvd_status launch(K kern, const A& a, long grid, size_t smem, cudaStream_t st, c
 }  // namespace
 
 mvd_status dd_forward_real(const FftGeom& g, const float* src, cdd* S2, cudaStream_t st) {
+    if (g.fast && dd_fast_length(g.X)) {
+        mvd_status rc = MVD_ERR_UNSUPPORTED;
+        DdXFast a = ddf_args(g);
+        a.src = src;
+        a.S2 = S2;
+        with_dd_len(g.X, [&](auto Lc) {
+            constexpr int L = decltype(Lc)::value;
+            rc = launch_raw(k_ddf_x_forward<L>, gen_div_up(g.YZ, 2 * ddf_pairs(L)), kDdThreads, ddf_x_smem(L), st,
+                            "dd x forward (fast)", KC_DD_X_FORWARD, a);
+        });
+        return rc;
+    }
     DdX a = dd_x_args(g.X, g.YZ, g.px, g.tw2x);
     a.src = src;
     a.S2 = S2;
     return launch(k_dd_x_forward, a, dd_x_tiles(g.X, g.YZ), dd_x_smem(g.X), st, "dd x forward", KC_DD_X_FORWARD);
 }
 
-mvd_status dd_x_ratio(const FftGeom& g, const cdd* S2, const float* phi, float eps, float2* S, cudaStream_t st) {
+mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cudaStream_t st) {
+    if (g.fast && dd_fast_length(g.X)) {
+        mvd_status rc = MVD_ERR_UNSUPPORTED;
+        DdXFast a = ddf_args(g);
+        a.S2 = S2;
+        a.phi = phi;
+        a.eps = eps;
+        with_dd_len(g.X, [&](auto Lc) {
+            constexpr int L = decltype(Lc)::value;
+            rc = launch_raw(k_ddf_x_ratio<L>, gen_div_up(g.YZ, 2 * ddf_pairs(L)), kDdThreads, ddf_x_smem(L), st,
+                            "dd x ratio (fast)", KC_DD_X_RATIO, a);
+        });
+        return rc;
+    }
     DdX a = dd_x_args(g.X, g.YZ, g.px, g.tw2x);
-    a.S2 = const_cast<cdd*>(S2);
+    a.S2 = S2;
     a.phi = phi;
     a.eps = eps;
-    a.S = S;
     return launch(k_dd_x_ratio, a, dd_x_tiles(g.X, g.YZ), dd_x_smem(g.X), st, "dd x ratio", KC_DD_X_RATIO);
 }
 
 mvd_status dd_y(const FftGeom& g, cdd* S2, int inverse, cudaStream_t st) {
+    if (g.fast && dd_fast_length(g.Y)) {
+        mvd_status rc = MVD_ERR_UNSUPPORTED;
+        const long nl = (long)g.Xh * g.Z;
+        with_dd_len(g.Y, [&](auto Lc) {
+            constexpr int L = decltype(Lc)::value;
+            rc = launch_raw(inverse ? k_ddf_y<L, +1> : k_ddf_y<L, -1>, gen_div_up(nl, ddf_y_lines(L)), kDdThreads,
+                            ddf_y_smem(L), st, "dd y (fast)", KC_DD_Y, S2, nl, g.tw2y);
+        });
+        return rc;
+    }
     DdY a = dd_y_args(g.Y, g.Xh, g.Z, g.py, g.tw2y, S2);
     return launch(inverse ? k_dd_y<+1> : k_dd_y<-1>, a, dd_y_tiles(g.Y, g.Xh, g.Z), dd_y_smem(g.Y), st, "dd y",
                   KC_DD_Y);
 }
 
+static mvd_status ddf_z(const FftGeom& g, cdd* S2, const cdd* K2, dd scale, bool mul, cudaStream_t st) {
+    mvd_status rc = MVD_ERR_UNSUPPORTED;
+    with_dd_len(g.Z, [&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        constexpr int Q = ddf_z_cols(L);
+        const int threads = Q * (L / kE8);
+        const int nty = (int)gen_div_up(g.Y, Q);
+        rc = launch_raw(mul ? k_ddf_z<L, true> : k_ddf_z<L, false>, (long)g.Xh * nty, threads, ddf_z_smem(L), st,
+                        "dd z (fast)", mul ? KC_DD_Z_MUL : KC_SETUP, S2, K2, g.Y, g.YZ, nty, scale, g.tw2z);
+    });
+    return rc;
+}
+
 mvd_status dd_z_mul(const FftGeom& g, cdd* S2, const cdd* K2, cudaStream_t st) {
+    if (g.fast && dd_fast_length(g.Z)) return ddf_z(g, S2, K2, dd{1.f, 0.f}, true, st);
     DdZ a = dd_z_args(g.Z, g.Y, g.YZ, g.pz, g.tw2z, S2, K2, dd{1.f, 0.f});
     return launch(k_dd_z<true>, a, dd_z_tiles(g.Z, g.Y, g.Xh), dd_z_smem(g.Z, g.Y), st, "dd z", KC_DD_Z_MUL);
 }
 
 mvd_status dd_z_forward_scaled(const FftGeom& g, cdd* S2, double scale, cudaStream_t st) {
     const float hi = (float)scale;
+    if (g.fast && dd_fast_length(g.Z)) return ddf_z(g, S2, nullptr, dd{hi, (float)(scale - (double)hi)}, false, st);
     DdZ a = dd_z_args(g.Z, g.Y, g.YZ, g.pz, g.tw2z, S2, nullptr, dd{hi, (float)(scale - (double)hi)});
     return launch(k_dd_z<false>, a, dd_z_tiles(g.Z, g.Y, g.Xh), dd_z_smem(g.Z, g.Y), st, "dd z forward", KC_SETUP);
 }

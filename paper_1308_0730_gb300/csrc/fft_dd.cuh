@@ -1,9 +1,11 @@
-// Forward blur b = psi * P_v in double-float (tile-level device functions,
-// generic mixed-radix plans). Same layout as the FP32 passes: spectrum
-// S2[kx][z][y] of complex double-float (16 bytes), two real x-lines per
-// complex line. The last pass leaves double-float: it rounds b to FP32, forms
-// the ratio and hands the FP32 forward x transform of (r - 1) to the FP32
-// back-projection passes.
+// Double-float passes (tile-level device functions, generic mixed-radix
+// plans). Same layout as the FP32 passes: spectrum S2[kx][z][y] of complex
+// double-float (16 bytes), two real x-lines per complex line. The forward
+// blur b = psi * P_v runs entirely in double-float; the ratio pass rounds b to
+// FP32, forms r - 1 = phi / max(b, eps) - 1, transforms it along x in FP32
+// and stores that spectrum exactly as double-float, so that the
+// back-projection's y and z passes (and the kernel multiply) run in
+// double-float too; the update pass reads S2 rounded to FP32.
 //
 // CO = true makes loads of data written inside the same launch L2 loads (the
 // persistent batch kernel).
@@ -39,11 +41,9 @@ struct DdX {
     long YZ;
     FftPlan plan;           // radices of X
     const cdd* tw2;         // double-float twiddles of X
-    const float2* tw;       // FP32 twiddles of X (the FP32 forward transform of r - 1)
     const float* src;       // real rows
     cdd* S2;                // double-float spectrum
     const float* phi;       // observed view
-    float2* S;              // FP32 spectrum of r - 1
     float eps;
 };
 
@@ -94,7 +94,9 @@ __device__ void dd_x_forward_tile(const DdX& a, long tile, cdd* sm) {
 }
 
 // double-float spectrum -> inverse x -> b (rounded to FP32) -> r - 1 with
-// r = phi / max(b, eps) -> FP32 forward x -> FP32 spectrum
+// r = phi / max(b, eps) -> FP32 forward x -> back into S2 (exact as
+// double-float), where the back-projection's y and z passes continue in
+// double-float
 template <bool CO>
 __device__ void dd_x_ratio_tile(const DdX& a, long tile, cdd* sm) {
     cdd* A = sm;
@@ -151,7 +153,7 @@ __device__ void dd_x_ratio_tile(const DdX& a, long tile, cdd* sm) {
             const float2 d = csub(zk, zm);
             val = make_float2(0.5f * d.y, -0.5f * d.x);
         }
-        a.S[(long)k * a.YZ + rho0 + row] = val;
+        cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, cdd{dd_from(val.x), dd_from(val.y)});
     }
 }
 

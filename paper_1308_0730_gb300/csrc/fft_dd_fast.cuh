@@ -1,0 +1,285 @@
+// Register-resident double-float line FFT and forward-blur tiles for
+// power-of-two lengths 32..1024 (same scheme as fft_fast.cuh, 8 elements per
+// thread: a line of length L is held by TPL = L/8 threads, thread t owning
+// elements t + TPL*q; radix-8 Stockham stages, then one radix 2 or 4 stage;
+// padded shared-memory exchanges between stages).
+#pragma once
+
+#include "dd.cuh"
+#include "fft_fast.cuh"
+
+namespace mvd {
+
+constexpr int kE8 = 8;
+constexpr int kDdThreads = 256;
+
+__host__ __device__ constexpr int plan8_n(int L) {
+    int n = 0;
+    while (L % 8 == 0 && L >= 8) {
+        L /= 8;
+        ++n;
+    }
+    return n;
+}
+__host__ __device__ constexpr int plan8_rem(int L) {
+    while (L % 8 == 0 && L >= 8) L /= 8;
+    return L;  // 1, 2 or 4
+}
+__host__ __device__ constexpr int plan8_radix(int L, int s) {
+    return s < plan8_n(L) ? 8 : (s == plan8_n(L) && plan8_rem(L) > 1 ? plan8_rem(L) : 0);
+}
+__host__ __device__ constexpr int plan8_nst(int L) { return plan8_n(L) + (plan8_rem(L) > 1 ? 1 : 0); }
+__host__ __device__ constexpr bool dd_fast_length(int L) { return L >= 32 && L <= 1024 && (L & (L - 1)) == 0; }
+
+// padded index: one pad slot per 8 elements; line stride shifts lines across banks
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int line_stride8(int L) { return L + L / 8 + 1; }
+
+template <int L, int S, bool WARP_LOCAL>
+struct LineFFTDD {
+    static constexpr int TPL = L / kE8;
+    static constexpr int NST = plan8_nst(L);
+
+    __device__ __forceinline__ static void sync() {
+        if (WARP_LOCAL && TPL <= 32)
+            __syncwarp();
+        else
+            __syncthreads();
+    }
+
+    template <int ST, int NS>
+    __device__ __forceinline__ static void stage(cdd (&v)[kE8], cdd* sm, int t, const cdd* __restrict__ tw) {
+        if constexpr (ST < NST) {
+            constexpr int R = plan8_radix(L, ST);
+            constexpr int B = kE8 / R;
+            constexpr bool LAST = (ST == NST - 1);
+#pragma unroll
+            for (int m = 0; m < B; ++m) {
+                cdd x[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[r] = v[m + r * B];
+                const int j = t + TPL * m;
+                const int k = j % NS;
+                if (NS > 1) {
+                    const int step = k * (L / (NS * R));
+#pragma unroll
+                    for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle_dd<S>(tw, r * step));
+                }
+                DftDD<R, S>::run(x);
+                if (LAST) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[m + r * B] = x[r];
+                } else {
+                    const int d = (j / NS) * NS * R + k;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) cdd_store(sm + pad8(d + r * NS), x[r]);
+                }
+            }
+            if constexpr (!LAST) {
+                sync();
+#pragma unroll
+                for (int q = 0; q < kE8; ++q) v[q] = cdd_load(sm + pad8(t + TPL * q));
+                sync();
+                stage<ST + 1, NS * R>(v, sm, t, tw);
+            }
+        }
+    }
+
+    __device__ __forceinline__ static void run(cdd (&v)[kE8], cdd* sm, int t, const cdd* __restrict__ tw) {
+        stage<0, 1>(v, sm, t, tw);
+    }
+};
+
+// tile geometry
+__host__ __device__ constexpr int ddf_pairs(int L) { return kDdThreads / (L / kE8); }  // x pass: pairs per tile
+__host__ __device__ constexpr int ddf_y_lines(int L) { return kDdThreads / (L / kE8); }
+__host__ __device__ constexpr int ddf_z_cols(int L) {
+    return (kDdThreads / (L / kE8)) >= 4 ? kDdThreads / (L / kE8) : 4;
+}
+__host__ __device__ constexpr size_t ddf_x_smem(int L) {
+    return (size_t)2 * ddf_pairs(L) * line_stride8(L) * sizeof(cdd);
+}
+__host__ __device__ constexpr size_t ddf_y_smem(int L) { return (size_t)ddf_y_lines(L) * line_stride8(L) * sizeof(cdd); }
+__host__ __device__ constexpr size_t ddf_z_smem(int L) { return (size_t)ddf_z_cols(L) * line_stride8(L) * sizeof(cdd); }
+
+template <bool CO>
+__device__ __forceinline__ cdd ld_cdd(const cdd* p) {
+    if constexpr (CO)
+        return cdd_load_cg(p);
+    else
+        return cdd_load(p);
+}
+
+template <int L, int S, bool CO>
+__device__ __forceinline__ void ddf_y_tile(cdd* __restrict__ S2, long nlines, const cdd* __restrict__ tw2, long tile,
+                                           cdd* sm) {
+    using F = LineFFTDD<L, S, true>;
+    constexpr int TPL = F::TPL, LPC = kDdThreads / TPL;
+    const int li = threadIdx.x / TPL, t = threadIdx.x - li * TPL;
+    const long line = tile * LPC + li;
+    const bool ok = line < nlines;
+    cdd* g = S2 + line * L;
+    cdd v[kE8];
+#pragma unroll
+    for (int q = 0; q < kE8; ++q) v[q] = ok ? ld_cdd<CO>(g + t + TPL * q) : czero_dd();
+    F::run(v, sm + li * line_stride8(L), t, tw2);
+    if (ok) {
+#pragma unroll
+        for (int q = 0; q < kE8; ++q) cdd_store(g + t + TPL * q, v[q]);
+    }
+}
+
+// z: forward, times the double-float kernel spectrum, inverse (MUL); or
+// forward times a scale. Needs Q * L/8 threads.
+template <int L, bool MUL, bool CO>
+__device__ __forceinline__ void ddf_z_tile(cdd* __restrict__ S2, const cdd* __restrict__ K2, int Y, long YZ,
+                                           int ntiles_y, dd scale, const cdd* __restrict__ tw2, long tile, cdd* sm) {
+    constexpr int TPL = L / kE8, Q = ddf_z_cols(L);
+    const int q = threadIdx.x % Q, t = threadIdx.x / Q;
+    const int kx = (int)(tile / ntiles_y);
+    const int y0 = (int)(tile - (long)kx * ntiles_y) * Q;
+    const bool ok = y0 + q < Y;
+    const long base = (long)kx * YZ + y0 + q;
+    cdd* line_sm = sm + q * line_stride8(L);
+    cdd v[kE8];
+#pragma unroll
+    for (int i = 0; i < kE8; ++i) v[i] = ok ? ld_cdd<CO>(S2 + base + (long)(t + TPL * i) * Y) : czero_dd();
+    LineFFTDD<L, -1, false>::run(v, line_sm, t, tw2);
+    if (MUL) {
+#pragma unroll
+        for (int i = 0; i < kE8; ++i) v[i] = cmul(v[i], ok ? cdd_load_nc(K2 + base + (long)(t + TPL * i) * Y) : czero_dd());
+        __syncthreads();
+        LineFFTDD<L, +1, false>::run(v, line_sm, t, tw2);
+    } else {
+#pragma unroll
+        for (int i = 0; i < kE8; ++i) v[i] = cdd{dd_mul(v[i].re, scale), dd_mul(v[i].im, scale)};
+    }
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < kE8; ++i) cdd_store(S2 + base + (long)(t + TPL * i) * Y, v[i]);
+    }
+}
+
+struct DdXFast {
+    const float* src;  // real rows
+    cdd* S2;
+    const float* phi;
+    long YZ;
+    float eps;
+    const cdd* tw2;
+    FftPlan plan;      // FP32 plan of X (radices + FP32 twiddles) for the r - 1 transform
+};
+
+// unpack the packed forward double-float spectra (natural order in registers
+// of pair p) into the two half spectra, coalesced over rows
+template <int L>
+__device__ __forceinline__ void ddf_store_halves(const DdXFast& a, cdd (&v)[kE8], cdd* sm, int p, int t, long rho0,
+                                                 int nrows) {
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L), XH = L / 2 + 1;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kE8; ++q) cdd_store(sm + p * LS + pad8(t + TPL * q), v[q]);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
+        const int k = idx / (2 * P), row = idx - k * 2 * P;
+        if (row >= nrows) continue;
+        const int pp = row < P ? row : row - P;
+        const cdd zk = cdd_load(sm + pp * LS + pad8(k));
+        const cdd zm = cconj(cdd_load(sm + pp * LS + pad8(k == 0 ? 0 : L - k)));
+        cdd val;
+        if (row < P) {
+            val = chalf(cadd(zk, zm));
+        } else {
+            const cdd d = chalf(csub(zk, zm));
+            val = cdd{d.im, dd{-d.re.hi, -d.re.lo}};
+        }
+        cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, val);
+    }
+}
+
+template <int L, bool CO>
+__device__ __forceinline__ void ddf_x_forward_tile(const DdXFast& a, long tile, cdd* sm) {
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L);
+    const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
+    const long rho0 = tile * 2 * P;
+    const int nrows = (int)min((long)2 * P, a.YZ - rho0);
+    const bool oka = p < nrows, okb = P + p < nrows;
+    const float* ra = a.src + (rho0 + p) * L;
+    const float* rb = a.src + (rho0 + P + p) * L;
+    cdd v[kE8];
+#pragma unroll
+    for (int q = 0; q < kE8; ++q) {
+        const int n = t + TPL * q;
+        v[q] = cdd{dd_from(oka ? ld1<CO>(ra + n) : 0.f), dd_from(okb ? ld1<CO>(rb + n) : 0.f)};
+    }
+    LineFFTDD<L, -1, true>::run(v, sm + p * LS, t, a.tw2);
+    ddf_store_halves<L>(a, v, sm, p, t, rho0, nrows);
+}
+
+// double-float spectrum -> inverse x -> b -> r - 1 = phi / max(b, eps) - 1
+// -> FP32 forward x (shared-memory Stockham) -> back into S2 as double-float
+template <int L, bool CO>
+__device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cdd* sm) {
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L), XH = L / 2 + 1;
+    const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
+    const long rho0 = tile * 2 * P;
+    const int nrows = (int)min((long)2 * P, a.YZ - rho0);
+    const bool oka = p < nrows, okb = P + p < nrows;
+    // gather both half spectra: rows < P -> line p (A), rows >= P -> line P + p (B)
+    for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
+        const int k = idx / (2 * P), row = idx - k * 2 * P;
+        const cdd val = row < nrows ? ld_cdd<CO>(a.S2 + (long)k * a.YZ + rho0 + row) : czero_dd();
+        cdd_store(sm + row * LS + pad8(k), val);
+    }
+    __syncthreads();
+    cdd v[kE8];
+#pragma unroll
+    for (int q = 0; q < kE8; ++q) {
+        const int k = t + TPL * q;
+        const int kk = k <= L / 2 ? k : L - k;
+        const cdd A = cdd_load(sm + p * LS + pad8(kk)), B = cdd_load(sm + (P + p) * LS + pad8(kk));
+        v[q] = k <= L / 2 ? cdd{dd_sub(A.re, B.im), dd_add(A.im, B.re)}    // A + iB
+                          : cdd{dd_add(A.re, B.im), dd_sub(B.re, A.im)};   // conj(A) + i conj(B)
+    }
+    // the observed rows, fetched now to overlap the inverse transform
+    float2 w[kE8];
+    const long ra = (rho0 + p) * L, rb = (rho0 + P + p) * L;
+#pragma unroll
+    for (int q = 0; q < kE8; ++q) {
+        const int n = t + TPL * q;
+        w[q] = make_float2(oka ? __ldg(a.phi + ra + n) : 0.f, okb ? __ldg(a.phi + rb + n) : 0.f);
+    }
+    __syncthreads();
+    LineFFTDD<L, +1, true>::run(v, sm + p * LS, t, a.tw2);
+    // r - 1 into FP32 lines (the B half of shared memory), then FP32 forward x
+    __syncthreads();
+    float2* F0 = reinterpret_cast<float2*>(sm + P * LS);
+    float2* F1 = F0 + P * (L + 1);
+#pragma unroll
+    for (int q = 0; q < kE8; ++q) {
+        const int n = t + TPL * q;
+        const float ba = v[q].re.hi + v[q].re.lo, bb = v[q].im.hi + v[q].im.lo;
+        const float xa = oka ? w[q].x / fmaxf(ba, a.eps) - 1.f : 0.f;
+        const float xb = okb ? w[q].y / fmaxf(bb, a.eps) - 1.f : 0.f;
+        F0[p * (L + 1) + n] = make_float2(xa, xb);
+    }
+    __syncthreads();
+    const float2* F = fft_lines<-1>(F0, F1, P, L + 1, a.plan);
+    for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
+        const int k = idx / (2 * P), row = idx - k * 2 * P;
+        if (row >= nrows) continue;
+        const int pp = row < P ? row : row - P;
+        const float2 zk = F[pp * (L + 1) + k];
+        const float2 zm = cconj(F[pp * (L + 1) + (k == 0 ? 0 : L - k)]);
+        float2 val;
+        if (row < P) {
+            val = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
+        } else {
+            const float2 d = csub(zk, zm);
+            val = make_float2(0.5f * d.y, -0.5f * d.x);
+        }
+        cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, cdd{dd_from(val.x), dd_from(val.y)});
+    }
+}
+
+}  // namespace mvd

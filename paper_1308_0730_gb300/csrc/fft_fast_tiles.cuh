@@ -6,6 +6,7 @@
 // requires.
 #pragma once
 
+#include "dd.cuh"
 #include "fft_fast.cuh"
 
 namespace mvd {
@@ -88,6 +89,7 @@ struct XFast {
     long YZ;
     float eps;
     const float2* tw;
+    const cdd* spec2;  // when set, the update reads this double-float spectrum (rounded to FP32)
 };
 
 // write the packed forward spectra (natural order in registers) as the two
@@ -133,7 +135,16 @@ __device__ __forceinline__ void x_load_packed(const XFast& a, float2 (&v)[kE], f
     for (int i = 0; i < NIT; ++i) {
         const int idx = threadIdx.x + i * kFastThreads;
         const int k = idx / (2 * P), row = idx - k * 2 * P;
-        tmp[i] = (idx < NTOT && row < nrows) ? ld2<CO>(a.spec + (long)k * a.YZ + rho0 + row) : make_float2(0.f, 0.f);
+        tmp[i] = make_float2(0.f, 0.f);
+        if (idx < NTOT && row < nrows) {
+            const long at = (long)k * a.YZ + rho0 + row;
+            if (a.spec2) {
+                const cdd z = CO ? cdd_load_cg(a.spec2 + at) : cdd_load(a.spec2 + at);
+                tmp[i] = make_float2(z.re.hi + z.re.lo, z.im.hi + z.im.lo);
+            } else {
+                tmp[i] = ld2<CO>(a.spec + at);
+            }
+        }
     }
 #pragma unroll
     for (int i = 0; i < NIT; ++i) {

@@ -8,6 +8,7 @@
 // x-lines per complex line, 1/M folded into the kernel spectra.
 #pragma once
 
+#include "dd.cuh"
 #include "fft.cuh"
 
 namespace mvd {
@@ -49,6 +50,7 @@ struct GenX {
     const float* phi;  // ratio epilogue
     float* psi;        // update epilogue / real output
     float eps;
+    const cdd* S2in;   // when set, the update reads this double-float spectrum (rounded to FP32)
 };
 
 __host__ __device__ inline GenX gen_x_args(int X, long YZ, const FftPlan& plan) {
@@ -103,7 +105,16 @@ __device__ __forceinline__ void gen_load_spectrum_pairs(const GenX& a, float2* A
     const int n = a.Xh * P2;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const int k = t / P2, row = t - k * P2;
-        const float2 v = row < nrows ? ld2<CO>(a.S + (long)k * a.YZ + rho0 + row) : make_float2(0.f, 0.f);
+        float2 v = make_float2(0.f, 0.f);
+        if (row < nrows) {
+            const long at = (long)k * a.YZ + rho0 + row;
+            if (a.S2in) {
+                const cdd z = CO ? cdd_load_cg(a.S2in + at) : cdd_load(a.S2in + at);
+                v = make_float2(z.re.hi + z.re.lo, z.im.hi + z.im.lo);
+            } else {
+                v = ld2<CO>(a.S + at);
+            }
+        }
         if (row < a.P)
             A[row * a.ls + k] = v;
         else

@@ -91,6 +91,14 @@ mvd_status fft_x_update_generic(const FftGeom& g, const float2* S, float* psi, f
     return launch(k_x_inverse<true>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
 }
 
+mvd_status fft_x_update_dd_generic(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st) {
+    GenX a = make_x(g);
+    a.S2in = S2;
+    a.psi = psi;
+    a.eps = eps;
+    return launch(k_x_inverse<true>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
+}
+
 mvd_status fft_inverse_real_generic(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
     GenX a = make_x(g);
     a.S = const_cast<float2*>(S);
@@ -129,6 +137,10 @@ mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps,
 mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st) {
     if (g.fast && fft_fast_supported(g.X)) return fft_x_update_fast(g, S, psi, eps, st);
     return fft_x_update_generic(g, S, psi, eps, st);
+}
+mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st) {
+    if (g.fast && fft_fast_supported(g.X)) return fft_x_update_dd_fast(g, S2, psi, eps, st);
+    return fft_x_update_dd_generic(g, S2, psi, eps, st);
 }
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
     if (g.fast && fft_fast_supported(g.X)) return fft_inverse_real_fast(g, S, dst, st);

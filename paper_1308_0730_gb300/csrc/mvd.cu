@@ -239,8 +239,7 @@ mvd_status setup_fft(mvd_ctx* c) {
     g.pz.tw = c->d_tw + g.X + g.Y;
     const size_t ns = (size_t)g.Xh * g.YZ;
     MVD_TRY(dev_alloc(&c->d_S, ns, "work spectrum"));
-    const int nk = c->precise ? c->nv : 2 * c->nv;
-    MVD_TRY(dev_alloc(&c->d_K, ns * nk, "kernel spectra"));
+    if (!c->precise) MVD_TRY(dev_alloc(&c->d_K, ns * 2 * c->nv, "kernel spectra"));
     const float inv_m = (float)(1.0 / (double)c->M);
     if (c->precise) {
         // double-float twiddles: hi = fl32(w), lo = fl32(w - hi), w in FP64
@@ -262,22 +261,22 @@ mvd_status setup_fft(mvd_ctx* c) {
         g.tw2y = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + g.X);
         g.tw2z = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + g.X + g.Y);
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_S2), ns, "double-float work spectrum"));
-        MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_KP2), ns * c->nv, "double-float PSF spectra"));
+        MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_KP2), ns * 2 * c->nv, "double-float kernel spectra"));
     }
-    // kernel spectra, scaled by 1/M: fast mode slot 2v = P_v, 2v+1 = P_v^comp;
-    // precise mode slot v = P_v^comp (FP32) and the double-float P_v
+    // kernel spectra, scaled by 1/M: slot 2v = P_v, 2v+1 = P_v^comp (FP32 in
+    // fast mode, double-float in precise mode)
     for (int v = 0; v < c->nv; ++v) {
         for (int which = 0; which < 2; ++which) {
             const float* k = (which == 0 ? c->d_psf : c->d_comp) + c->koff[v];
             MVD_TRY(place_kernel(c->dims, k, &c->kd[3 * v], c->d_r, c->stream));
-            if (c->precise && which == 0) {
-                cdd* dst = reinterpret_cast<cdd*>(reinterpret_cast<float4*>(c->d_KP2) + ns * v);
+            if (c->precise) {
+                cdd* dst = reinterpret_cast<cdd*>(reinterpret_cast<float4*>(c->d_KP2) + ns * (2 * v + which));
                 MVD_TRY(dd_forward_real(g, c->d_r, dst, c->stream));
                 MVD_TRY(dd_y(g, dst, 0, c->stream));
                 MVD_TRY(dd_z_forward_scaled(g, dst, 1.0 / (double)c->M, c->stream));
                 continue;
             }
-            float2* dst = c->d_K + ns * (c->precise ? v : 2 * v + which);
+            float2* dst = c->d_K + ns * (2 * v + which);
             MVD_TRY(fft_forward_real(g, c->d_r, dst, c->stream));
             MVD_TRY(fft_y(g, dst, 0, c->stream));
             MVD_TRY(fft_z_forward_scaled(g, dst, inv_m, c->stream));
@@ -297,17 +296,18 @@ mvd_status one_update(mvd_ctx* c, int v) {
     const size_t ns = (size_t)g.Xh * g.YZ;
     if (c->precise) {
         cdd* S2 = c->d_S2;
-        const cdd* Kp2 = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_KP2) + ns * v);
-        const float2* Kc = c->d_K + ns * v;
+        const float4* K4 = reinterpret_cast<const float4*>(c->d_KP2);
+        const cdd* Kp2 = reinterpret_cast<const cdd*>(K4 + ns * (2 * v));
+        const cdd* Kc2 = reinterpret_cast<const cdd*>(K4 + ns * (2 * v + 1));
         MVD_TRY(dd_forward_real(g, c->d_psi, S2, c->stream));
         MVD_TRY(dd_y(g, S2, 0, c->stream));
         MVD_TRY(dd_z_mul(g, S2, Kp2, c->stream));
         MVD_TRY(dd_y(g, S2, 1, c->stream));
-        MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->d_S, c->stream));
-        MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
-        MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
-        MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
-        return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream);
+        MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream));
+        MVD_TRY(dd_y(g, S2, 0, c->stream));
+        MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
+        MVD_TRY(dd_y(g, S2, 1, c->stream));
+        return fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream);
     }
     const float2* Kp = c->d_K + ns * (2 * v);
     const float2* Kc = c->d_K + ns * (2 * v + 1);
