@@ -20,4 +20,5 @@ from .oracle import (  # noqa: F401
     deconvolve,
     mean_views,
     num_threads,
+    unrolled_grad,
 )

@@ -302,3 +302,309 @@ void mvdo_update_at(const double* psi, const double* phi, const double* P, const
         out[s] = fmax(psi[li] * c, eps);
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Gradient of the unrolled iteration (reverse mode, FP64).
+ *
+ * Loss: L = mean_x (psi_K(x) - truth(x))^2 after n_iter iterations of the
+ * schedule from the flat start psi0 = mean of the views. One update, written
+ * as a chain of elementary steps (floors inactive where the derivative is
+ * taken: max(a, eps) passes its gradient when a > eps, else none):
+ *   b = psi * P ; b' = max(b, eps) ; r = phi / b' ; c = r * K ;
+ *   t = psi . c ; psi' = max(t, eps)
+ * and its adjoint, for an incoming gradient g = dL/dpsi':
+ *   tb = g [t > eps] ; psi_bar = tb . c ; cb = tb . psi
+ *   rb = cb * K^*            (K^*(d) = K(-d): transpose of the convolution)
+ *   Kb(d) += sum_x cb(x) r(x - d)
+ *   phib += rb / b' ; bb = -rb r / b' [b > eps]
+ *   psi_bar += bb * P^* ; Pb(d) += sum_x bb(x) psi(x - d)
+ * The kernel gradients Kb flow back through the compound kernel (Eq. 222,
+ * 230 or 240 and the normalisation) to every PSF, the PSF gradients through
+ * the PSF normalisation to the raw PSF values, and the gradient of psi0
+ * (flat start = mean of all views) spreads evenly over every view voxel.
+ * The floor eps = 1e-4 psi0 also depends on the views; it only acts through
+ * active floors, which the gradient ignores as stated above.
+ * ------------------------------------------------------------------------ */
+
+/* out(d) = sum_x a(x) b((x - d) mod dims) for d on a centred box */
+static void corr_box(const double* a, const double* b, const int dims[3], const int kd[3], double* out) {
+    const int X = dims[0], Y = dims[1], Z = dims[2];
+    const int hx = (kd[0] - 1) / 2, hy = (kd[1] - 1) / 2, hz = (kd[2] - 1) / 2;
+    const long T = (long)kd[0] * kd[1] * kd[2];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long i = 0; i < T; ++i) {
+        const int dx = (int)(i % kd[0]) - hx, dy = (int)((i / kd[0]) % kd[1]) - hy,
+                  dz = (int)(i / ((long)kd[0] * kd[1])) - hz;
+        double s = 0.0;
+        for (int z = 0; z < Z; ++z) {
+            const int sz = ((z - dz) % Z + Z) % Z;
+            for (int y = 0; y < Y; ++y) {
+                const int sy = ((y - dy) % Y + Y) % Y;
+                const double* ar = a + idx3(0, y, z, X, Y);
+                const double* br = b + idx3(0, sy, sz, X, Y);
+                for (int x = 0; x < X; ++x) s += ar[x] * br[((x - dx) % X + X) % X];
+            }
+        }
+        out[i] = s;
+    }
+}
+
+/* value of a centred-box kernel at offset (dx,dy,dz), 0 outside the box */
+static double kat(const double* k, const int kd[3], int dx, int dy, int dz) {
+    const int hx = (kd[0] - 1) / 2, hy = (kd[1] - 1) / 2, hz = (kd[2] - 1) / 2;
+    if (dx < -hx || dx > hx || dy < -hy || dy > hy || dz < -hz || dz > hz) return 0.0;
+    return k[idx3(dx + hx, dy + hy, dz + hz, kd[0], kd[1])];
+}
+
+/* Gradient of the compound kernel of view v (normalised PSFs Pn) with
+ * respect to every normalised PSF: adds into Pb[w] given Kb (box of v). */
+static void compound_vjp(int nv, double* const* Pn, const int* pd, int v, int variant, const double* Kb,
+                         double* const* Pb) {
+    const int* dv = pd + 3 * v;
+    const long Tv = (long)dv[0] * dv[1] * dv[2];
+    const int hvx = (dv[0] - 1) / 2, hvy = (dv[1] - 1) / 2, hvz = (dv[2] - 1) / 2;
+    double* A = (double*)malloc(sizeof(double) * Tv);
+    mvdo_mirror(Pn[v], dv, A);
+    /* forward factors C_w on v's box (1 for w == v) */
+    double** C = (double**)calloc(nv, sizeof(double*));
+    double** Q = (double**)calloc(nv, sizeof(double*));
+    int (*qd)[3] = malloc(sizeof(int[3]) * nv);
+    double* U = (double*)malloc(sizeof(double) * Tv);
+    for (long i = 0; i < Tv; ++i) U[i] = A[i];
+    if (variant != MVDO_PLAIN) {
+        for (int w = 0; w < nv; ++w) {
+            if (w == v) continue;
+            const int* dw = pd + 3 * w;
+            C[w] = (double*)malloc(sizeof(double) * Tv);
+            if (variant == MVDO_EFFICIENT) {
+                const long Tw = (long)dw[0] * dw[1] * dw[2];
+                qd[w][0] = 2 * dw[0] - 1;
+                qd[w][1] = 2 * dw[1] - 1;
+                qd[w][2] = 2 * dw[2] - 1;
+                double* pws = (double*)malloc(sizeof(double) * Tw);
+                Q[w] = (double*)malloc(sizeof(double) * (long)qd[w][0] * qd[w][1] * qd[w][2]);
+                mvdo_mirror(Pn[w], dw, pws);
+                mvdo_kconv(Pn[w], dw, pws, dw, Q[w], qd[w]);
+                mvdo_kconv(A, dv, Q[w], qd[w], C[w], dv);
+                free(pws);
+            } else if (variant == MVDO_OPT1) {
+                mvdo_kconv(A, dv, Pn[w], dw, C[w], dv);
+            } else {
+                for (long i = 0; i < Tv; ++i) C[w][i] = A[i];
+            }
+            for (long i = 0; i < Tv; ++i) U[i] *= C[w][i];
+        }
+    }
+    double su = 0.0, kk = 0.0;
+    for (long i = 0; i < Tv; ++i) su += U[i];
+    for (long i = 0; i < Tv; ++i) kk += Kb[i] * (U[i] / su);
+    double* Ub = (double*)malloc(sizeof(double) * Tv);
+    for (long i = 0; i < Tv; ++i) Ub[i] = (Kb[i] - kk) / su; /* through K = U / sum(U) */
+    double* Ab = (double*)calloc(Tv, sizeof(double));
+    for (long i = 0; i < Tv; ++i) {
+        double prod = 1.0;
+        for (int w = 0; w < nv; ++w)
+            if (C[w]) prod *= C[w][i];
+        Ab[i] += Ub[i] * prod; /* U = A . prod C_w */
+    }
+    for (int w = 0; w < nv; ++w) {
+        if (!C[w]) continue;
+        const int* dw = pd + 3 * w;
+        double* Cb = (double*)malloc(sizeof(double) * Tv);
+        for (long i = 0; i < Tv; ++i) {
+            double prod = A[i];
+            for (int u = 0; u < nv; ++u)
+                if (C[u] && u != w) prod *= C[u][i];
+            Cb[i] = Ub[i] * prod;
+        }
+        if (variant == MVDO_OPT2) { /* C_w = A */
+            for (long i = 0; i < Tv; ++i) Ab[i] += Cb[i];
+        } else {
+            /* C_w(d) = sum_e A(e) G(d - e), G = Q_w (Eq. 222) or P_w (Eq. 230) */
+            const double* G = variant == MVDO_EFFICIENT ? Q[w] : Pn[w];
+            const int* gd = variant == MVDO_EFFICIENT ? qd[w] : dw;
+            const int ghx = (gd[0] - 1) / 2, ghy = (gd[1] - 1) / 2, ghz = (gd[2] - 1) / 2;
+            const long Tg = (long)gd[0] * gd[1] * gd[2];
+            double* Gb = (double*)calloc(Tg, sizeof(double));
+            for (long ie = 0; ie < Tv; ++ie) {
+                const int ex = (int)(ie % dv[0]) - hvx, ey = (int)((ie / dv[0]) % dv[1]) - hvy,
+                          ez = (int)(ie / ((long)dv[0] * dv[1])) - hvz;
+                for (long id = 0; id < Tv; ++id) {
+                    const int dx = (int)(id % dv[0]) - hvx, dy = (int)((id / dv[0]) % dv[1]) - hvy,
+                              dz = (int)(id / ((long)dv[0] * dv[1])) - hvz;
+                    const int fx = dx - ex, fy = dy - ey, fz = dz - ez;
+                    if (fx < -ghx || fx > ghx || fy < -ghy || fy > ghy || fz < -ghz || fz > ghz) continue;
+                    const long ig = idx3(fx + ghx, fy + ghy, fz + ghz, gd[0], gd[1]);
+                    Ab[ie] += Cb[id] * G[ig];
+                    Gb[ig] += Cb[id] * A[ie];
+                }
+            }
+            if (variant == MVDO_EFFICIENT) {
+                /* Q_w(f) = sum_g Pn_w(g) Pn_w(g - f): dQ(f)/dPn_w(h) = Pn_w(h - f) + Pn_w(h + f) */
+                const int hwx = (dw[0] - 1) / 2, hwy = (dw[1] - 1) / 2, hwz = (dw[2] - 1) / 2;
+                const long Tw = (long)dw[0] * dw[1] * dw[2];
+                for (long ih = 0; ih < Tw; ++ih) {
+                    const int hx = (int)(ih % dw[0]) - hwx, hy = (int)((ih / dw[0]) % dw[1]) - hwy,
+                              hz = (int)(ih / ((long)dw[0] * dw[1])) - hwz;
+                    double s = 0.0;
+                    for (long ig = 0; ig < Tg; ++ig) {
+                        const int fx = (int)(ig % gd[0]) - ghx, fy = (int)((ig / gd[0]) % gd[1]) - ghy,
+                                  fz = (int)(ig / ((long)gd[0] * gd[1])) - ghz;
+                        s += Gb[ig] * (kat(Pn[w], dw, hx - fx, hy - fy, hz - fz) + kat(Pn[w], dw, hx + fx, hy + fy, hz + fz));
+                    }
+                    Pb[w][ih] += s;
+                }
+            } else {
+                const long Tw = (long)dw[0] * dw[1] * dw[2];
+                for (long i = 0; i < Tw; ++i) Pb[w][i] += Gb[i];
+            }
+            free(Gb);
+        }
+        free(Cb);
+    }
+    /* A = Pn_v^*: Pn_v(d) = A(-d) */
+    for (long i = 0; i < Tv; ++i) {
+        const int x = (int)(i % dv[0]), y = (int)((i / dv[0]) % dv[1]), z = (int)(i / ((long)dv[0] * dv[1]));
+        Pb[v][idx3(dv[0] - 1 - x, dv[1] - 1 - y, dv[2] - 1 - z, dv[0], dv[1])] += Ab[i];
+    }
+    for (int w = 0; w < nv; ++w) {
+        free(C[w]);
+        free(Q[w]);
+    }
+    free(C);
+    free(Q);
+    free(qd);
+    free(A);
+    free(U);
+    free(Ub);
+    free(Ab);
+}
+
+/* Loss and gradients of the unrolled iteration (see the block comment).
+ * grad_views: nv volumes; grad_psfs: nv boxes of the RAW PSFs as given.
+ * Returns the loss, or -1 on error. psiK (optional) receives the estimate. */
+double mvdo_unrolled_grad(int nv, const double* const* views, const double* const* psfs, const int* pd,
+                          const int dims[3], int variant, int n_iter, const double* truth, double* const* grad_views,
+                          double* const* grad_psfs, double* psiK) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double** Pn = (double**)malloc(sizeof(double*) * nv);
+    double** K = (double**)malloc(sizeof(double*) * nv);
+    double** Pb = (double**)malloc(sizeof(double*) * nv);
+    double** Kb = (double**)malloc(sizeof(double*) * nv);
+    double* psum = (double*)malloc(sizeof(double) * nv);
+    for (int v = 0; v < nv; ++v) {
+        const long T = (long)pd[3 * v] * pd[3 * v + 1] * pd[3 * v + 2];
+        double s = 0.0;
+        for (long i = 0; i < T; ++i) s += psfs[v][i];
+        psum[v] = s;
+        Pn[v] = (double*)malloc(sizeof(double) * T);
+        for (long i = 0; i < T; ++i) Pn[v][i] = psfs[v][i] / s;
+        Pb[v] = (double*)calloc(T, sizeof(double));
+        Kb[v] = (double*)calloc(T, sizeof(double));
+    }
+    for (int v = 0; v < nv; ++v) {
+        const long T = (long)pd[3 * v] * pd[3 * v + 1] * pd[3 * v + 2];
+        K[v] = (double*)malloc(sizeof(double) * T);
+        mvdo_compound(nv, (const double* const*)Pn, pd, v, variant, K[v]);
+    }
+    const double psi0 = mvdo_mean_views(nv, views, dims);
+    const double eps = 1e-4 * psi0;
+    const long nup = (long)n_iter * nv;
+    double* hist = (double*)malloc(sizeof(double) * M * (nup + 1));
+    for (long i = 0; i < M; ++i) hist[i] = psi0;
+    double *b = (double*)malloc(sizeof(double) * M), *r = (double*)malloc(sizeof(double) * M),
+           *c = (double*)malloc(sizeof(double) * M);
+    for (long u = 0; u < nup; ++u) {
+        const int v = (int)(u % nv);
+        for (long i = 0; i < M; ++i) hist[(u + 1) * M + i] = hist[u * M + i];
+        mvdo_update(hist + (u + 1) * M, views[v], Pn[v], pd + 3 * v, K[v], pd + 3 * v, dims, eps, b, r, c);
+    }
+    const double* pk = hist + nup * M;
+    double loss = 0.0;
+    double* g = (double*)malloc(sizeof(double) * M);
+    for (long i = 0; i < M; ++i) {
+        const double d = pk[i] - truth[i];
+        loss += d * d;
+        g[i] = 2.0 * d / (double)M;
+    }
+    loss /= (double)M;
+    if (psiK)
+        for (long i = 0; i < M; ++i) psiK[i] = pk[i];
+    for (int v = 0; v < nv; ++v)
+        for (long i = 0; i < M; ++i) grad_views[v][i] = 0.0;
+    double *cb = (double*)malloc(sizeof(double) * M), *rb = (double*)malloc(sizeof(double) * M),
+           *bb = (double*)malloc(sizeof(double) * M), *tmp = (double*)malloc(sizeof(double) * M);
+    for (long u = nup - 1; u >= 0; --u) {
+        const int v = (int)(u % nv);
+        const int* kd = pd + 3 * v;
+        const long T = (long)kd[0] * kd[1] * kd[2];
+        const double* psi = hist + u * M;
+        /* recompute the forward intermediates of this update */
+        mvdo_conv(psi, dims, Pn[v], kd, b);
+        for (long i = 0; i < M; ++i) r[i] = views[v][i] / fmax(b[i], eps);
+        mvdo_conv(r, dims, K[v], kd, c);
+        double* gnew = tmp;
+        for (long i = 0; i < M; ++i) {
+            const double t = psi[i] * c[i];
+            const double tb = t > eps ? g[i] : 0.0;
+            gnew[i] = tb * c[i];
+            cb[i] = tb * psi[i];
+        }
+        double* Ks = (double*)malloc(sizeof(double) * T);
+        double* kg = (double*)malloc(sizeof(double) * T);
+        mvdo_mirror(K[v], kd, Ks);
+        mvdo_conv(cb, dims, Ks, kd, rb);
+        corr_box(cb, r, dims, kd, kg);
+        for (long i = 0; i < T; ++i) Kb[v][i] += kg[i];
+        for (long i = 0; i < M; ++i) {
+            const double bp = fmax(b[i], eps);
+            grad_views[v][i] += rb[i] / bp;
+            bb[i] = b[i] > eps ? -rb[i] * r[i] / bp : 0.0;
+        }
+        double* Ps = Ks;
+        mvdo_mirror(Pn[v], kd, Ps);
+        mvdo_conv(bb, dims, Ps, kd, c);
+        for (long i = 0; i < M; ++i) gnew[i] += c[i];
+        corr_box(bb, psi, dims, kd, kg);
+        for (long i = 0; i < T; ++i) Pb[v][i] += kg[i];
+        free(Ks);
+        free(kg);
+        double* sw = g;
+        g = gnew;
+        tmp = sw;
+    }
+    /* flat start psi0 = mean of all views */
+    double gs = 0.0;
+    for (long i = 0; i < M; ++i) gs += g[i];
+    for (int v = 0; v < nv; ++v)
+        for (long i = 0; i < M; ++i) grad_views[v][i] += gs / ((double)M * nv);
+    for (int v = 0; v < nv; ++v) compound_vjp(nv, Pn, pd, v, variant, Kb[v], Pb);
+    /* PSF normalisation Pn = p / sum(p) */
+    for (int v = 0; v < nv; ++v) {
+        const long T = (long)pd[3 * v] * pd[3 * v + 1] * pd[3 * v + 2];
+        double dot = 0.0;
+        for (long i = 0; i < T; ++i) dot += Pb[v][i] * Pn[v][i];
+        for (long i = 0; i < T; ++i) grad_psfs[v][i] = (Pb[v][i] - dot) / psum[v];
+    }
+    for (int v = 0; v < nv; ++v) {
+        free(Pn[v]);
+        free(K[v]);
+        free(Pb[v]);
+        free(Kb[v]);
+    }
+    free(Pn);
+    free(K);
+    free(Pb);
+    free(Kb);
+    free(psum);
+    free(hist);
+    free(b);
+    free(r);
+    free(c);
+    free(g);
+    free(cb);
+    free(rb);
+    free(bb);
+    free(tmp);
+    return loss;
+}

@@ -60,6 +60,10 @@ def _load():
             lib.mvdo_update_at.argtypes = [_D, _D, _D, _I, _D, _I, _I, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_long), ctypes.c_int, _D]
             lib.mvdo_num_threads.restype = ctypes.c_int
+            lib.mvdo_unrolled_grad.argtypes = [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D), _I, _I,
+                                               ctypes.c_int, ctypes.c_int, _D, ctypes.POINTER(_D),
+                                               ctypes.POINTER(_D), _D]
+            lib.mvdo_unrolled_grad.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -182,3 +186,23 @@ def deconvolve(views, psfs, n_iter, variant="efficient", schedule=None, eps=0.0,
     if used < 0:
         raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
     return psi, used
+
+
+def unrolled_grad(views, psfs, n_iter, truth, variant="efficient"):
+    """Loss mean((psi_K - truth)^2) of n_iter iterations from the flat start and its
+    gradients with respect to every view and every raw PSF (reverse mode, FP64).
+
+    Returns ``(loss, grad_views, grad_psfs, psi_K)``.
+    """
+    var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    vs = [_f64(v) for v in views]
+    ps, parr, pd = _psf_arrays(psfs)
+    varr = (_D * len(vs))(*[_dptr(v) for v in vs])
+    t = _f64(truth)
+    gv = [np.empty_like(v) for v in vs]
+    gp = [np.empty_like(p) for p in ps]
+    psik = np.empty_like(vs[0])
+    loss = _load().mvdo_unrolled_grad(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), _dptr(t),
+                                      (_D * len(gv))(*[_dptr(g) for g in gv]),
+                                      (_D * len(gp))(*[_dptr(g) for g in gp]), _dptr(psik))
+    return loss, gv, gp, psik
