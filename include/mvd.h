@@ -207,6 +207,49 @@ long long mvd_batch_tasks(const mvd_batch* batch);
 void mvd_batch_destroy(mvd_batch* batch);
 
 /*
+ * Differentiation of the unrolled iteration, for calibrating PSF parameters
+ * or views against a target (the paper's update, Eq. 15 with the kernels of
+ * Eq. 222 / 230 / 240 / 51, read as a differentiable function of the views
+ * and PSFs; the paper itself does not differentiate it).
+ *   mvd_unrolled_forward   n_iter >= 0 iterations of the default schedule
+ *            (views 0..N-1) from the flat start psi0 = mean of the views,
+ *            keeping the estimate before every view update on the device
+ *            (n_iter * N volumes, freed by the next call or mvd_destroy).
+ *            Afterwards the context's estimate is psi_K (mvd_result*).
+ *            Needs a precomputed context (else MVD_ERR_STATE).
+ *   mvd_unrolled_backward  reverse pass for the last forward run.
+ *            grad_psi    device, X*Y*Z floats: dL/dpsi_K.
+ *            grad_views  N device pointers, X*Y*Z floats each, written with
+ *                        dL/dphi_v (including the flat start's share).
+ *            grad_psfs   N HOST pointers, Kx*Ky*Kz floats each (the PSF
+ *                        box), written with dL/dp_v for the RAW PSF as
+ *                        passed to mvd_create (through the normalisation of
+ *                        Eq. 3 and the compound kernel).
+ *            The floors max(., eps) pass gradient only where inactive; eps
+ *            is held fixed. Volume work runs on the direct engine in FP32
+ *            (MVD_ERR_UNSUPPORTED for PSF boxes it cannot stage, or more than
+ *            32 views). Synchronises the stream. MVD_ERR_STATE without a
+ *            forward run.
+ */
+mvd_status mvd_unrolled_forward(mvd_ctx* ctx, int n_iter);
+mvd_status mvd_unrolled_backward(mvd_ctx* ctx, const float* grad_psi, float* const* grad_views,
+                                 float* const* grad_psfs);
+
+/*
+ * Gaussian PSF model (host, FP64 arithmetic, FP32 output) for calibration:
+ * p(d) = exp(-0.5 * u^T diag(1/v) u) / sum, u = R^T d, R the rotation about
+ * y by angle_deg (x towards z), v = sigma_xy^2 on the two lateral axes and
+ * sigma_ax^2 on axis (0 = x, 1 = y, 2 = z), on a centred box (odd sizes;
+ * MVD_ERR_SHAPE otherwise). mvd_gaussian_psf_vjp returns
+ * grad_sigma = {dL/dsigma_xy, dL/dsigma_ax} for grad_psf = dL/dp (host,
+ * box layout). Sigmas must be > 0 (MVD_ERR_ARG).
+ */
+mvd_status mvd_gaussian_psf(double sigma_xy, double sigma_ax, double angle_deg, int axis, const int box[3],
+                            float* out);
+mvd_status mvd_gaussian_psf_vjp(double sigma_xy, double sigma_ax, double angle_deg, int axis, const int box[3],
+                                const float* grad_psf, double grad_sigma[2]);
+
+/*
  * Allocation-free view update. The paper has no counterpart: this entry point
  * serves callers that cannot call cudaMalloc, such as applications whose
  * device memory belongs to a caching allocator that must see every

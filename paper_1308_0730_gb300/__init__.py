@@ -28,4 +28,8 @@ from .mvd import (  # noqa: F401
     mvd_batch_wait,
     mvd_batch_tasks,
     mvd_batch_destroy,
+    mvd_unrolled_forward,
+    mvd_unrolled_backward,
+    mvd_gaussian_psf,
+    mvd_gaussian_psf_vjp,
 )

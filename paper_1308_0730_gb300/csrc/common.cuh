@@ -132,6 +132,11 @@ mvd_status build_compound(int n_views, const float* d_psf, const long* koff_h, c
                           int v, int variant, float* d_out, float* d_tmp, double* d_red,
                           cudaStream_t st);
 mvd_status normalize_kernel(float* d_k, int n, int* d_bad, cudaStream_t st);
+mvd_status mirror_kernel(const float* k, const int kd[3], float* out, cudaStream_t st);
+mvd_status autocorr_kernel(const float* P, const int kd[3], float* Q, cudaStream_t st);  // Q box = 2K-1
+mvd_status direct_conv_add(const int dims[3], const float* in, const float* k, const int kd[3], float* out,
+                           cudaStream_t st);
+mvd_status one_update(mvd_ctx* c, int v);
 mvd_status place_kernel(const int dims[3], const float* k, const int kd[3], float* vol,
                         cudaStream_t st);
 mvd_status view_stats(const float* views, long n, double* d_sum, int* d_bad, cudaStream_t st);
@@ -180,6 +185,13 @@ struct mvd_ctx {
         unsigned nodes;
     };
     std::map<std::vector<int>, Graph> graphs;
+
+    // unrolled iteration for differentiation: psi at the start of every
+    // iteration, then psi_K (n_iter + 1 volumes)
+    float* d_ckpt = nullptr;
+    long ckpt_iters = -1;
+    int ckpt_flat = 0;           // the unrolled run started from the flat estimate
+    std::vector<double> psf_sum;  // sums of the raw PSFs (normalisation)
 
     int state = 0;  // 1 created, 2 kernels precomputed
     int variant = -1;

@@ -14,14 +14,20 @@ namespace mvd {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, TZ = 4;
-constexpr int kThreads = TX * TY;
+constexpr int TX = 32, TZ = 4;
 constexpr size_t kMaxSmem = 200 * 1024;
 
-inline size_t smem_bytes(const int kd[3]) {
+// tile height TY (8, 4, 2 or 1 rows of 32 threads): the largest whose input
+// tile + halo and kernel taps fit in shared memory
+inline size_t smem_bytes(const int kd[3], int ty) {
     const size_t T = (size_t)kd[0] * kd[1] * kd[2];
-    const size_t tile = (size_t)(TX + kd[0] - 1) * (TY + kd[1] - 1) * (TZ + kd[2] - 1);
+    const size_t tile = (size_t)(TX + kd[0] - 1) * (ty + kd[1] - 1) * (TZ + kd[2] - 1);
     return (T + tile) * sizeof(float);
+}
+inline int pick_ty(const int kd[3]) {
+    for (int ty : {8, 4, 2, 1})
+        if (smem_bytes(kd, ty) <= kMaxSmem) return ty;
+    return 0;
 }
 
 struct DArgs {
@@ -33,9 +39,10 @@ struct DArgs {
     float eps;
 };
 
-// MODE 0: out = phi / max(conv, eps); MODE 1: out = max(out . conv, eps); MODE 2: out = conv
-template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_direct(DArgs a) {
+// MODE 0: out = phi / max(conv, eps); MODE 1: out = max(out . conv, eps); MODE 2: out = conv;
+// MODE 3: out += conv
+template <int MODE, int TY>
+__global__ void __launch_bounds__(TX * TY) k_direct(DArgs a) {
     extern __shared__ float smem[];
     const int T = a.Kx * a.Ky * a.Kz;
     float* sk = smem;
@@ -58,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_direct(DArgs a) {
     }
     __syncthreads();
 
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;  // ty < TY
     float acc[TZ];
 #pragma unroll
     for (int o = 0; o < TZ; ++o) acc[o] = 0.f;
@@ -90,27 +97,40 @@ __global__ void __launch_bounds__(kThreads) k_direct(DArgs a) {
             a.out[g] = __ldg(a.phi + g) / fmaxf(acc[o], a.eps);
         else if (MODE == 1)
             a.out[g] = fmaxf(a.out[g] * acc[o], a.eps);
-        else
+        else if (MODE == 2)
             a.out[g] = acc[o];
+        else
+            a.out[g] += acc[o];
     }
 }
 
-template <int MODE>
-mvd_status launch(const DArgs& a, const int kd[3], cudaStream_t st, const char* name) {
-    const size_t sm = smem_bytes(kd);
-    if (sm > kMaxSmem) {
-        set_error("%s: kernel box %dx%dx%d too large for the direct engine", name, kd[0], kd[1], kd[2]);
-        return MVD_ERR_UNSUPPORTED;
-    }
-    cudaError_t e = cudaFuncSetAttribute(k_direct<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <int MODE, int TY>
+mvd_status launch_ty(const DArgs& a, size_t sm, cudaStream_t st, const char* name) {
+    cudaError_t e = cudaFuncSetAttribute(k_direct<MODE, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_status(e, name);
     dim3 grid((a.X + TX - 1) / TX, (a.Y + TY - 1) / TY, (a.Z + TZ - 1) / TZ);
     const int cls = MODE == 0 ? KC_DIRECT_RATIO : MODE == 1 ? KC_DIRECT_UPDATE : KC_SETUP;
     prof_begin(cls, st);
-    k_direct<MODE><<<grid, kThreads, sm, st>>>(a);
+    k_direct<MODE, TY><<<grid, TX * TY, sm, st>>>(a);
     prof_end(cls, st);
     count_launch();
     return check_launch(name);
+}
+
+template <int MODE>
+mvd_status launch(const DArgs& a, const int kd[3], cudaStream_t st, const char* name) {
+    const int ty = pick_ty(kd);
+    if (ty == 0) {
+        set_error("%s: kernel box %dx%dx%d too large for the direct engine", name, kd[0], kd[1], kd[2]);
+        return MVD_ERR_UNSUPPORTED;
+    }
+    const size_t sm = smem_bytes(kd, ty);
+    switch (ty) {
+        case 8: return launch_ty<MODE, 8>(a, sm, st, name);
+        case 4: return launch_ty<MODE, 4>(a, sm, st, name);
+        case 2: return launch_ty<MODE, 2>(a, sm, st, name);
+        default: return launch_ty<MODE, 1>(a, sm, st, name);
+    }
 }
 
 DArgs make(const int dims[3], const float* in, const float* k, const int kd[3]) {
@@ -128,7 +148,7 @@ DArgs make(const int dims[3], const float* in, const float* k, const int kd[3]) 
 
 }  // namespace
 
-bool direct_supported(const int kd[3]) { return smem_bytes(kd) <= kMaxSmem; }
+bool direct_supported(const int kd[3]) { return pick_ty(kd) > 0; }
 
 mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, const int kd[3],
                         const float* phi, float eps, float* r, cudaStream_t st) {
@@ -152,6 +172,13 @@ mvd_status direct_conv(const int dims[3], const float* in, const float* k, const
     DArgs a = make(dims, in, k, kd);
     a.out = out;
     return launch<2>(a, kd, st, "direct conv");
+}
+
+mvd_status direct_conv_add(const int dims[3], const float* in, const float* k, const int kd[3], float* out,
+                           cudaStream_t st) {
+    DArgs a = make(dims, in, k, kd);
+    a.out = out;
+    return launch<3>(a, kd, st, "direct conv add");
 }
 
 }  // namespace mvd

@@ -173,6 +173,7 @@ void free_fft(mvd_ctx* c) {
 
 void free_all(mvd_ctx* c) {
     drop_graphs(c);
+    dev_free(c->d_ckpt);
     free_fft(c);
     dev_free(c->d_views);
     dev_free(c->d_psi);
@@ -285,7 +286,9 @@ mvd_status setup_fft(mvd_ctx* c) {
     return MVD_OK;
 }
 
-mvd_status one_update(mvd_ctx* c, int v) {
+}  // namespace
+
+mvd_status mvd::one_update(mvd_ctx* c, int v) {
     const float* phi = c->d_views + (size_t)v * c->M;
     const int* kd = &c->kd[3 * v];
     if (c->path == MVD_PATH_DIRECT) {
@@ -321,6 +324,8 @@ mvd_status one_update(mvd_ctx* c, int v) {
     MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
     return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream);
 }
+
+namespace {
 
 mvd_status read_flag(mvd_ctx* c, int* flag) {
     MVD_CUDA(cudaMemcpyAsync(flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -406,6 +411,7 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     }
     // PSF shapes and values; normalise to sum 1 (Eq. 3)
     std::vector<float> psf_h;
+    std::vector<double> psf_sum;
     std::vector<long> koff(n_views);
     long ktotal = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -440,6 +446,7 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
             return MVD_ERR_ARG;
         }
         for (long i = 0; i < T; ++i) psf_h.push_back((float)(psfs[v][i] / s));
+        psf_sum.push_back(s);
         ktotal += T;
     }
 
@@ -459,6 +466,7 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     c->kd.assign(psf_dims, psf_dims + 3 * n_views);
     c->koff = koff;
     c->ktotal = ktotal;
+    c->psf_sum = psf_sum;
     c->path_opt = opt.path;
     c->precise = opt.precision == MVD_PRECISE ? 1 : 0;
 

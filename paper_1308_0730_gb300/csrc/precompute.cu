@@ -186,6 +186,21 @@ mvd_status build_compound(int n_views, const float* d_psf, const long* koff, con
     return MVD_OK;
 }
 
+mvd_status mirror_kernel(const float* k, const int kd[3], float* out, cudaStream_t st) {
+    const Box b = box_of(kd);
+    k_mirror<<<blocks_for((long)b.kx * b.ky * b.kz), kThreads, 0, st>>>(k, b, out);
+    count_launch();
+    return check_launch("mirror kernel");
+}
+
+mvd_status autocorr_kernel(const float* P, const int kd[3], float* Q, cudaStream_t st) {
+    const Box b = box_of(kd);
+    const Box q{2 * b.kx - 1, 2 * b.ky - 1, 2 * b.kz - 1};
+    k_autocorr<<<blocks_for((long)q.kx * q.ky * q.kz), kThreads, 0, st>>>(P, b, Q, q);
+    count_launch();
+    return check_launch("autocorrelation");
+}
+
 mvd_status normalize_kernel(float* d_k, int n, int* d_bad, cudaStream_t st) {
     k_normalize<<<1, 1024, 0, st>>>(d_k, n, d_bad);
     count_launch();

@@ -29,7 +29,8 @@ EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_s
            "mvd_result", "mvd_result_device", "mvd_synchronize", "mvd_destroy", "mvd_last_error",
            "mvd_get_eps", "mvd_get_psi0", "mvd_get_path", "mvd_get_compound_kernel", "mvd_launch_count",
            "mvd_profile_enable", "mvd_profile_read", "mvd_update_direct_noalloc", "mvd_batch_create",
-           "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy"]
+           "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy", "mvd_unrolled_forward",
+           "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp"]
 
 
 class MvdError(RuntimeError):
@@ -100,7 +101,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_batch_tasks.restype = ctypes.c_longlong
     lib.mvd_batch_destroy.argtypes = [vp]
     lib.mvd_batch_destroy.restype = None
-    for name in ("mvd_create", "mvd_precompute_kernels", "mvd_set_estimate", "mvd_iterate", "mvd_result",
+    lib.mvd_unrolled_forward.argtypes = [vp, ci]
+    lib.mvd_unrolled_backward.argtypes = [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    _DP = ctypes.POINTER(ctypes.c_double)
+    lib.mvd_gaussian_psf.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ci, ctypes.POINTER(ci), _FP]
+    lib.mvd_gaussian_psf_vjp.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ci, ctypes.POINTER(ci),
+                                         _FP, _DP]
+    for name in ("mvd_unrolled_forward", "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp",
+                 "mvd_create", "mvd_precompute_kernels", "mvd_set_estimate", "mvd_iterate", "mvd_result",
                  "mvd_result_device", "mvd_synchronize", "mvd_get_compound_kernel"):
         getattr(lib, name).restype = ci
     _lib = lib
@@ -284,6 +292,48 @@ def mvd_batch_tasks(batch) -> int:
 def mvd_batch_destroy(batch):
     if batch:
         load().mvd_batch_destroy(batch)
+
+
+def mvd_unrolled_forward(ctx, n_iter: int):
+    """n_iter iterations from the flat start, keeping per-iteration checkpoints."""
+    _check(load().mvd_unrolled_forward(ctx, int(n_iter)))
+
+
+def mvd_unrolled_backward(ctx, grad_psi, grad_views, psf_shapes):
+    """Reverse pass of the last unrolled forward run.
+
+    ``grad_psi``: contiguous float32 CUDA tensor ``[Z][Y][X]``; ``grad_views``:
+    CUDA tensors of the same shape, overwritten with dL/dphi_v. Returns the
+    raw-PSF gradients as float32 numpy arrays shaped ``psf_shapes``.
+    """
+    gp = [np.empty(sh, dtype=np.float32) for sh in psf_shapes]
+    gv = (ctypes.c_void_p * len(grad_views))(*[ctypes.c_void_p(int(g.data_ptr())) for g in grad_views])
+    gpp = (ctypes.c_void_p * len(gp))(*[ctypes.c_void_p(g.ctypes.data) for g in gp])
+    _check(load().mvd_unrolled_backward(ctx, ctypes.c_void_p(int(grad_psi.data_ptr())), gv, gpp))
+    return gp
+
+
+_AXES = {"x": 0, "y": 1, "z": 2}
+
+
+def mvd_gaussian_psf(sigma_xy: float, sigma_ax: float, box_xyz, angle_deg: float = 0.0, axis="z") -> np.ndarray:
+    """Gaussian PSF model sampled on the centred box ``box_xyz`` (Kx, Ky, Kz); shaped ``[Kz][Ky][Kx]``."""
+    box = (ctypes.c_int * 3)(*[int(b) for b in box_xyz])
+    out = np.empty((box_xyz[2], box_xyz[1], box_xyz[0]), dtype=np.float32)
+    _check(load().mvd_gaussian_psf(float(sigma_xy), float(sigma_ax), float(angle_deg), _AXES.get(axis, axis), box,
+                                   out.ctypes.data_as(_FP)))
+    return out
+
+
+def mvd_gaussian_psf_vjp(sigma_xy: float, sigma_ax: float, box_xyz, grad_psf, angle_deg: float = 0.0,
+                         axis="z") -> np.ndarray:
+    """(dL/dsigma_xy, dL/dsigma_ax) for dL/dPSF ``grad_psf`` (``[Kz][Ky][Kx]``)."""
+    box = (ctypes.c_int * 3)(*[int(b) for b in box_xyz])
+    g = _host_f32(grad_psf)
+    out = np.zeros(2, dtype=np.float64)
+    _check(load().mvd_gaussian_psf_vjp(float(sigma_xy), float(sigma_ax), float(angle_deg), _AXES.get(axis, axis), box,
+                                       g.ctypes.data_as(_FP), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 class Deconvolver:
