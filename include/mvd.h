@@ -69,12 +69,15 @@ typedef enum {
 /* Convolution engine. AUTO lets the autotuner pick per (dims, PSF boxes). */
 typedef enum { MVD_PATH_AUTO = 0, MVD_PATH_DIRECT = 1, MVD_PATH_FFT = 2 } mvd_path;
 
-/* Arithmetic of the FFT engine's forward blur b = psi * P_v.
+/* Arithmetic of the FFT engine.
  *   MVD_PRECISE: double-float (pairs of FP32, about 48 significant bits) for
- *     the forward blur, FP32 for the back-projection. FP32 FFT rounding is
- *     absolute (it scales with the whole volume's norm), so in FP32 the dim
- *     voxels of b carry large relative errors that the ratio phi / b and the
- *     iteration amplify; double-float removes them.
+ *     the whole forward blur b = psi * P_v and for the back-projection's y, z
+ *     and inverse x passes; the back-projection's forward x pass transforms
+ *     r - 1 in FP32 (c = (r - 1) * K + 1 holds because K sums to 1, and r - 1
+ *     is small where the estimate fits). FP32 FFT rounding is absolute (it
+ *     scales with the whole volume's norm), so in FP32 the dim voxels of b
+ *     carry large relative errors that the ratio phi / b and the iteration
+ *     amplify; double-float removes them.
  *   MVD_FAST: everything in FP32 (faster; after tens of iterations dim voxels
  *     differ from an exact computation by about 1e-3 relative). */
 typedef enum { MVD_PRECISE = 0, MVD_FAST = 1 } mvd_precision;
@@ -117,8 +120,10 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
 /*
  * Builds P_v^comp for every view on the device (FP32) for the given
  * mvd_variant (Eq. 222 / Eq. 230 / Eq. 240 / Eq. 51), normalised to sum 1,
- * on P_v's own box; chooses the convolution engine (autotuner when the path
- * is AUTO) and, for the FFT engine, builds the two kernel spectra per view.
+ * on P_v's own box; chooses the convolution engine (with MVD_PATH_AUTO: the
+ * autotuner's cached choice for this shape if MVD_TUNE_CACHE holds one, else
+ * a cost model of both engines; see mvd_autotune) and, for the FFT engine,
+ * builds the two kernel spectra per view.
  * May be called again to switch variant.
  */
 mvd_status mvd_precompute_kernels(mvd_ctx* ctx, int variant);
@@ -205,6 +210,31 @@ mvd_status mvd_batch_run(mvd_batch* batch);
 mvd_status mvd_batch_wait(mvd_batch* batch);
 long long mvd_batch_tasks(const mvd_batch* batch);
 void mvd_batch_destroy(mvd_batch* batch);
+
+/*
+ * Autotuner: picks the engine (direct tiled convolution or FFT) and its tile
+ * shape for this problem by timing one pass of view updates per candidate on
+ * the context's own data (the estimate is restored afterwards), then sets the
+ * fastest on the context. Candidates: the FFT engine with register-resident
+ * power-of-two passes and with mixed-radix Stockham passes (where the dims
+ * are {2,3,5}-smooth), and the direct engine with output tiles of 32 x ty x 4
+ * for every ty in {8,4,2,1} whose staging fits in shared memory.
+ * The choice is persisted per (dims, precision, PSF boxes, GPU model) as one
+ * text line appended to cache_path (NULL = the MVD_TUNE_CACHE environment
+ * variable; neither = not persisted). An existing entry is applied without
+ * timing (from_cache = 1), and mvd_precompute_kernels with MVD_PATH_AUTO
+ * applies a cached entry for its shape when MVD_TUNE_CACHE names a file.
+ * Needs a precomputed context (MVD_ERR_STATE); synchronises the stream; out
+ * may be NULL. Drops the context's captured graphs.
+ */
+typedef struct {
+    int path;             /* MVD_PATH_DIRECT or MVD_PATH_FFT */
+    int direct_tile_y;    /* direct engine: output tile height ty; 0 for FFT */
+    int fft_engine;       /* FFT: 1 register-resident passes, 0 Stockham passes; -1 for direct */
+    int from_cache;       /* 1 when read from the cache without timing */
+    double ms_per_update; /* measured time of one view update (ms) */
+} mvd_tune_result;
+mvd_status mvd_autotune(mvd_ctx* ctx, const char* cache_path, mvd_tune_result* out);
 
 /*
  * Differentiation of the unrolled iteration, for calibrating PSF parameters

@@ -28,6 +28,7 @@ from .mvd import (  # noqa: F401
     mvd_batch_wait,
     mvd_batch_tasks,
     mvd_batch_destroy,
+    mvd_autotune,
     mvd_unrolled_forward,
     mvd_unrolled_backward,
     mvd_gaussian_psf,

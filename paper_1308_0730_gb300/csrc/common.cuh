@@ -120,10 +120,13 @@ mvd_status fft_x_update_dd_fast(const FftGeom& g, const cdd* S2, float* psi, flo
 
 // Direct (spatial) periodic convolution with fused epilogues.
 bool direct_supported(const int kd[3]);
+// ty = output tile height (8, 4, 2 or 1 rows of 32 x 4 outputs); 0 = the
+// largest whose staging fits in shared memory
 mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, const int kd[3],
-                        const float* phi, float eps, float* r, cudaStream_t st);
+                        const float* phi, float eps, float* r, cudaStream_t st, int ty = 0);
 mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
-                         float* psi, float eps, cudaStream_t st);
+                         float* psi, float eps, cudaStream_t st, int ty = 0);
+int direct_tile_heights(const int kd[3], int out[4]);  // tile heights that fit, largest first
 mvd_status direct_conv(const int dims[3], const float* in, const float* k, const int kd[3],
                        float* out, cudaStream_t st);
 
@@ -196,6 +199,7 @@ struct mvd_ctx {
     int state = 0;  // 1 created, 2 kernels precomputed
     int variant = -1;
     int path_opt = MVD_PATH_AUTO;
+    int direct_ty = 0;  // direct-engine tile height chosen by the autotuner (0 = default)
     int path = MVD_PATH_AUTO;
     float psi0 = 0.f, eps = 0.f;
 };

@@ -118,8 +118,10 @@ mvd_status launch_ty(const DArgs& a, size_t sm, cudaStream_t st, const char* nam
 }
 
 template <int MODE>
-mvd_status launch(const DArgs& a, const int kd[3], cudaStream_t st, const char* name) {
-    const int ty = pick_ty(kd);
+mvd_status launch(const DArgs& a, const int kd[3], cudaStream_t st, const char* name, int ty_req = 0) {
+    const int ty = (ty_req == 8 || ty_req == 4 || ty_req == 2 || ty_req == 1) && smem_bytes(kd, ty_req) <= kMaxSmem
+                       ? ty_req
+                       : pick_ty(kd);
     if (ty == 0) {
         set_error("%s: kernel box %dx%dx%d too large for the direct engine", name, kd[0], kd[1], kd[2]);
         return MVD_ERR_UNSUPPORTED;
@@ -150,21 +152,28 @@ DArgs make(const int dims[3], const float* in, const float* k, const int kd[3]) 
 
 bool direct_supported(const int kd[3]) { return pick_ty(kd) > 0; }
 
+int direct_tile_heights(const int kd[3], int out[4]) {
+    int n = 0;
+    for (int ty : {8, 4, 2, 1})
+        if (smem_bytes(kd, ty) <= kMaxSmem) out[n++] = ty;
+    return n;
+}
+
 mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, const int kd[3],
-                        const float* phi, float eps, float* r, cudaStream_t st) {
+                        const float* phi, float eps, float* r, cudaStream_t st, int ty) {
     DArgs a = make(dims, psi, k, kd);
     a.phi = phi;
     a.out = r;
     a.eps = eps;
-    return launch<0>(a, kd, st, "direct ratio");
+    return launch<0>(a, kd, st, "direct ratio", ty);
 }
 
 mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
-                         float* psi, float eps, cudaStream_t st) {
+                         float* psi, float eps, cudaStream_t st, int ty) {
     DArgs a = make(dims, r, k, kd);
     a.out = psi;
     a.eps = eps;
-    return launch<1>(a, kd, st, "direct update");
+    return launch<1>(a, kd, st, "direct update", ty);
 }
 
 mvd_status direct_conv(const int dims[3], const float* in, const float* k, const int kd[3], float* out,

@@ -1,5 +1,6 @@
 // C ABI of the mvd library (declared in include/mvd.h): context life cycle,
 // precompute, the sequential update loop and result access.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -288,12 +289,121 @@ mvd_status setup_fft(mvd_ctx* c) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// autotuner (engine and tile choice per problem shape, timed on the context's
+// own data, persisted in a text cache)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TuneChoice {
+    int path = MVD_PATH_FFT;
+    int ty = 0;
+    int fast = 1;
+    double ms = 0.0;
+};
+
+std::string tune_key(const mvd_ctx* c) {
+    std::string k = "mvd-tune-v1 dims " + std::to_string(c->dims[0]) + " " + std::to_string(c->dims[1]) + " " +
+                    std::to_string(c->dims[2]) + " precision " + std::to_string(c->precise ? 0 : 1) + " boxes";
+    for (int v = 0; v < c->nv; ++v)
+        for (int a = 0; a < 3; ++a) k += " " + std::to_string(c->kd[3 * v + a]);
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+        std::string name = prop.name;
+        for (char& ch : name)
+            if (ch == ' ' || ch == '|') ch = '_';
+        k += " gpu " + name + " sms " + std::to_string(prop.multiProcessorCount);
+    }
+    return k;
+}
+
+// cache line: "<key> | <path> <tile height> <fast> <ms per update>"
+bool tune_lookup(const char* path, const std::string& key, TuneChoice* out) {
+    if (!path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[4096];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        const char* bar = std::strchr(line, '|');
+        if (!bar) continue;
+        std::string k(line, bar - line);
+        while (!k.empty() && k.back() == ' ') k.pop_back();
+        if (k != key) continue;
+        TuneChoice t;
+        if (std::sscanf(bar + 1, "%d %d %d %lf", &t.path, &t.ty, &t.fast, &t.ms) != 4) continue;
+        if (t.path != MVD_PATH_DIRECT && t.path != MVD_PATH_FFT) continue;
+        *out = t;  // the last valid entry wins
+        found = true;
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_store(const char* path, const std::string& key, const TuneChoice& t) {
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s | %d %d %d %.6f\n", key.c_str(), t.path, t.ty, t.fast, t.ms);
+    std::fclose(f);
+}
+
+void apply_choice(mvd_ctx* c, const TuneChoice& t) {
+    drop_graphs(c);
+    c->path = t.path;
+    c->direct_ty = t.path == MVD_PATH_DIRECT ? t.ty : 0;
+    c->geom.fast = t.fast != 0;
+}
+
+// milliseconds per view update of the configuration now set on c: one warm
+// update, then one pass over all views; the estimate is restored afterwards
+mvd_status time_updates(mvd_ctx* c, float* psi_save, double cutoff_ms, double* ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MVD_CUDA(cudaEventCreate(&e0));
+    MVD_CUDA(cudaEventCreate(&e1));
+    mvd_status st = MVD_OK;
+    float t_warm = 0.f, t_all = 0.f;
+    do {
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) { st = MVD_ERR_CUDA; break; }
+        if ((st = one_update(c, 0)) != MVD_OK) break;
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            st = MVD_ERR_CUDA;
+            break;
+        }
+        cudaEventElapsedTime(&t_warm, e0, e1);
+        if (cutoff_ms > 0 && t_warm > 4.0 * cutoff_ms) {  // far slower than the best so far: skip the timed pass
+            *ms = t_warm;
+            break;
+        }
+        cudaEventRecord(e0, c->stream);
+        for (int v = 0; v < c->nv && st == MVD_OK; ++v) st = one_update(c, v);
+        if (st != MVD_OK) break;
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            st = MVD_ERR_CUDA;
+            break;
+        }
+        cudaEventElapsedTime(&t_all, e0, e1);
+        *ms = t_all / c->nv;
+    } while (false);
+    if (st == MVD_ERR_CUDA) set_error("autotune: timing failed");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaMemcpyAsync(c->d_psi, psi_save, sizeof(float) * c->M, cudaMemcpyDeviceToDevice, c->stream);
+    if (st == MVD_OK && e != cudaSuccess) st = cuda_status(e, "autotune: restore estimate");
+    return st;
+}
+
+}  // namespace
+
 mvd_status mvd::one_update(mvd_ctx* c, int v) {
     const float* phi = c->d_views + (size_t)v * c->M;
     const int* kd = &c->kd[3 * v];
     if (c->path == MVD_PATH_DIRECT) {
-        MVD_TRY(direct_ratio(c->dims, c->d_psi, c->d_psf + c->koff[v], kd, phi, c->eps, c->d_r, c->stream));
-        return direct_update(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_psi, c->eps, c->stream);
+        MVD_TRY(direct_ratio(c->dims, c->d_psi, c->d_psf + c->koff[v], kd, phi, c->eps, c->d_r, c->stream,
+                             c->direct_ty));
+        return direct_update(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_psi, c->eps, c->stream,
+                             c->direct_ty);
     }
     const FftGeom& g = c->geom;
     const size_t ns = (size_t)g.Xh * g.YZ;
@@ -537,6 +647,7 @@ mvd_status mvd_precompute_kernels(mvd_ctx* c, int variant) {
     DeviceGuard dg(c->device);
     drop_graphs(c);
     free_fft(c);
+    c->direct_ty = 0;
     dev_free(c->d_comp);
     dev_free(c->d_ktmp);
     c->state = 1;
@@ -563,6 +674,23 @@ mvd_status mvd_precompute_kernels(mvd_ctx* c, int variant) {
     }
     int path = c->path_opt;
     const bool fft_ok = smooth235(c->dims[0]) && smooth235(c->dims[1]) && smooth235(c->dims[2]);
+    TuneChoice cached;
+    const bool use_cached = path == MVD_PATH_AUTO && tune_lookup(std::getenv("MVD_TUNE_CACHE"), tune_key(c), &cached);
+    if (use_cached) {
+        bool ok = cached.path == MVD_PATH_FFT ? fft_ok : true;
+        for (int v = 0; v < c->nv && cached.path == MVD_PATH_DIRECT; ++v) ok = ok && direct_supported(&c->kd[3 * v]);
+        if (ok) {
+            c->path = cached.path;
+            c->direct_ty = cached.path == MVD_PATH_DIRECT ? cached.ty : 0;
+            if (cached.path == MVD_PATH_FFT) {
+                MVD_TRY(setup_fft(c));
+                c->geom.fast = cached.fast != 0;
+            }
+            c->variant = variant;
+            c->state = 2;
+            return MVD_OK;
+        }
+    }
     if (path == MVD_PATH_AUTO) {
         path = choose_path(c);
         if (path < 0) {
@@ -762,6 +890,91 @@ mvd_status mvd_get_compound_kernel(mvd_ctx* c, int v, float* out, size_t n_elems
     DeviceGuard dg(c->device);
     MVD_CUDA(cudaMemcpyAsync(out, c->d_comp + c->koff[v], T * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     MVD_CUDA(cudaStreamSynchronize(c->stream));
+    return MVD_OK;
+}
+
+mvd_status mvd_autotune(mvd_ctx* c, const char* cache_path, mvd_tune_result* out) {
+    clear_error();
+    if (!c) {
+        set_error("mvd_autotune: NULL context");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 2) {
+        set_error("mvd_autotune: kernels not precomputed");
+        return MVD_ERR_STATE;
+    }
+    DeviceGuard dg(c->device);
+    if (!cache_path) cache_path = std::getenv("MVD_TUNE_CACHE");
+    const std::string key = tune_key(c);
+    TuneChoice best;
+    int from_cache = 0;
+    const bool fft_ok = smooth235(c->dims[0]) && smooth235(c->dims[1]) && smooth235(c->dims[2]);
+    bool direct_ok = true;
+    for (int v = 0; v < c->nv; ++v) direct_ok = direct_ok && direct_supported(&c->kd[3 * v]);
+    if (tune_lookup(cache_path, key, &best) && (best.path == MVD_PATH_FFT ? fft_ok : direct_ok)) {
+        from_cache = 1;
+        if (best.path == MVD_PATH_FFT && !c->d_S) MVD_TRY(setup_fft(c));
+    } else {
+        float* save = nullptr;
+        MVD_TRY(dev_alloc(&save, (size_t)c->M, "autotune estimate copy"));
+        mvd_status st = MVD_OK;
+        const cudaError_t ce =
+            cudaMemcpyAsync(save, c->d_psi, sizeof(float) * c->M, cudaMemcpyDeviceToDevice, c->stream);
+        if (ce != cudaSuccess) {
+            dev_free(save);
+            return cuda_status(ce, "autotune: save estimate");
+        }
+        best.ms = -1.0;
+        std::vector<TuneChoice> cands;
+        if (fft_ok) {
+            const bool any_fast = fft_fast_supported(c->dims[0]) || fft_fast_supported(c->dims[1]) ||
+                                  fft_fast_z_supported(c->dims[2]);
+            if (any_fast) cands.push_back({MVD_PATH_FFT, 0, 1, 0.0});
+            cands.push_back({MVD_PATH_FFT, 0, 0, 0.0});
+        }
+        if (direct_ok) {
+            // tile heights that fit every view's box
+            int common[4] = {8, 4, 2, 1};
+            for (int ty : common) {
+                bool fits = true;
+                for (int v = 0; v < c->nv; ++v) {
+                    int opts[4];
+                    const int n = direct_tile_heights(&c->kd[3 * v], opts);
+                    fits = fits && std::find(opts, opts + n, ty) != opts + n;
+                }
+                if (fits) cands.push_back({MVD_PATH_DIRECT, ty, 1, 0.0});
+            }
+        }
+        const int prev_path = c->path, prev_ty = c->direct_ty, prev_fast = c->geom.fast ? 1 : 0;
+        for (size_t i = 0; i < cands.size() && st == MVD_OK; ++i) {
+            TuneChoice t = cands[i];
+            if (t.path == MVD_PATH_FFT && !c->d_S && (st = setup_fft(c)) != MVD_OK) break;
+            apply_choice(c, t);
+            double ms = 0.0;
+            if ((st = time_updates(c, save, best.ms, &ms)) != MVD_OK) break;
+            t.ms = ms;
+            if (best.ms < 0 || ms < best.ms) best = t;
+        }
+        dev_free(save);
+        if (st != MVD_OK) {
+            apply_choice(c, {prev_path, prev_ty, prev_fast, 0.0});
+            return st;
+        }
+        if (best.ms < 0) {
+            set_error("mvd_autotune: no engine fits this problem");
+            return MVD_ERR_UNSUPPORTED;
+        }
+        tune_store(cache_path, key, best);
+    }
+    apply_choice(c, best);
+    if (best.path == MVD_PATH_DIRECT) free_fft(c);
+    if (out) {
+        out->path = best.path;
+        out->direct_tile_y = best.path == MVD_PATH_DIRECT ? best.ty : 0;
+        out->fft_engine = best.path == MVD_PATH_FFT ? best.fast : -1;
+        out->from_cache = from_cache;
+        out->ms_per_update = best.ms;
+    }
     return MVD_OK;
 }
 

@@ -30,7 +30,7 @@ EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_s
            "mvd_get_eps", "mvd_get_psi0", "mvd_get_path", "mvd_get_compound_kernel", "mvd_launch_count",
            "mvd_profile_enable", "mvd_profile_read", "mvd_update_direct_noalloc", "mvd_batch_create",
            "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy", "mvd_unrolled_forward",
-           "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp"]
+           "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp", "mvd_autotune"]
 
 
 class MvdError(RuntimeError):
@@ -42,6 +42,11 @@ class MvdError(RuntimeError):
 
 MVD_PRECISE, MVD_FAST = 0, 1
 PRECISIONS = {"precise": MVD_PRECISE, "fast": MVD_FAST}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("direct_tile_y", ctypes.c_int), ("fft_engine", ctypes.c_int),
+                ("from_cache", ctypes.c_int), ("ms_per_update", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):
@@ -101,13 +106,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_batch_tasks.restype = ctypes.c_longlong
     lib.mvd_batch_destroy.argtypes = [vp]
     lib.mvd_batch_destroy.restype = None
+    lib.mvd_autotune.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(TuneResult)]
     lib.mvd_unrolled_forward.argtypes = [vp, ci]
     lib.mvd_unrolled_backward.argtypes = [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
     _DP = ctypes.POINTER(ctypes.c_double)
     lib.mvd_gaussian_psf.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ci, ctypes.POINTER(ci), _FP]
     lib.mvd_gaussian_psf_vjp.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ci, ctypes.POINTER(ci),
                                          _FP, _DP]
-    for name in ("mvd_unrolled_forward", "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp",
+    for name in ("mvd_autotune", "mvd_unrolled_forward", "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp",
                  "mvd_create", "mvd_precompute_kernels", "mvd_set_estimate", "mvd_iterate", "mvd_result",
                  "mvd_result_device", "mvd_synchronize", "mvd_get_compound_kernel"):
         getattr(lib, name).restype = ci
@@ -294,6 +300,16 @@ def mvd_batch_destroy(batch):
         load().mvd_batch_destroy(batch)
 
 
+def mvd_autotune(ctx, cache_path=None) -> dict:
+    """Times the engine candidates on this context and keeps the fastest (see include/mvd.h)."""
+    r = TuneResult()
+    cp = None if cache_path is None else os.fsencode(cache_path)
+    _check(load().mvd_autotune(ctx, cp, ctypes.byref(r)))
+    return {"path": {MVD_PATH_DIRECT: "direct", MVD_PATH_FFT: "fft"}[r.path], "direct_tile_y": r.direct_tile_y,
+            "fft_engine": {1: "register", 0: "stockham", -1: None}[r.fft_engine], "from_cache": bool(r.from_cache),
+            "ms_per_update": r.ms_per_update}
+
+
 def mvd_unrolled_forward(ctx, n_iter: int):
     """n_iter iterations from the flat start, keeping per-iteration checkpoints."""
     _check(load().mvd_unrolled_forward(ctx, int(n_iter)))
@@ -360,6 +376,9 @@ class Deconvolver:
         if out is None:
             out = np.empty(self.shape, dtype=np.float32)
         return mvd_result(self.ctx, out)
+
+    def autotune(self, cache_path=None) -> dict:
+        return mvd_autotune(self.ctx, cache_path)
 
     def compound_kernel(self, v):
         return mvd_get_compound_kernel(self.ctx, v, self.psf_shapes[v])

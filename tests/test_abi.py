@@ -106,3 +106,7 @@ def test_null_context_calls_fail_cleanly(lib):
     lib.mvd_destroy(None)
     assert lib.mvd_get_path(None) == -1
     assert isinstance(mvd.mvd_launch_count(), int)
+    assert lib.mvd_autotune(None, None, None) == mvd.MVD_ERR_ARG
+    assert lib.mvd_unrolled_forward(None, 1) == mvd.MVD_ERR_ARG
+    assert lib.mvd_unrolled_backward(None, None, None, None) == mvd.MVD_ERR_ARG
+    assert "NULL" in mvd.mvd_last_error()

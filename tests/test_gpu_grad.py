@@ -44,7 +44,7 @@ def _gpu_run(env, w, psfs, n_iter, variant="efficient", path="auto"):
     truth = torch.from_numpy(np.asarray(w.truth, np.float32)).cuda()
     loss = torch.mean((psi.double() - truth.double()) ** 2)
     loss.backward()
-    return float(loss), psi.detach().cpu().numpy(), views.grad.cpu().numpy(), [p.grad.numpy() for p in ps]
+    return float(loss.detach()), psi.detach().cpu().numpy(), views.grad.cpu().numpy(), [p.grad.numpy() for p in ps]
 
 
 @pytest.fixture(scope="module")
@@ -108,7 +108,7 @@ def _sigma_chain(env, w, sigmas, n_iter):
     truth = torch.from_numpy(w.truth).cuda()
     loss = torch.mean((psi.double() - truth.double()) ** 2)
     loss.backward()
-    return float(loss), np.array([s.grad.numpy() for s in sig])
+    return float(loss.detach()), np.array([s.grad.numpy() for s in sig])
 
 
 def test_sigma_gradient_matches_finite_differences_24cubed(env):
