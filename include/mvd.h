@@ -190,22 +190,36 @@ int mvd_profile_read(const char** names, unsigned long long* launches, double* m
  * Batched form: many independent problems of uneven size and view count
  * (time points, tiles of a large specimen; the paper processes such units
  * independently, Suppl. Table 1 and main text) advanced together by one
- * persistent kernel launch, captured in a CUDA graph.
- *   ctxs    n contexts, each created and precomputed with the FFT engine,
- *           all on one device and one stream (else MVD_ERR_ARG /
- *           MVD_ERR_STATE / MVD_ERR_UNSUPPORTED). The batch keeps pointers
- *           into them: destroy the batch before any of its contexts, and do
- *           not re-precompute a context while a batch uses it.
+ * launch of a CUDA graph. Two executions (mvd_batch_mode):
+ *   MVD_BATCH_BRANCHES    one graph in which each volume's whole run (the
+ *                         single-volume engine's kernels) is an independent
+ *                         branch; kernels of different volumes run side by
+ *                         side. Needs a non-NULL stream and per-kernel timing
+ *                         off. Any engine.
+ *   MVD_BATCH_PERSISTENT  one persistent kernel over a global work queue of
+ *                         FFT-pass tiles of all volumes, with bounded
+ *                         per-volume dependency waits. FFT engine only.
+ *   MVD_BATCH_AUTO        BRANCHES where it is allowed, else PERSISTENT.
+ *   ctxs    n distinct contexts, each precomputed, all on one device and one
+ *           stream (else MVD_ERR_ARG / MVD_ERR_STATE / MVD_ERR_UNSUPPORTED).
+ *           The batch keeps pointers into them: destroy the batch before any
+ *           of its contexts, and do not re-precompute or autotune a context
+ *           while a batch uses it.
  *   n_iter  iterations of each context's default schedule (views 0..N-1)
  *           per mvd_batch_run.
  * mvd_batch_run enqueues the job on the shared stream (each context's psi
  * advances by n_iter iterations from its current value); mvd_batch_wait
- * synchronises and returns MVD_ERR_TIMEOUT if a block gave up waiting for a
- * dependency (a bounded wait; MVD_BATCH_POLL_LIMIT sets the poll count).
- * mvd_batch_tasks gives the number of tiles in one run.
+ * synchronises and returns MVD_ERR_TIMEOUT if a persistent block gave up
+ * waiting for a dependency (a bounded wait; MVD_BATCH_POLL_LIMIT sets the
+ * poll count). mvd_batch_tasks gives the work items of one run (tiles of the
+ * persistent queue, or kernels of the branch graph); mvd_batch_mode the
+ * execution chosen. mvd_batch_create = mvd_batch_create_mode(..., AUTO, ...).
  */
+typedef enum { MVD_BATCH_AUTO = 0, MVD_BATCH_PERSISTENT = 1, MVD_BATCH_BRANCHES = 2 } mvd_batch_mode_t;
 typedef struct mvd_batch mvd_batch;
 mvd_status mvd_batch_create(mvd_ctx* const* ctxs, int n, int n_iter, mvd_batch** out);
+mvd_status mvd_batch_create_mode(mvd_ctx* const* ctxs, int n, int n_iter, int mode, mvd_batch** out);
+int mvd_batch_mode(const mvd_batch* batch);
 mvd_status mvd_batch_run(mvd_batch* batch);
 mvd_status mvd_batch_wait(mvd_batch* batch);
 long long mvd_batch_tasks(const mvd_batch* batch);

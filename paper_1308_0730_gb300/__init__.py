@@ -28,6 +28,7 @@ from .mvd import (  # noqa: F401
     mvd_batch_wait,
     mvd_batch_tasks,
     mvd_batch_destroy,
+    mvd_batch_mode,
     mvd_autotune,
     mvd_unrolled_forward,
     mvd_unrolled_backward,

@@ -1,5 +1,14 @@
 // Batched form: many independent deconvolution problems (contexts of uneven
-// size and view count) advanced together by ONE persistent kernel launch.
+// size and view count) advanced together by one launch. Two executions:
+//
+// MVD_BATCH_BRANCHES. One CUDA graph in which every volume's whole run (its
+// n_iter iterations of view updates, each the single-volume engine's kernels)
+// is an independent branch. The graph executor runs kernels of different
+// branches side by side, so small volumes, whose kernels fill only part of
+// the GPU, and the tails of large kernels overlap with other volumes' work.
+// Branches start largest volume first.
+//
+// MVD_BATCH_PERSISTENT. ONE persistent kernel launch, described below.
 //
 // Work queue. Every view update of every volume is the same 9 passes
 // (x-forward, y+, z*K_v, y-, x-ratio, y+, z*K_v^comp, y-, x-update); each
@@ -25,6 +34,7 @@
 #include <vector>
 
 #include "fft_dd.cuh"
+#include "fft_dd_fast.cuh"
 #include "fft_fast_tiles.cuh"
 #include "fft_generic.cuh"
 
@@ -85,9 +95,56 @@ __device__ __forceinline__ void with_len(int L, F&& f) {
     }
 }
 
+// precise mode, axes of length 64, 128 or 256: register-resident
+// double-float passes (the same tiles as the single-volume engine)
+__device__ bool run_tile_ddf(const VolDesc& d, int pass, int view, long tile, cdd* sm) {
+    const size_t ns = (size_t)d.Xh * d.YZ;
+    switch (pass) {
+        case XF:
+        case XR: {
+            if (!d.fx) return false;
+            const DdXFast a{d.psi, d.S2, d.views + (size_t)view * d.M, d.YZ, d.eps, d.tw2x, d.px};
+            with_len(d.X, [&](auto Lc) {
+                constexpr int L = decltype(Lc)::value;
+                if (pass == XF)
+                    ddf_x_forward_tile<L, true>(a, tile, sm);
+                else
+                    ddf_x_ratio_tile<L, true>(a, tile, sm);
+            });
+            return true;
+        }
+        case Z1:
+        case Z2: {
+            if (!d.fz) return false;
+            const cdd* K2 = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(d.KP2) +
+                                                         ns * (2 * view + (pass == Z2 ? 1 : 0)));
+            with_len(d.Z, [&](auto Lc) {
+                constexpr int L = decltype(Lc)::value;
+                const int nty = (int)gen_div_up(d.Y, ddf_z_cols(L));
+                ddf_z_tile<L, true, true>(d.S2, K2, d.Y, d.YZ, nty, dd{1.f, 0.f}, d.tw2z, tile, sm);
+            });
+            return true;
+        }
+        default: {  // y passes
+            if (!d.fy) return false;
+            const long nl = (long)d.Xh * d.Z;
+            const bool inv = pass == YI1 || pass == YI2;
+            with_len(d.Y, [&](auto Lc) {
+                constexpr int L = decltype(Lc)::value;
+                if (inv)
+                    ddf_y_tile<L, +1, true>(d.S2, nl, d.tw2y, tile, sm);
+                else
+                    ddf_y_tile<L, -1, true>(d.S2, nl, d.tw2y, tile, sm);
+            });
+            return true;
+        }
+    }
+}
+
 // precise mode: every pass but the update runs in double-float
 __device__ void run_tile_dd(const VolDesc& d, int pass, int view, long tile, cdd* sm) {
     const size_t ns = (size_t)d.Xh * d.YZ;
+    if (run_tile_ddf(d, pass, view, tile, sm)) return;
     switch (pass) {
         case XF: {
             DdX a = dd_x_args(d.X, d.YZ, d.px, d.tw2x);
@@ -261,15 +318,30 @@ void pass_tiles(const VolDesc& d, int pass, long* ntiles, long* elems) {
         switch (pass) {
             case XF:
             case XR:
+                if (d.fx) {
+                    *ntiles = gen_div_up(d.YZ, 2L * ddf_pairs(d.X));
+                    *elems = 2L * ddf_pairs(d.X) * d.X * 4;
+                    return;
+                }
                 *ntiles = dd_x_tiles(d.X, d.YZ);
                 *elems = 2L * dd_x_pairs(d.X) * d.X * 4;  // double-float work counts about 4x
                 return;
             case Z1:
             case Z2:
+                if (d.fz) {
+                    *ntiles = (long)d.Xh * gen_div_up(d.Y, ddf_z_cols(d.Z));
+                    *elems = (long)ddf_z_cols(d.Z) * d.Z * 4;
+                    return;
+                }
                 *ntiles = dd_z_tiles(d.Z, d.Y, d.Xh);
                 *elems = (long)dd_z_cols(d.Z, d.Y) * d.Z * 4;
                 return;
             default:
+                if (d.fy) {
+                    *ntiles = gen_div_up((long)d.Xh * d.Z, ddf_y_lines(d.Y));
+                    *elems = (long)ddf_y_lines(d.Y) * d.Y * 4;
+                    return;
+                }
                 *ntiles = dd_y_tiles(d.Y, d.Xh, d.Z);
                 *elems = (long)dd_y_lines(d.Y) * d.Y * 4;
                 return;
@@ -330,6 +402,8 @@ struct mvd_batch {
     int grid = 0;
     size_t smem = 0;
     long long poll_limit = 0;
+    int mode = MVD_BATCH_PERSISTENT;
+    unsigned graph_nodes = 0;  // kernels in one run (branches mode)
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -343,6 +417,69 @@ void batch_free(mvd_batch* b) {
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->d_error) cudaFree(b->d_error);
     delete b;
+}
+
+// One graph whose branches are the volumes' whole runs, captured from the
+// single-volume engine with each context's work redirected to a branch stream.
+mvd_status capture_branches(mvd_batch* b, mvd_ctx* const* ctxs) {
+    const int n = b->n;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (double)ctxs[x]->M * ctxs[x]->nv > (double)ctxs[y]->M * ctxs[y]->nv;
+    });
+    std::vector<cudaStream_t> streams(n, nullptr);
+    std::vector<cudaEvent_t> joins(n, nullptr);
+    cudaEvent_t fork = nullptr;
+    mvd_status st = MVD_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&joins[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) st = cuda_status(e, "batch branch streams");
+    bool capturing = false;
+    if (st == MVD_OK) {
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) st = cuda_status(e, "batch capture");
+        capturing = st == MVD_OK;
+    }
+    const unsigned long long before = g_launches.load();
+    if (st == MVD_OK && (e = cudaEventRecord(fork, b->stream)) != cudaSuccess) st = cuda_status(e, "batch fork");
+    for (int k = 0; k < n && st == MVD_OK; ++k) {
+        mvd_ctx* c = ctxs[order[k]];
+        if ((e = cudaStreamWaitEvent(streams[k], fork, 0)) != cudaSuccess) {
+            st = cuda_status(e, "batch branch start");
+            break;
+        }
+        cudaStream_t own = c->stream;
+        c->stream = streams[k];
+        for (int it = 0; it < b->n_iter && st == MVD_OK; ++it)
+            for (int v = 0; v < c->nv && st == MVD_OK; ++v) st = one_update(c, v);
+        c->stream = own;
+        if (st != MVD_OK) break;
+        if ((e = cudaEventRecord(joins[k], streams[k])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(b->stream, joins[k], 0)) != cudaSuccess)
+            st = cuda_status(e, "batch branch join");
+    }
+    b->graph_nodes = (unsigned)(g_launches.load() - before);
+    g_launches.fetch_sub(b->graph_nodes);  // captured, not launched
+    if (capturing) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(b->stream, &graph);
+        if (st == MVD_OK && e != cudaSuccess) st = cuda_status(e, "batch capture end");
+        if (st == MVD_OK) {
+            e = cudaGraphInstantiate(&b->exec, graph, 0);
+            if (e != cudaSuccess) st = cuda_status(e, "batch graph");
+        }
+        if (graph) cudaGraphDestroy(graph);
+    }
+    for (int k = 0; k < n; ++k) {
+        if (joins[k]) cudaEventDestroy(joins[k]);
+        if (streams[k]) cudaStreamDestroy(streams[k]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    return st;
 }
 
 mvd_status enqueue(mvd_batch* b) {
@@ -360,8 +497,12 @@ mvd_status enqueue(mvd_batch* b) {
 extern "C" {
 
 mvd_status mvd_batch_create(mvd_ctx* const* ctxs, int n, int n_iter, mvd_batch** out) {
+    return mvd_batch_create_mode(ctxs, n, n_iter, MVD_BATCH_AUTO, out);
+}
+
+mvd_status mvd_batch_create_mode(mvd_ctx* const* ctxs, int n, int n_iter, int mode, mvd_batch** out) {
     clear_error();
-    if (!out || !ctxs || n < 1 || n_iter < 0) {
+    if (!out || !ctxs || n < 1 || n_iter < 0 || mode < MVD_BATCH_AUTO || mode > MVD_BATCH_BRANCHES) {
         set_error("mvd_batch_create: bad arguments");
         return MVD_ERR_ARG;
     }
@@ -372,14 +513,31 @@ mvd_status mvd_batch_create(mvd_ctx* const* ctxs, int n, int n_iter, mvd_batch**
             set_error("mvd_batch_create: context %d is NULL", i);
             return MVD_ERR_ARG;
         }
-        if (c->state < 2 || c->path != MVD_PATH_FFT) {
-            set_error("mvd_batch_create: context %d must be precomputed with the FFT engine", i);
-            return c->state < 2 ? MVD_ERR_STATE : MVD_ERR_UNSUPPORTED;
+        if (c->state < 2) {
+            set_error("mvd_batch_create: context %d is not precomputed", i);
+            return MVD_ERR_STATE;
         }
         if (c->device != ctxs[0]->device || c->stream != ctxs[0]->stream) {
             set_error("mvd_batch_create: all contexts must share one device and one stream");
             return MVD_ERR_ARG;
         }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) {
+                set_error("mvd_batch_create: context %d appears twice", i);
+                return MVD_ERR_ARG;
+            }
+    }
+    bool all_fft = true;
+    for (int i = 0; i < n; ++i) all_fft = all_fft && ctxs[i]->path == MVD_PATH_FFT;
+    const bool branches_ok = ctxs[0]->stream != nullptr && !profiling_on();
+    if (mode == MVD_BATCH_AUTO) mode = branches_ok ? MVD_BATCH_BRANCHES : MVD_BATCH_PERSISTENT;
+    if (mode == MVD_BATCH_PERSISTENT && !all_fft) {
+        set_error("mvd_batch_create: the persistent kernel needs every context on the FFT engine");
+        return MVD_ERR_UNSUPPORTED;
+    }
+    if (mode == MVD_BATCH_BRANCHES && !branches_ok) {
+        set_error("mvd_batch_create: graph branches need a non-NULL stream and per-kernel timing off");
+        return MVD_ERR_UNSUPPORTED;
     }
     int prev = -1;
     cudaGetDevice(&prev);
@@ -389,14 +547,21 @@ mvd_status mvd_batch_create(mvd_ctx* const* ctxs, int n, int n_iter, mvd_batch**
     b->stream = ctxs[0]->stream;
     b->n = n;
     b->n_iter = n_iter;
+    b->mode = mode;
     auto fail = [&](mvd_status st) {
         batch_free(b);
         if (prev >= 0 && prev != ctxs[0]->device) cudaSetDevice(prev);
         return st;
     };
+    if (mode == MVD_BATCH_BRANCHES) {
+        const mvd_status st = capture_branches(b, ctxs);
+        if (st != MVD_OK) return fail(st);
+        if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+        *out = b;
+        return MVD_OK;
+    }
 
     std::vector<VolDesc> vols(n);
-    int max_nv = 0;
     size_t smem = 0;
     for (int i = 0; i < n; ++i) {
         const mvd_ctx* c = ctxs[i];
@@ -426,28 +591,58 @@ mvd_status mvd_batch_create(mvd_ctx* const* ctxs, int n, int n_iter, mvd_batch**
         d.tw2x = g.tw2x;
         d.tw2y = g.tw2y;
         d.tw2z = g.tw2z;
-        max_nv = std::max(max_nv, c->nv);
         smem = std::max({smem, d.fx ? fast_x_smem(g.X) : gen_x_smem(g.X), d.fy ? fast_y_smem(g.Y) : gen_y_smem(g.Y),
                          d.fz ? fast_z_smem(g.Z) : gen_z_smem(g.Z, g.Y)});
-        if (d.precise) smem = std::max({smem, dd_x_smem(g.X), dd_y_smem(g.Y), dd_z_smem(g.Z, g.Y)});
+        if (d.precise)
+            smem = std::max({smem, d.fx ? ddf_x_smem(g.X) : dd_x_smem(g.X), d.fy ? ddf_y_smem(g.Y) : dd_y_smem(g.Y),
+                             d.fz ? ddf_z_smem(g.Z) : dd_z_smem(g.Z, g.Y)});
     }
-    // phase-ordered entries (default schedule: views 0..nv-1 per iteration)
-    std::vector<Entry> entries;
-    std::vector<unsigned long long> done(n, 0);
-    long task = 0;
-    for (int it = 0; it < n_iter; ++it)
-        for (int s = 0; s < max_nv; ++s)
-            for (int p = 0; p < NPASS; ++p)
-                for (int i = 0; i < n; ++i) {
-                    if (vols[i].nv <= s) continue;
+    // Entries (default schedule: views 0..nv-1 per iteration). Each volume's
+    // own entries stay in order; across volumes they are merged by the
+    // fraction of the volume's work done at the entry's midpoint, so that
+    // every stretch of the queue holds passes of all volumes (volumes with
+    // few views or small passes do not queue behind the others' last views).
+    struct Pending {
+        double key;
+        int vol;
+        Entry e;
+    };
+    std::vector<Pending> pend;
+    for (int i = 0; i < n; ++i) {
+        std::vector<Entry> own;
+        std::vector<double> work;
+        unsigned long long done_i = 0;
+        double total_i = 0.0;
+        for (int it = 0; it < n_iter; ++it)
+            for (int s = 0; s < vols[i].nv; ++s)
+                for (int p = 0; p < NPASS; ++p) {
                     long nt = 0, el = 0;
                     pass_tiles(vols[i], p, &nt, &el);
                     // a task covers several small tiles (about 16K elements of work)
                     const int tpt = (int)std::min(8L, std::max(1L, 16384 / std::max(1L, el)));
-                    entries.push_back({task, done[i], i, p, s, (int)nt, tpt});
-                    task += gen_div_up(nt, tpt);
-                    done[i] += (unsigned long long)nt;
+                    own.push_back({0, done_i, i, p, s, (int)nt, tpt});
+                    work.push_back((double)nt * (double)el);
+                    total_i += (double)nt * (double)el;
+                    done_i += (unsigned long long)nt;
                 }
+        double cum = 0.0;
+        for (size_t k = 0; k < own.size(); ++k) {
+            pend.push_back({(cum + 0.5 * work[k]) / std::max(total_i, 1.0), i, own[k]});
+            cum += work[k];
+        }
+    }
+    std::stable_sort(pend.begin(), pend.end(), [](const Pending& a, const Pending& b) {
+        return a.key < b.key || (a.key == b.key && a.vol < b.vol);
+    });
+    std::vector<Entry> entries;
+    entries.reserve(pend.size());
+    long task = 0;
+    for (const Pending& q : pend) {
+        Entry e = q.e;
+        e.begin = task;
+        task += gen_div_up((long)e.ntiles, (long)e.tpt);
+        entries.push_back(e);
+    }
     b->n_entries = (int)entries.size();
     b->total = task;
     b->smem = smem;
@@ -518,7 +713,7 @@ mvd_status mvd_batch_run(mvd_batch* b) {
         if (e != cudaSuccess)
             st = cuda_status(e, "mvd_batch_run: graph launch");
         else
-            count_launch();
+            count_launch(b->mode == MVD_BATCH_BRANCHES ? b->graph_nodes : 1);
     } else {
         st = enqueue(b);
     }
@@ -533,7 +728,7 @@ mvd_status mvd_batch_wait(mvd_batch* b) {
         return MVD_ERR_ARG;
     }
     int flag = 0;
-    MVD_CUDA(cudaMemcpyAsync(&flag, b->d_error, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    if (b->d_error) MVD_CUDA(cudaMemcpyAsync(&flag, b->d_error, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     MVD_CUDA(cudaStreamSynchronize(b->stream));
     if (flag) {
         set_error("mvd_batch_wait: a block gave up waiting for a dependency (poll limit %lld)", b->poll_limit);
@@ -542,7 +737,12 @@ mvd_status mvd_batch_wait(mvd_batch* b) {
     return MVD_OK;
 }
 
-long long mvd_batch_tasks(const mvd_batch* b) { return b ? b->total : 0; }
+long long mvd_batch_tasks(const mvd_batch* b) {
+    if (!b) return 0;
+    return b->mode == MVD_BATCH_BRANCHES ? (long long)b->graph_nodes : b->total;
+}
+
+int mvd_batch_mode(const mvd_batch* b) { return b ? b->mode : -1; }
 
 void mvd_batch_destroy(mvd_batch* b) {
     if (!b) return;

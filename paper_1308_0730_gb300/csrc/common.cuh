@@ -42,6 +42,7 @@ enum KernelClass {
 };
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
+bool profiling_on();
 
 // Converts the last CUDA error (after a launch) into a status.
 mvd_status check_launch(const char* what);

@@ -70,6 +70,8 @@ cudaEvent_t next_event() {
 }
 }  // namespace
 
+bool profiling_on() { return g_prof_on.load(std::memory_order_relaxed) != 0; }
+
 void prof_begin(int cls, cudaStream_t st) {
     if (!g_prof_on.load(std::memory_order_relaxed)) return;
     cudaEvent_t e = next_event();

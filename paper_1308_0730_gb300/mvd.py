@@ -30,7 +30,8 @@ EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_s
            "mvd_get_eps", "mvd_get_psi0", "mvd_get_path", "mvd_get_compound_kernel", "mvd_launch_count",
            "mvd_profile_enable", "mvd_profile_read", "mvd_update_direct_noalloc", "mvd_batch_create",
            "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy", "mvd_unrolled_forward",
-           "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp", "mvd_autotune"]
+           "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp", "mvd_autotune",
+           "mvd_batch_create_mode", "mvd_batch_mode"]
 
 
 class MvdError(RuntimeError):
@@ -98,6 +99,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_update_direct_noalloc.restype = ci
     lib.mvd_batch_create.argtypes = [ctypes.POINTER(vp), ci, ci, ctypes.POINTER(vp)]
     lib.mvd_batch_create.restype = ci
+    lib.mvd_batch_create_mode.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ctypes.POINTER(vp)]
+    lib.mvd_batch_create_mode.restype = ci
+    lib.mvd_batch_mode.argtypes = [vp]
+    lib.mvd_batch_mode.restype = ci
     lib.mvd_batch_run.argtypes = [vp]
     lib.mvd_batch_run.restype = ci
     lib.mvd_batch_wait.argtypes = [vp]
@@ -275,12 +280,20 @@ def mvd_update_direct_noalloc(psi, phi, psf, comp, eps: float, stream=None):
     _check(load().mvd_update_direct_noalloc(ptr(psi), ptr(phi), ptr(psf), ptr(comp), dims, kd, float(eps), st))
 
 
-def mvd_batch_create(ctxs, n_iter: int):
-    """Batch over context handles (all FFT-engine, one device, one stream)."""
+BATCH_MODES = {"auto": 0, "persistent": 1, "branches": 2}
+
+
+def mvd_batch_create(ctxs, n_iter: int, mode="auto"):
+    """Batch over contexts (one device, one stream); mode "auto", "persistent" or "branches"."""
     arr = (ctypes.c_void_p * len(ctxs))(*[c if isinstance(c, ctypes.c_void_p) else c.ctx for c in ctxs])
     h = ctypes.c_void_p()
-    _check(load().mvd_batch_create(arr, len(ctxs), int(n_iter), ctypes.byref(h)))
+    m = BATCH_MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(load().mvd_batch_create_mode(arr, len(ctxs), int(n_iter), m, ctypes.byref(h)))
     return h
+
+
+def mvd_batch_mode(batch) -> str:
+    return {1: "persistent", 2: "branches"}.get(int(load().mvd_batch_mode(batch)), "none")
 
 
 def mvd_batch_run(batch):

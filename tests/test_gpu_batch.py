@@ -1,5 +1,6 @@
-"""Batched form: many volumes of uneven size and view count in one persistent
-launch, against per-volume runs and the FP64 oracle."""
+"""Batched form: many volumes of uneven size and view count in one launch (the
+persistent kernel and the graph of per-volume branches), against per-volume
+runs and the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -39,19 +40,26 @@ def _workloads(seed=500, n_iter=3):
             for i, (d, b) in enumerate(SPECS)]
 
 
-def test_batch_matches_per_volume_runs_and_oracle(env):
+MODES = ["persistent", "branches"]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_matches_per_volume_runs_and_oracle(env, mode):
     torch, mvd = env
     ws = _workloads()
     s = torch.cuda.Stream()
+    # the branch graph also takes direct-engine contexts
+    paths = ["fft"] * len(ws) if mode == "persistent" else ["fft", "direct", "fft", "direct", "fft"]
     plain = []
-    for w in ws:
-        with mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", stream=s) as d:
+    for w, path in zip(ws, paths):
+        with mvd.Deconvolver(w.views, w.psfs, "efficient", path=path, stream=s) as d:
             d.iterate(w.n_iter)
             plain.append(d.result())
-    ds = [mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", stream=s) for w in ws]
+    ds = [mvd.Deconvolver(w.views, w.psfs, "efficient", path=path, stream=s) for w, path in zip(ws, paths)]
     try:
-        b = mvd.mvd_batch_create(ds, ws[0].n_iter)
+        b = mvd.mvd_batch_create(ds, ws[0].n_iter, mode)
         try:
+            assert mvd.mvd_batch_mode(b) == mode
             assert mvd.mvd_batch_tasks(b) > 0
             mvd.mvd_batch_run(b)
             mvd.mvd_batch_wait(b)
@@ -66,6 +74,8 @@ def test_batch_matches_per_volume_runs_and_oracle(env):
         for d in ds:
             d.close()
     for w, g, p in zip(ws, got, plain):
+        if mode == "branches":  # the same kernels as the per-volume run
+            assert np.array_equal(g, p), w.name
         assert rel_err(g, p) < PARITY_TOL, f"{w.name}: {err_report(g, p)}"
     for i in (0, 3, 4):
         w = ws[i]
@@ -86,8 +96,13 @@ def test_batch_rejects_bad_contexts(env):
             mvd.mvd_batch_create([a, b], 1)
         assert ei.value.status == mvd.MVD_ERR_ARG
         with pytest.raises(mvd.MvdError) as ei:
-            mvd.mvd_batch_create([a, c], 1)
+            mvd.mvd_batch_create([a, c], 1, "persistent")
         assert ei.value.status == mvd.MVD_ERR_UNSUPPORTED
+        with pytest.raises(mvd.MvdError) as ei:
+            mvd.mvd_batch_create([a, a], 1)
+        assert ei.value.status == mvd.MVD_ERR_ARG
+        bc = mvd.mvd_batch_create([a, c], 1, "branches")
+        mvd.mvd_batch_destroy(bc)
 
 
 def test_batch_wait_times_out_and_context_stays_usable(env, monkeypatch):
@@ -100,7 +115,7 @@ def test_batch_wait_times_out_and_context_stays_usable(env, monkeypatch):
     monkeypatch.setenv("MVD_BATCH_POLL_LIMIT", "20000")
     ds = [mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", stream=s) for w in ws]
     try:
-        b = mvd.mvd_batch_create(ds, 1)
+        b = mvd.mvd_batch_create(ds, 1, "persistent")
         try:
             mvd.mvd_batch_run(b)
             with pytest.raises(mvd.MvdError) as ei:
@@ -119,12 +134,19 @@ def test_batch_wait_times_out_and_context_stays_usable(env, monkeypatch):
             d.close()
 
 
-def test_batched_volumes_of_the_48_volume_workload_match_oracle(env):
+@pytest.fixture(scope="module")
+def cfg4_subset():
+    ws = synth.config4(only=[0, 36, 19])
+    return ws, [oracle.deconvolve(w.views, w.psfs, w.n_iter, "efficient")[0] for w in ws]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batched_volumes_of_the_48_volume_workload_match_oracle(env, cfg4_subset, mode):
     """Three of the 48 batched volumes (all-generic 48x60x60 with 5 views; 100x128x54 with 5
     views and 128x72x81 with 2 views, which have power-of-two axes), 15 iterations, against the
     FP64 oracle at 1e-4: per volume and inside one batch."""
     torch, mvd = env
-    ws = synth.config4(only=[0, 36, 19])
+    ws, wants = cfg4_subset
     s = torch.cuda.Stream()
     ds = [mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", stream=s) for w in ws]
     try:
@@ -133,7 +155,7 @@ def test_batched_volumes_of_the_48_volume_workload_match_oracle(env):
             d.iterate(w.n_iter)
             plain.append(d.result())
             d.set_estimate(None)
-        b = mvd.mvd_batch_create(ds, ws[0].n_iter)
+        b = mvd.mvd_batch_create(ds, ws[0].n_iter, mode)
         try:
             mvd.mvd_batch_run(b)
             mvd.mvd_batch_wait(b)
@@ -143,7 +165,6 @@ def test_batched_volumes_of_the_48_volume_workload_match_oracle(env):
     finally:
         for d in ds:
             d.close()
-    for w, p, q in zip(ws, plain, batched):
-        want, _ = oracle.deconvolve(w.views, w.psfs, w.n_iter, "efficient")
+    for w, p, q, want in zip(ws, plain, batched, wants):
         assert rel_err(p, want) < PARITY_TOL, f"{w.name} per volume: {err_report(p, want)}"
         assert rel_err(q, want) < PARITY_TOL, f"{w.name} batched: {err_report(q, want)}"
