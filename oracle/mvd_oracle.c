@@ -15,7 +15,10 @@
  *     optimization I (Eq. 230) and optimization II (Eq. 240);
  *   - sequential, view-by-view (OSEM-style) application of each view's
  *     update (Suppl. Note "Alternative iteration for faster convergence");
- *   - flat initial estimate equal to the mean observed intensity (Eq. 15 text).
+ *   - flat initial estimate equal to the mean observed intensity (Eq. 15 text);
+ *   - reverse-mode gradient of K unrolled iterations (the paper does not
+ *     differentiate its update; the chain rule through Eq. 15, Eq. 222 and the
+ *     PSF normalisation of Eq. 3, pinned by FP64 central differences).
  *
  * Readings where the paper is silent (same on the CUDA side):
  *   - image convolutions are periodic (circular) on the given grid, i.e. what
