@@ -62,14 +62,15 @@ def _kernel_bytes(X, Y, Z, precise=True):
 
 
 # FP32-ALU work model of the double-float kernels (ALU-bound): one op = one FP32
-# add, multiply or FMA instruction. A double-float add costs 11 ops (TwoSum, two
-# adds, FastTwoSum), a double-float multiply 7 (product, three FMAs, FastTwoSum);
-# a complex FFT of length N is counted as the radix-2 algorithm's 3 N log2 N real
-# adds and 2 N log2 N real multiplies, i.e. 47 N log2 N ops in double-float and
-# 5 N log2 N in FP32; a complex double-float multiply is 4 mul + 2 add = 50 ops.
-DD_FFT_OPS = 47.0
+# add, multiply or FMA instruction. A double-float add costs 8 ops (TwoSum and two
+# adds), a double-float multiply 7 (product, three FMAs, FastTwoSum), a complex
+# double-float multiply 38 (two fused dot products of 19); a complex FFT of
+# length N is counted as the radix-2 algorithm's 3 N log2 N real adds and
+# 2 N log2 N real multiplies, i.e. 38 N log2 N ops in double-float and 5 N log2 N
+# in FP32.
+DD_FFT_OPS = 38.0
 FP32_FFT_OPS = 5.0
-DD_CMUL_OPS = 50.0
+DD_CMUL_OPS = 38.0
 
 
 def _kernel_alu_ops(X, Y, Z):

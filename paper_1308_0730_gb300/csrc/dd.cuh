@@ -27,9 +27,16 @@ __device__ __forceinline__ dd dd_fast_two_sum(float a, float b) {  // needs |a| 
     const float s = a + b;
     return {s, b - (s - a)};
 }
+// Sum without the final renormalisation: hi is the rounded sum of the high
+// parts, lo collects that rounding error and both low parts (8 FP32 ops instead
+// of 11). hi + lo carries the same error as the renormalised sum; |lo| may grow
+// to a few ulp(hi) over chained additions, which the multiplications below
+// (all ending in FastTwoSum) bring back. Where heavy cancellation leaves lo
+// larger than hi, the values involved are themselves of the order of the
+// operands' last bits, so the absolute error stays at that level.
 __device__ __forceinline__ dd dd_add(dd x, dd y) {
     const dd s = dd_two_sum(x.hi, y.hi);
-    return dd_fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+    return {s.hi, s.lo + (x.lo + y.lo)};
 }
 __device__ __forceinline__ dd dd_sub(dd x, dd y) { return dd_add(x, dd{-y.hi, -y.lo}); }
 __device__ __forceinline__ dd dd_mul(dd x, dd y) {
@@ -48,8 +55,22 @@ struct __align__(16) cdd {
 
 __device__ __forceinline__ cdd cadd(cdd a, cdd b) { return {dd_add(a.re, b.re), dd_add(a.im, b.im)}; }
 __device__ __forceinline__ cdd csub(cdd a, cdd b) { return {dd_sub(a.re, b.re), dd_sub(a.im, b.im)}; }
+// x.y + sg * z.w with one TwoSum: both high products and their exact errors
+// (TwoProd by FMA) plus the cross terms, renormalised once (19 ops).
+template <int SG>
+__device__ __forceinline__ dd dd_dot2(dd x, dd y, dd z, dd w) {
+    const float p = x.hi * y.hi, q = z.hi * w.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    float f = fmaf(z.hi, w.hi, -q);
+    f = fmaf(z.hi, w.lo, f);
+    f = fmaf(z.lo, w.hi, f);
+    const dd t = dd_two_sum(p, SG > 0 ? q : -q);
+    return dd_fast_two_sum(t.hi, t.lo + (SG > 0 ? e + f : e - f));
+}
 __device__ __forceinline__ cdd cmul(cdd a, cdd b) {
-    return {dd_sub(dd_mul(a.re, b.re), dd_mul(a.im, b.im)), dd_add(dd_mul(a.re, b.im), dd_mul(a.im, b.re))};
+    return {dd_dot2<-1>(a.re, b.re, a.im, b.im), dd_dot2<+1>(a.re, b.im, a.im, b.re)};
 }
 __device__ __forceinline__ cdd cconj(cdd a) { return {a.re, dd{-a.im.hi, -a.im.lo}}; }
 __device__ __forceinline__ cdd chalf(cdd a) {  // exact
@@ -121,10 +142,16 @@ struct DftDD<8, S> {
         cdd o[4] = {v[1], v[3], v[5], v[7]};
         DftDD<4, S>::run(e);
         DftDD<4, S>::run(o);
-        const double h = 0.70710678118654752440;  // sqrt(2)/2
-        const cdd w1{MVD_DD(h), MVD_DD(S * h)};
-        const cdd w3{MVD_DD(-h), MVD_DD(S * h)};
-        const cdd o1 = cmul(o[1], w1), o2 = mul_si<S>(o[2]), o3 = cmul(o[3], w3);
+        // o1 (1 + S i) h = h (re - S im, im + S re);
+        // o3 (-1 + S i) h = h (-(re + S im), S re - im): one add and one product by h per part
+        const dd hd = MVD_DD(0.70710678118654752440);  // sqrt(2)/2
+        auto sg = [](dd x) { return S > 0 ? x : dd{-x.hi, -x.lo}; };
+        const dd a1 = dd_sub(o[1].re, sg(o[1].im)), b1 = dd_add(o[1].im, sg(o[1].re));
+        const dd a3 = dd_add(o[3].re, sg(o[3].im)), b3 = dd_sub(sg(o[3].re), o[3].im);
+        const dd m3 = dd_mul(hd, a3);
+        const cdd o1{dd_mul(hd, a1), dd_mul(hd, b1)};
+        const cdd o3{dd{-m3.hi, -m3.lo}, dd_mul(hd, b3)};
+        const cdd o2 = mul_si<S>(o[2]);
         v[0] = cadd(e[0], o[0]);
         v[4] = csub(e[0], o[0]);
         v[1] = cadd(e[1], o1);

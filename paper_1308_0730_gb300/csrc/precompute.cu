@@ -33,21 +33,49 @@ __device__ __forceinline__ void offset_of(const Box& b, int i, int& dx, int& dy,
     dz = r / b.ky - b.hz();
 }
 
-// Q(d) = sum_e P(e) P(e - d)   (P * P^*), on the box of size 2K-1
+// Sum over the box [xlo,xhi] x [ylo,yhi] x [zlo,zhi] of the terms that
+// f(ex, ey, ez, acc) adds to acc (one FMA each), by one
+// warp: lanes stride over the flattened (ey, ex) plane (stepped incrementally,
+// no division in the loop), z runs serially; the lanes' partial sums are
+// combined with shuffles. Every lane returns the total.
+template <typename F>
+__device__ __forceinline__ float warp_box_sum(int xlo, int xhi, int ylo, int yhi, int zlo, int zhi, F&& f) {
+    const int lane = threadIdx.x & 31;
+    const int nx = xhi - xlo + 1, ny = yhi - ylo + 1;
+    float s = 0.f;
+    if (nx > 0 && ny > 0) {
+        const int n2 = nx * ny;
+        for (int ez = zlo; ez <= zhi; ++ez) {
+            int ey = ylo + lane / nx, ex = xlo + lane % nx;
+            for (int i = lane; i < n2; i += 32) {
+                s = f(ex, ey, ez, s);
+                ex += 32;
+                while (ex > xhi) {
+                    ex -= nx;
+                    ++ey;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Q(d) = sum_e P(e) P(e - d)   (P * P^*), on the box of size 2K-1; one warp per d
 __global__ void k_autocorr(const float* P, Box b, float* Q, Box q) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
     if (i >= q.size()) return;
     int dx, dy, dz;
     offset_of(q, i, dx, dy, dz);
-    float s = 0.f;
     // e and e - d both inside b
     const int zlo = max(-b.hz(), dz - b.hz()), zhi = min(b.hz(), dz + b.hz());
     const int ylo = max(-b.hy(), dy - b.hy()), yhi = min(b.hy(), dy + b.hy());
     const int xlo = max(-b.hx(), dx - b.hx()), xhi = min(b.hx(), dx + b.hx());
-    for (int ez = zlo; ez <= zhi; ++ez)
-        for (int ey = ylo; ey <= yhi; ++ey)
-            for (int ex = xlo; ex <= xhi; ++ex) s = fmaf(b.at(P, ex, ey, ez), b.at(P, ex - dx, ey - dy, ez - dz), s);
-    Q[i] = s;
+    const float s = warp_box_sum(xlo, xhi, ylo, yhi, zlo, zhi, [&](int ex, int ey, int ez, float acc) {
+        return fmaf(b.at(P, ex, ey, ez), b.at(P, ex - dx, ey - dy, ez - dz), acc);
+    });
+    if ((threadIdx.x & 31) == 0) Q[i] = s;
 }
 
 // out(d) = P^*(d) = P(-d)
@@ -59,20 +87,19 @@ __global__ void k_mirror(const float* P, Box b, float* out) {
     out[i] = b.at(P, -dx, -dy, -dz);
 }
 
-// out(d) *= sum_e P^*(e) G(d - e)  for d on P's box  (P^*(e) = P(-e))
+// out(d) *= sum_e P^*(e) G(d - e)  for d on P's box  (P^*(e) = P(-e)); one warp per d
 __global__ void k_mul_conv(const float* P, Box b, const float* G, Box g, float* out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5);
     if (i >= b.size()) return;
     int dx, dy, dz;
     offset_of(b, i, dx, dy, dz);
     const int zlo = max(-b.hz(), dz - g.hz()), zhi = min(b.hz(), dz + g.hz());
     const int ylo = max(-b.hy(), dy - g.hy()), yhi = min(b.hy(), dy + g.hy());
     const int xlo = max(-b.hx(), dx - g.hx()), xhi = min(b.hx(), dx + g.hx());
-    float s = 0.f;
-    for (int ez = zlo; ez <= zhi; ++ez)
-        for (int ey = ylo; ey <= yhi; ++ey)
-            for (int ex = xlo; ex <= xhi; ++ex) s = fmaf(b.at(P, -ex, -ey, -ez), g.at(G, dx - ex, dy - ey, dz - ez), s);
-    out[i] *= s;
+    const float s = warp_box_sum(xlo, xhi, ylo, yhi, zlo, zhi, [&](int ex, int ey, int ez, float acc) {
+        return fmaf(b.at(P, -ex, -ey, -ez), g.at(G, dx - ex, dy - ey, dz - ez), acc);
+    });
+    if ((threadIdx.x & 31) == 0) out[i] *= s;
 }
 
 // out(d) *= P^*(d)
@@ -148,6 +175,7 @@ __global__ void k_fill(float* p, long n, float v) {
 
 inline Box box_of(const int* kd) { return Box{kd[0], kd[1], kd[2]}; }
 inline int blocks_for(long n) { return (int)((n + kThreads - 1) / kThreads); }
+inline int warp_blocks_for(long n) { return (int)((n * 32 + kThreads - 1) / kThreads); }  // one warp per output
 inline int grid_stride_blocks(long n) {
     long b = (n + kThreads - 1) / kThreads;
     return (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
@@ -170,12 +198,12 @@ mvd_status build_compound(int n_views, const float* d_psf, const long* koff, con
             const float* Pw = d_psf + koff[w];
             if (variant == MVD_EFFICIENT) {
                 const Box bq{2 * bw.kx - 1, 2 * bw.ky - 1, 2 * bw.kz - 1};
-                k_autocorr<<<blocks_for((long)bq.kx * bq.ky * bq.kz), kThreads, 0, st>>>(Pw, bw, d_tmp, bq);
+                k_autocorr<<<warp_blocks_for((long)bq.kx * bq.ky * bq.kz), kThreads, 0, st>>>(Pw, bw, d_tmp, bq);
                 count_launch();
                 MVD_TRY(check_launch("compound autocorrelation"));
-                k_mul_conv<<<blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, d_tmp, bq, d_out);
+                k_mul_conv<<<warp_blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, d_tmp, bq, d_out);
             } else if (variant == MVD_OPT1) {
-                k_mul_conv<<<blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, Pw, bw, d_out);
+                k_mul_conv<<<warp_blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, Pw, bw, d_out);
             } else {
                 k_mul_mirror<<<blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, d_out);
             }
@@ -196,7 +224,7 @@ mvd_status mirror_kernel(const float* k, const int kd[3], float* out, cudaStream
 mvd_status autocorr_kernel(const float* P, const int kd[3], float* Q, cudaStream_t st) {
     const Box b = box_of(kd);
     const Box q{2 * b.kx - 1, 2 * b.ky - 1, 2 * b.kz - 1};
-    k_autocorr<<<blocks_for((long)q.kx * q.ky * q.kz), kThreads, 0, st>>>(P, b, Q, q);
+    k_autocorr<<<warp_blocks_for((long)q.kx * q.ky * q.kz), kThreads, 0, st>>>(P, b, Q, q);
     count_launch();
     return check_launch("autocorrelation");
 }

@@ -98,11 +98,11 @@ def write(w):
         fh.write(f"# written by tests/golden/make_oracle_grad.py; reverse mode {t_adj:.0f} s, finite differences "
                  f"{t_fd:.0f} s on {oracle.num_threads()} threads\n")
         fh.write(f"inputs_sha256 {input_digest(w, psfs)}\n")
-        fh.write(f"loss {loss!r}\n")
+        fh.write(f"loss {float(loss)!r}\n")
         for v in range(w.n_views):
-            fh.write(f"sigma {v} {sig[v][0]!r} {sig[v][1]!r}\n")
-            fh.write(f"dsigma_adjoint {v} {chain[v, 0]!r} {chain[v, 1]!r}\n")
-            fh.write(f"dsigma_fd {v} {fd[v, 0]!r} {fd[v, 1]!r}\n")
+            fh.write(f"sigma {v} {float(sig[v][0])!r} {float(sig[v][1])!r}\n")
+            fh.write(f"dsigma_adjoint {v} {float(chain[v, 0])!r} {float(chain[v, 1])!r}\n")
+            fh.write(f"dsigma_fd {v} {float(fd[v, 0])!r} {float(fd[v, 1])!r}\n")
             fh.write(f"max_abs_dview {v} {float(np.abs(gv[v]).max())!r}\n")
             fh.write(f"max_abs_dpsf {v} {float(np.abs(gp[v]).max())!r}\n")
             for i in samples(gv[v].size, N_VOX, 100 + v):
