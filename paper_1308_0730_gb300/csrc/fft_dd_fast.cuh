@@ -90,6 +90,65 @@ struct LineFFTDD {
     }
 };
 
+// The same register-resident plan in FP32 (float2 elements, FP32 twiddle
+// table): used for the back-projection's forward x transform of r - 1, whose
+// input the double-float inverse leaves in exactly this distribution. A line
+// uses L/8 + L/64 + 1 float2 of shared memory at stride line_stride8(L).
+template <int L, int S, bool WARP_LOCAL>
+struct LineFFT8F {
+    static constexpr int TPL = L / kE8;
+    static constexpr int NST = plan8_nst(L);
+
+    __device__ __forceinline__ static void sync() {
+        if (WARP_LOCAL && TPL <= 32)
+            __syncwarp();
+        else
+            __syncthreads();
+    }
+
+    template <int ST, int NS>
+    __device__ __forceinline__ static void stage(float2 (&v)[kE8], float2* sm, int t, const float2* __restrict__ tw) {
+        if constexpr (ST < NST) {
+            constexpr int R = plan8_radix(L, ST);
+            constexpr int B = kE8 / R;
+            constexpr bool LAST = (ST == NST - 1);
+#pragma unroll
+            for (int m = 0; m < B; ++m) {
+                float2 x[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[r] = v[m + r * B];
+                const int j = t + TPL * m;
+                const int k = j % NS;
+                if (NS > 1) {
+                    const int step = k * (L / (NS * R));
+#pragma unroll
+                    for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<S>(tw, r * step));
+                }
+                Dft<R, S>::run(x);
+                if (LAST) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[m + r * B] = x[r];
+                } else {
+                    const int d = (j / NS) * NS * R + k;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) sm[pad8(d + r * NS)] = x[r];
+                }
+            }
+            if constexpr (!LAST) {
+                sync();
+#pragma unroll
+                for (int q = 0; q < kE8; ++q) v[q] = sm[pad8(t + TPL * q)];
+                sync();
+                stage<ST + 1, NS * R>(v, sm, t, tw);
+            }
+        }
+    }
+
+    __device__ __forceinline__ static void run(float2 (&v)[kE8], float2* sm, int t, const float2* __restrict__ tw) {
+        stage<0, 1>(v, sm, t, tw);
+    }
+};
+
 // tile geometry
 __host__ __device__ constexpr int ddf_pairs(int L) { return kDdThreads / (L / kE8); }  // x pass: pairs per tile
 __host__ __device__ constexpr int ddf_y_lines(int L) { return kDdThreads / (L / kE8); }
@@ -251,26 +310,32 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
     }
     __syncthreads();
     LineFFTDD<L, +1, true>::run(v, sm + p * LS, t, a.tw2);
-    // r - 1 into FP32 lines (the B half of shared memory), then FP32 forward x
-    __syncthreads();
-    float2* F0 = reinterpret_cast<float2*>(sm + P * LS);
-    float2* F1 = F0 + P * (L + 1);
+    // r - 1 of both rows as one complex FP32 line, forward x in registers (the
+    // double-float inverse leaves the line in the same distribution; its last
+    // shared-memory read was followed by a barrier, so the line's shared
+    // memory is free)
+    float2 f[kE8];
 #pragma unroll
     for (int q = 0; q < kE8; ++q) {
-        const int n = t + TPL * q;
         const float ba = v[q].re.hi + v[q].re.lo, bb = v[q].im.hi + v[q].im.lo;
         const float xa = oka ? w[q].x / fmaxf(ba, a.eps) - 1.f : 0.f;
         const float xb = okb ? w[q].y / fmaxf(bb, a.eps) - 1.f : 0.f;
-        F0[p * (L + 1) + n] = make_float2(xa, xb);
+        f[q] = make_float2(xa, xb);
     }
+    // each FP32 line lives inside its own line's double-float region (the
+    // threads of a line are the only ones touching it until the barrier)
+    float2* Fp = reinterpret_cast<float2*>(sm + p * LS);
+    LineFFT8F<L, -1, true>::run(f, Fp, t, a.plan.tw);
+#pragma unroll
+    for (int q = 0; q < kE8; ++q) Fp[pad8(t + TPL * q)] = f[q];
     __syncthreads();
-    const float2* F = fft_lines<-1>(F0, F1, P, L + 1, a.plan);
     for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
         const int k = idx / (2 * P), row = idx - k * 2 * P;
         if (row >= nrows) continue;
         const int pp = row < P ? row : row - P;
-        const float2 zk = F[pp * (L + 1) + k];
-        const float2 zm = cconj(F[pp * (L + 1) + (k == 0 ? 0 : L - k)]);
+        const float2* F = reinterpret_cast<const float2*>(sm + pp * LS);
+        const float2 zk = F[pad8(k)];
+        const float2 zm = cconj(F[pad8(k == 0 ? 0 : L - k)]);
         float2 val;
         if (row < P) {
             val = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
