@@ -16,6 +16,7 @@ Seeds: the workload of the k-th configuration uses ``default_rng(1000 + k)``.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -173,32 +174,63 @@ def blobs_truth(rng, dims, n, sigma_range, peak_range, background) -> np.ndarray
     return coarse + background
 
 
-def ellipsoids_truth(rng, dims, n, radii_range, intensity_range) -> np.ndarray:
-    """Solid ellipsoids (random radii, orientation, intensity), additive, periodic."""
-    X, Y, Z = dims
-    h = int(math.ceil(radii_range[1])) + 1
+def _ellipsoid_counts(args):
+    """Fine samples inside each ellipsoid, summed over the 2x2x2 fine cells of
+    every coarse voxel of its (2h+1)^3 block (0..8, uint8)."""
+    h, frac, radii, rots = args
     nb = 2 * h + 1
     f = _fine_offsets(h)
     FZ, FY, FX = np.meshgrid(f, f, f, indexing="ij")
     P = np.stack([FX.ravel(), FY.ravel(), FZ.ravel()], axis=0)  # 3 x (2nb)^3
+    out = np.empty((len(frac), nb, nb, nb), dtype=np.uint8)
+    for k, (fr, r, Rm) in enumerate(zip(frac, radii, rots)):
+        # fine points relative to the ellipsoid centre, in its body frame
+        rel = P - fr[:, None]
+        body = (Rm.T @ rel) / r[:, None]
+        inside = (np.einsum("ij,ij->j", body, body) <= 1.0).reshape(2 * nb, 2 * nb, 2 * nb)
+        out[k] = inside.reshape(nb, 2, nb, 2, nb, 2).sum(axis=(1, 3, 5))
+    return out
+
+
+def ellipsoids_truth(rng, dims, n, radii_range, intensity_range, workers: int = 1) -> np.ndarray:
+    """Solid ellipsoids (random radii, orientation, intensity), additive, periodic.
+
+    Each coarse voxel takes the fraction of its 2x2x2 fine samples inside the
+    ellipsoid times the intensity. ``workers > 1`` rasterises chunks in a
+    spawned process pool (the calling program's main module must be
+    import-safe, i.e. guarded by ``if __name__ == "__main__"``); the result is
+    identical.
+    """
+    X, Y, Z = dims
+    h = int(math.ceil(radii_range[1])) + 1
+    nb = 2 * h + 1
     vol = np.zeros((Z, Y, X))
     centres = rng.uniform(0, 1, size=(n, 3)) * np.array([X, Y, Z])
     radii = rng.uniform(*radii_range, size=(n, 3))
     inten = rng.uniform(*intensity_range, size=n)
     rots = [_random_rotation(rng) for _ in range(n)]
     base = np.arange(nb) - h
-    for c, r, I, Rm in zip(centres, radii, inten, rots):
-        ci = np.floor(c).astype(int)
-        frac = c - ci  # centre offset within its voxel
-        # fine points relative to the ellipsoid centre, in its body frame
-        rel = P - frac[:, None]
-        body = (Rm.T @ rel) / r[:, None]
-        inside = (np.einsum("ij,ij->j", body, body) <= 1.0).reshape(2 * nb, 2 * nb, 2 * nb)
-        block = inside.reshape(nb, 2, nb, 2, nb, 2).mean(axis=(1, 3, 5)) * I
-        xi = (ci[0] + base) % X
-        yi = (ci[1] + base) % Y
-        zi = (ci[2] + base) % Z
-        vol[np.ix_(zi, yi, xi)] += block
+    ci_all = np.floor(centres).astype(int)
+    frac_all = centres - ci_all  # centre offset within its voxel
+    chunk = 2048
+    jobs = [(h, frac_all[a:a + chunk], radii[a:a + chunk], rots[a:a + chunk]) for a in range(0, n, chunk)]
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(workers) as pool:
+            counts = pool.map(_ellipsoid_counts, jobs)
+    else:
+        counts = [_ellipsoid_counts(j) for j in jobs]
+    k = 0
+    for cnt in counts:
+        for c8 in cnt:
+            ci = ci_all[k]
+            block = (c8 / 8.0) * inten[k]
+            xi = (ci[0] + base) % X
+            yi = (ci[1] + base) % Y
+            zi = (ci[2] + base) % Z
+            vol[np.ix_(zi, yi, xi)] += block
+            k += 1
     return vol
 
 
@@ -305,14 +337,27 @@ def config2(seed: int = 1002) -> Workload:
 
 
 def config3(seed: int = 1003, dims=(1024, 1024, 512), n_objects=150_000) -> Workload:
-    """1024x1024x512, 150k ellipsoids, 7 views at k*51.43 deg, peak 200 + background 5."""
+    """1024x1024x512, 150k ellipsoids, 7 views at k*51.43 deg, peak 200 + background 5.
+
+    Every view is blurred once: with B_v the exact blur of the unscaled
+    objects, the truth is s * objects + 5 (s puts the brightest blurred
+    voxel of any view at 200 photons) and its image is s * B_v + 5 (the PSFs
+    sum to 1), drawn as Poisson counts.
+    """
     rng = np.random.default_rng(seed)
-    truth = ellipsoids_truth(rng, dims, n_objects, (3.0, 6.0), (0.5, 1.0))
+    objects = ellipsoids_truth(rng, dims, n_objects, (3.0, 6.0), (0.5, 1.0), workers=os.cpu_count() or 1)
     psfs, angles = _spim_psfs(7, 1.5, 5.0, (19, 19, 51))
-    truth = _scale_to_peak(truth, psfs, 200.0) + 5.0
-    views = _observe(rng, truth, psfs)
+    blurred = [image_exact(objects, _as_stored(p)).astype(np.float32) for p in psfs]
+    scale = 200.0 / max(float(b.max()) for b in blurred)
+    views = []
+    for i in range(len(blurred)):
+        lam = blurred[i].astype(np.float64) * scale + 5.0
+        blurred[i] = None
+        views.append(rng.poisson(lam).astype(np.float32))
+        del lam
+    truth = objects * scale + 5.0
     return _finish("ellipsoids-1024x1024x512-7views", dims, truth, psfs, views, 10,
-                   angles=angles)
+                   angles=angles, box=(19, 19, 51))
 
 
 def config4_layout(seed: int = 1004, n_volumes: int = 48):
