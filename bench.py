@@ -576,6 +576,92 @@ def run_large(args):
     return 0
 
 
+def run_grad(args):
+    """The PSF-calibration step on the 128x128x96 four-view workload: Gaussian PSFs from
+    per-view (sigma_xy, sigma_ax), 8 unrolled iterations, MSE to the truth, backward to
+    the sigmas and the views (forward + hand-written adjoint)."""
+    import torch
+
+    import __graft_entry__
+    import synth
+    from synth.workloads import config5_sigmas, rotated_box
+
+    __graft_entry__.build()
+    from paper_1308_0730_gb300 import autograd as ag
+    from paper_1308_0730_gb300 import mvd
+
+    w = synth.config5()
+    box, angles = w.meta["box"], w.meta["angles"]
+    views = torch.from_numpy(np.stack(w.views)).cuda()
+    truth = torch.from_numpy(w.truth).cuda()
+    sig0 = config5_sigmas(w.n_views)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sig = [torch.tensor(s_, dtype=torch.float64, requires_grad=True) for s_ in sig0]
+        psfs = [ag.gaussian_psf(s_, rotated_box(box, a), a, "z") for s_, a in zip(sig, angles)]
+        psi = ag.unrolled_deconvolve(views, psfs, w.n_iter)
+        loss = torch.mean((psi.double() - truth.double()) ** 2)
+        loss.backward()
+        return float(loss.detach()), [s_.grad for s_ in sig]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = mvd.mvd_launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            loss, grads = step()
+        ev1.record(stream)
+        ev1.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (mvd.mvd_launch_count() - launches0) / args.steps
+    mvd.mvd_profile_enable(True)
+    step()
+    torch.cuda.synchronize()
+    prof = mvd.mvd_profile_read()
+    mvd.mvd_profile_enable(False)
+    # the forward alone (the same 8 iterations through the single-volume engine)
+    psfs32 = [mvd.mvd_gaussian_psf(s_[0], s_[1], rotated_box(box, a), a, "z") for s_, a in zip(sig0, angles)]
+    with mvd.Deconvolver([views[v] for v in range(w.n_views)], psfs32, "efficient", stream=stream,
+                         path="fft") as d:
+        d.iterate(w.n_iter)
+        d.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            d.set_estimate(None)
+            d.iterate(w.n_iter)
+        ev1.record(stream)
+        ev1.synchronize()
+        fwd_ms = ev0.elapsed_time(ev1) / args.steps
+    X, Y, Z = w.dims
+    units = w.voxels * w.n_views * w.n_iter
+    tot = sum(t for (_, t) in prof.values())
+    kernels = {k: {"launches": n, "ms": t, "share": t / tot} for k, (n, t) in prof.items() if n}
+    T = max(int(np.prod(p.shape)) for p in psfs32)
+    conv_ops = w.voxels * T  # one FMA per voxel and tap
+    roof = None
+    if "direct_conv" in kernels:
+        per = kernels["direct_conv"]["ms"] / kernels["direct_conv"]["launches"]
+        ach = conv_ops / (per * 1e-3) / 1e12
+        peak = _alu_peak_tops(torch.cuda.get_device_properties(0).multi_processor_count)
+        roof = {"bound": "alu", "kernel": "direct_conv", "achieved": ach, "peak": peak, "unit": "T FP32 ops/s",
+                "frac": ach / peak, "traffic": None,
+                "note": "one FMA per voxel and tap of the largest PSF box"}
+    print(json.dumps({
+        "metric": "Gvoxel-view updates/s differentiated (forward + backward)", "value": units / (ms * 1e-3) / 1e9,
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "volume": [X, Y, Z], "views": w.n_views, "psf_box": list(box),
+                   "unrolled_iterations": w.n_iter, "loss": "mse to truth", "params": "per-view (sigma_xy, sigma_ax)"},
+        "forward_only_ms": fwd_ms, "backward_over_forward": (ms - fwd_ms) / fwd_ms, "loss": loss,
+        "dsigma": [[float(x) for x in g.tolist()] for g in grads], "gpu_launches": launches,
+        "kernels": kernels, "roofline": roof, "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -584,6 +670,8 @@ def main():
     ap.add_argument("--impl", default="mvd", choices=["mvd", "reference"])
     ap.add_argument("--quick", action="store_true",
                     help="only the device-resident timing (no FP32 comparison, end-to-end or CPU legs)")
+    ap.add_argument("--grad", action="store_true",
+                    help="time the PSF-calibration step (8 unrolled iterations, forward + adjoint) instead")
     ap.add_argument("--large", action="store_true",
                     help="time the 1024x1024x512 seven-view specimen (10 iterations) instead")
     ap.add_argument("--batched", action="store_true",
@@ -595,6 +683,8 @@ def main():
         return run_batched(args)
     if args.large:
         return run_large(args)
+    if args.grad:
+        return run_grad(args)
     return run_gpu(args)
 
 

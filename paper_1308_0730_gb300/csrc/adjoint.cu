@@ -25,7 +25,9 @@
 #include <cmath>
 #include <vector>
 
+#include "box_sum.cuh"
 #include "common.cuh"
+#include "dd.cuh"
 
 namespace mvd {
 
@@ -47,6 +49,20 @@ inline int grid_stride(long n) {
 __global__ void k_ratio(const float* b, const float* phi, float eps, float* r, long n) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         r[i] = phi[i] / fmaxf(b[i], eps);
+}
+
+// r = phi / max(b, eps) and r - 1 (the back-projection transforms r - 1:
+// c = (r - 1) * K + 1 because K sums to 1, and r - 1 is small where psi fits)
+__global__ void k_ratio_m1(const float* b, const float* phi, float eps, float* r, float* rm1, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float q = phi[i] / fmaxf(b[i], eps);
+        r[i] = q;
+        rm1[i] = q - 1.f;
+    }
+}
+
+__global__ void k_add_one(float* x, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) x[i] += 1.f;
 }
 
 // tb = g [psi c > eps] ; gnew = tb c ; cb = tb psi
@@ -86,6 +102,21 @@ __global__ void k_sum(const float* x, long n, double* out) {
 __global__ void k_add_mean(float* x, long n, const double* sum, double count) {
     const float add = (float)(*sum / count);
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) x[i] += add;
+}
+
+// out(x) = in((-x) mod dims): the mirrored volume, whose spectrum is the
+// conjugate (correlation with a volume = convolution with its mirror)
+__global__ void k_mirror_volume(const float* in, int X, int Y, int Z, float* out) {
+    const long n = (long)X * Y * Z;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % X), y = (int)((i / X) % Y), z = (int)(i / ((long)X * Y));
+        const int mx = x ? X - x : 0, my = y ? Y - y : 0, mz = z ? Z - z : 0;
+        out[i] = in[(long)mx + (long)X * (my + (long)Y * mz)];
+    }
+}
+
+__global__ void k_add_volume(float* y, const float* x, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) y[i] += x[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -169,64 +200,76 @@ struct KBox {
     }
 };
 
+// One warp per output value (blocks of kThreads threads hold kThreads / 32
+// outputs); i = the output's index, uniform within the warp.
+__device__ __forceinline__ int warp_item() { return (int)((blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5); }
+inline int warp_blocks(long n) { return (int)((n * 32 + kThreads - 1) / kThreads); }
+
 // out(d) = sum_e a(e) g(d - e), d and e on box a
 __global__ void k_kconv(const float* a, KBox ba, const float* g, KBox bg, float* out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = warp_item();
     if (i >= ba.size()) return;
     int dx, dy, dz;
     ba.offset(i, dx, dy, dz);
-    float s = 0.f;
-    for (int ez = max(-ba.hz(), dz - bg.hz()); ez <= min(ba.hz(), dz + bg.hz()); ++ez)
-        for (int ey = max(-ba.hy(), dy - bg.hy()); ey <= min(ba.hy(), dy + bg.hy()); ++ey)
-            for (int ex = max(-ba.hx(), dx - bg.hx()); ex <= min(ba.hx(), dx + bg.hx()); ++ex)
-                s = fmaf(a[ba.index(ex, ey, ez)], g[bg.index(dx - ex, dy - ey, dz - ez)], s);
-    out[i] = s;
+    const float s = warp_box_sum(max(-ba.hx(), dx - bg.hx()), min(ba.hx(), dx + bg.hx()),
+                                 max(-ba.hy(), dy - bg.hy()), min(ba.hy(), dy + bg.hy()),
+                                 max(-ba.hz(), dz - bg.hz()), min(ba.hz(), dz + bg.hz()),
+                                 [&](int ex, int ey, int ez, float acc) {
+                                     return fmaf(a[ba.index(ex, ey, ez)], g[bg.index(dx - ex, dy - ey, dz - ez)], acc);
+                                 });
+    if ((threadIdx.x & 31) == 0) out[i] = s;
 }
 
 // ab(e) += sum_d cb(d) g(d - e)   (adjoint of k_kconv in a), d and e on box a
 __global__ void k_kconv_ta(const float* cb, KBox ba, const float* g, KBox bg, float* ab) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = warp_item();
     if (i >= ba.size()) return;
     int ex, ey, ez;
     ba.offset(i, ex, ey, ez);
-    float s = 0.f;
-    for (int dz = max(-ba.hz(), ez - bg.hz()); dz <= min(ba.hz(), ez + bg.hz()); ++dz)
-        for (int dy = max(-ba.hy(), ey - bg.hy()); dy <= min(ba.hy(), ey + bg.hy()); ++dy)
-            for (int dx = max(-ba.hx(), ex - bg.hx()); dx <= min(ba.hx(), ex + bg.hx()); ++dx)
-                s = fmaf(cb[ba.index(dx, dy, dz)], g[bg.index(dx - ex, dy - ey, dz - ez)], s);
-    ab[i] += s;
+    const float s = warp_box_sum(max(-ba.hx(), ex - bg.hx()), min(ba.hx(), ex + bg.hx()),
+                                 max(-ba.hy(), ey - bg.hy()), min(ba.hy(), ey + bg.hy()),
+                                 max(-ba.hz(), ez - bg.hz()), min(ba.hz(), ez + bg.hz()),
+                                 [&](int dx, int dy, int dz, float acc) {
+                                     return fmaf(cb[ba.index(dx, dy, dz)], g[bg.index(dx - ex, dy - ey, dz - ez)], acc);
+                                 });
+    if ((threadIdx.x & 31) == 0) ab[i] += s;
 }
 
 // gb(f) = sum_e cb(e + f) a(e)   (adjoint of k_kconv in g), f on box g
 __global__ void k_kconv_tg(const float* cb, const float* a, KBox ba, float* gb, KBox bg) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = warp_item();
     if (i >= bg.size()) return;
     int fx, fy, fz;
     bg.offset(i, fx, fy, fz);
-    float s = 0.f;
-    for (int ez = max(-ba.hz(), -ba.hz() - fz); ez <= min(ba.hz(), ba.hz() - fz); ++ez)
-        for (int ey = max(-ba.hy(), -ba.hy() - fy); ey <= min(ba.hy(), ba.hy() - fy); ++ey)
-            for (int ex = max(-ba.hx(), -ba.hx() - fx); ex <= min(ba.hx(), ba.hx() - fx); ++ex)
-                s = fmaf(cb[ba.index(ex + fx, ey + fy, ez + fz)], a[ba.index(ex, ey, ez)], s);
-    gb[i] = s;
+    const float s = warp_box_sum(max(-ba.hx(), -ba.hx() - fx), min(ba.hx(), ba.hx() - fx),
+                                 max(-ba.hy(), -ba.hy() - fy), min(ba.hy(), ba.hy() - fy),
+                                 max(-ba.hz(), -ba.hz() - fz), min(ba.hz(), ba.hz() - fz),
+                                 [&](int ex, int ey, int ez, float acc) {
+                                     return fmaf(cb[ba.index(ex + fx, ey + fy, ez + fz)], a[ba.index(ex, ey, ez)], acc);
+                                 });
+    if ((threadIdx.x & 31) == 0) gb[i] = s;
 }
 
-// Q(f) = sum_g P(g) P(g - f): pb(h) += sum_f qb(f) (P(h - f) + P(h + f)), h on box p
+// Q(f) = sum_g P(g) P(g - f): pb(h) += sum_f qb(f) (P(h - f) + P(h + f)), h on box p,
+// f on box q (the two terms as two box sums: h - f in box p, h + f in box p)
 __global__ void k_autocorr_vjp(const float* qb, KBox bq, const float* p, KBox bp, float* pb) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = warp_item();
     if (i >= bp.size()) return;
     int hx, hy, hz;
     bp.offset(i, hx, hy, hz);
-    float s = 0.f;
-    for (int fz = -bq.hz(); fz <= bq.hz(); ++fz)
-        for (int fy = -bq.hy(); fy <= bq.hy(); ++fy)
-            for (int fx = -bq.hx(); fx <= bq.hx(); ++fx) {
-                float pp = 0.f;
-                if (bp.in(hx - fx, hy - fy, hz - fz)) pp += p[bp.index(hx - fx, hy - fy, hz - fz)];
-                if (bp.in(hx + fx, hy + fy, hz + fz)) pp += p[bp.index(hx + fx, hy + fy, hz + fz)];
-                s = fmaf(qb[bq.index(fx, fy, fz)], pp, s);
-            }
-    pb[i] += s;
+    const float s1 = warp_box_sum(max(-bq.hx(), hx - bp.hx()), min(bq.hx(), hx + bp.hx()),
+                                  max(-bq.hy(), hy - bp.hy()), min(bq.hy(), hy + bp.hy()),
+                                  max(-bq.hz(), hz - bp.hz()), min(bq.hz(), hz + bp.hz()),
+                                  [&](int fx, int fy, int fz, float acc) {
+                                      return fmaf(qb[bq.index(fx, fy, fz)], p[bp.index(hx - fx, hy - fy, hz - fz)], acc);
+                                  });
+    const float s2 = warp_box_sum(max(-bq.hx(), -bp.hx() - hx), min(bq.hx(), bp.hx() - hx),
+                                  max(-bq.hy(), -bp.hy() - hy), min(bq.hy(), bp.hy() - hy),
+                                  max(-bq.hz(), -bp.hz() - hz), min(bq.hz(), bp.hz() - hz),
+                                  [&](int fx, int fy, int fz, float acc) {
+                                      return fmaf(qb[bq.index(fx, fy, fz)], p[bp.index(hx + fx, hy + fy, hz + fz)], acc);
+                                  });
+    if ((threadIdx.x & 31) == 0) pb[i] += s1 + s2;
 }
 
 // pb(d) += ab(-d)
@@ -236,6 +279,17 @@ __global__ void k_mirror_add(const float* ab, KBox b, float* pb) {
     int dx, dy, dz;
     b.offset(i, dx, dy, dz);
     pb[i] += ab[b.index(-dx, -dy, -dz)];
+}
+
+// out(d) += vol(d mod dims) for d on the centred box b (a full correlation
+// volume cropped to the kernel's support)
+__global__ void k_crop_add(const float* vol, int X, int Y, int Z, KBox b, float* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.size()) return;
+    int dx, dy, dz;
+    b.offset(i, dx, dy, dz);
+    const int x = ((dx % X) + X) % X, y = ((dy % Y) + Y) % Y, z = ((dz % Z) + Z) % Z;
+    out[i] += vol[(long)x + (long)X * (y + (long)Y * z)];
 }
 
 constexpr int kMaxViews = 32;
@@ -335,45 +389,53 @@ mvd_status corr_to_box(const float* a, const float* b, const int dims[3], const 
         return MVD_ERR_UNSUPPORTED;
     }
     MVD_CUDA(cudaFuncSetAttribute(k_corr_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    prof_begin(KC_KERNEL_GRAD, st);
     k_corr_partial<<<(unsigned)ntiles, kThreads, smem, st>>>(a, b, X, Y, Z, kd[0], kd[1], kd[2], partial);
-    LAUNCH_CHECK("kernel-gradient correlation");
     const int T = kd[0] * kd[1] * kd[2];
     k_corr_reduce<<<blocks_for(T), kThreads, 0, st>>>(partial, ntiles, T, out_acc);
-    LAUNCH_CHECK("kernel-gradient reduction");
+    prof_end(KC_KERNEL_GRAD, st);
+    count_launch(2);
+    MVD_TRY(check_launch("kernel-gradient correlation"));
     return MVD_OK;
 }
 
 }  // namespace
 
+// scratch of the compound-kernel VJP, sized for the largest box
+struct VjpScratch {
+    float *A = nullptr, *U = nullptr, *Ab = nullptr, *Cb = nullptr, *Cf = nullptr, *Q = nullptr, *Gb = nullptr;
+    long qmax = 1;
+    mvd_status alloc_for(const mvd_ctx* c) {
+        long tmax = 1;
+        for (int w = 0; w < c->nv; ++w) {
+            const int* k = &c->kd[3 * w];
+            tmax = std::max(tmax, (long)k[0] * k[1] * k[2]);
+            qmax = std::max(qmax, (long)(2 * k[0] - 1) * (2 * k[1] - 1) * (2 * k[2] - 1));
+        }
+        MVD_TRY(alloc(&A, tmax, "vjp A"));
+        MVD_TRY(alloc(&U, tmax, "vjp U"));
+        MVD_TRY(alloc(&Ab, tmax, "vjp Ab"));
+        MVD_TRY(alloc(&Cb, (size_t)c->nv * tmax, "vjp Cb"));
+        MVD_TRY(alloc(&Cf, (size_t)c->nv * tmax, "vjp C"));
+        MVD_TRY(alloc(&Q, (size_t)c->nv * qmax, "vjp Q"));
+        return alloc(&Gb, qmax, "vjp Gb");
+    }
+    void release() {
+        for (float* p : {A, U, Ab, Cb, Cf, Q, Gb})
+            if (p) cudaFree(p);
+        A = U = Ab = Cb = Cf = Q = Gb = nullptr;
+    }
+};
+
 // compound-kernel VJP for view v: Pb[w] += d K_v / d Pn_w applied to Kb
-static mvd_status compound_vjp(mvd_ctx* c, int v, const float* Kb, float* Pb, cudaStream_t st) {
+static mvd_status compound_vjp(mvd_ctx* c, int v, const float* Kb, float* Pb, const VjpScratch& sc, cudaStream_t st) {
     const int nv = c->nv;
     const int* dv = &c->kd[3 * v];
     const int Tv = dv[0] * dv[1] * dv[2];
     const KBox bv = kbox(dv);
     const float* Pv = c->d_psf + c->koff[v];
-    long qmax = 1;
-    for (int w = 0; w < nv; ++w) {
-        const int* k = &c->kd[3 * w];
-        qmax = std::max(qmax, (long)(2 * k[0] - 1) * (2 * k[1] - 1) * (2 * k[2] - 1));
-    }
-    float *A, *U, *Ab, *Cb, *Cf, *Q, *Gb;
-    MVD_TRY(alloc(&A, Tv, "vjp A"));
-    MVD_TRY(alloc(&U, Tv, "vjp U"));
-    MVD_TRY(alloc(&Ab, Tv, "vjp Ab"));
-    MVD_TRY(alloc(&Cb, (size_t)nv * Tv, "vjp Cb"));
-    MVD_TRY(alloc(&Cf, (size_t)nv * Tv, "vjp C"));
-    MVD_TRY(alloc(&Q, (size_t)nv * qmax, "vjp Q"));
-    MVD_TRY(alloc(&Gb, qmax, "vjp Gb"));
-    auto cleanup = [&]() {
-        cudaFree(A);
-        cudaFree(U);
-        cudaFree(Ab);
-        cudaFree(Cb);
-        cudaFree(Cf);
-        cudaFree(Q);
-        cudaFree(Gb);
-    };
+    const long qmax = sc.qmax;
+    float *A = sc.A, *U = sc.U, *Ab = sc.Ab, *Cb = sc.Cb, *Cf = sc.Cf, *Q = sc.Q, *Gb = sc.Gb;
     mvd_status stt = MVD_OK;
     do {
         if ((stt = mirror_kernel(Pv, dv, A, st)) != MVD_OK) break;
@@ -388,9 +450,9 @@ static mvd_status compound_vjp(mvd_ctx* c, int v, const float* Kb, float* Pb, cu
                     float* Qw = Q + (size_t)w * qmax;
                     const int qd[3] = {2 * dw[0] - 1, 2 * dw[1] - 1, 2 * dw[2] - 1};
                     if ((stt = autocorr_kernel(Pw, dw, Qw, st)) != MVD_OK) break;
-                    k_kconv<<<blocks_for(Tv), kThreads, 0, st>>>(A, bv, Qw, kbox(qd), Cw);
+                    k_kconv<<<warp_blocks(Tv), kThreads, 0, st>>>(A, bv, Qw, kbox(qd), Cw);
                 } else if (c->variant == MVD_OPT1) {
-                    k_kconv<<<blocks_for(Tv), kThreads, 0, st>>>(A, bv, Pw, kbox(dw), Cw);
+                    k_kconv<<<warp_blocks(Tv), kThreads, 0, st>>>(A, bv, Pw, kbox(dw), Cw);
                 } else {
                     cudaError_t e = cudaMemcpyAsync(Cw, A, sizeof(float) * Tv, cudaMemcpyDeviceToDevice, st);
                     if (e != cudaSuccess) {
@@ -422,12 +484,12 @@ static mvd_status compound_vjp(mvd_ctx* c, int v, const float* Kb, float* Pb, cu
             const int qd[3] = {2 * dw[0] - 1, 2 * dw[1] - 1, 2 * dw[2] - 1};
             const float* G = c->variant == MVD_EFFICIENT ? Q + (size_t)w * qmax : Pw;
             const KBox bg = c->variant == MVD_EFFICIENT ? kbox(qd) : kbox(dw);
-            k_kconv_ta<<<blocks_for(Tv), kThreads, 0, st>>>(Cbw, bv, G, bg, Ab);
+            k_kconv_ta<<<warp_blocks(Tv), kThreads, 0, st>>>(Cbw, bv, G, bg, Ab);
             count_launch();
-            k_kconv_tg<<<blocks_for(bg.kx * bg.ky * bg.kz), kThreads, 0, st>>>(Cbw, A, bv, Gb, bg);
+            k_kconv_tg<<<warp_blocks(bg.kx * bg.ky * bg.kz), kThreads, 0, st>>>(Cbw, A, bv, Gb, bg);
             count_launch();
             if (c->variant == MVD_EFFICIENT) {
-                k_autocorr_vjp<<<blocks_for(Tw), kThreads, 0, st>>>(Gb, bg, Pw, kbox(dw), Pbw);
+                k_autocorr_vjp<<<warp_blocks(Tw), kThreads, 0, st>>>(Gb, bg, Pw, kbox(dw), Pbw);
             } else {
                 k_add<<<blocks_for(Tw), kThreads, 0, st>>>(Pbw, Gb, Tw);
             }
@@ -439,9 +501,179 @@ static mvd_status compound_vjp(mvd_ctx* c, int v, const float* Kb, float* Pb, cu
         count_launch();
         stt = check_launch("vjp mirror");
     } while (false);
+    return stt;
+}
+
+// Circular convolutions through the FP32 FFT engine: spectra of kernels or
+// volumes (full 3D transform, scaled by 1/M) and products with them.
+struct FftConv {
+    mvd_ctx* c;
+    float2* S;  // work spectrum
+    cudaStream_t st;
+    mvd_status spectrum(const float* vol, float2* spec) const {
+        MVD_TRY(fft_forward_real(c->geom, vol, spec, st));
+        MVD_TRY(fft_y(c->geom, spec, 0, st));
+        return fft_z_forward_scaled(c->geom, spec, (float)(1.0 / (double)c->M), st);
+    }
+    mvd_status conv(const float* in, const float2* spec, float* out) const {
+        MVD_TRY(fft_forward_real(c->geom, in, S, st));
+        MVD_TRY(fft_y(c->geom, S, 0, st));
+        MVD_TRY(fft_z_mul(c->geom, S, spec, st));
+        MVD_TRY(fft_y(c->geom, S, 1, st));
+        return fft_inverse_real(c->geom, S, out, st);
+    }
+};
+
+// The reverse pass on the FFT engine (contexts whose path is FFT). Per update:
+// b = psi * P, r, c = (r - 1) * K + 1 recomputed; r_bar = c_bar * K^*,
+// psi_bar += b_bar * P^* (mirrored kernels' spectra); K_bar and P_bar are the
+// full correlations c_bar * mirror(r) and b_bar * mirror(psi), cropped to the
+// kernel box. FFT rounding is absolute (it scales with the whole volume's
+// norm), while the view gradient r_bar / b is largest where b is dim, so when
+// the forward ran in double-float, b, r_bar and the b_bar * P^* term are
+// double-float convolutions too; c and the cropped correlations (sums over
+// the whole volume) stay FP32.
+static mvd_status backward_fft(mvd_ctx* c, const float* grad_psi, float* const* grad_views, float* Kb, float* Pb,
+                               double* dsum) {
+    const long M = c->M;
+    const int nv = c->nv;
+    cudaStream_t st = c->stream;
+    const FftGeom& g = c->geom;
+    const size_t ns = (size_t)g.Xh * g.YZ;
+    float *work = nullptr, *stage = nullptr, *kt = nullptr;
+    float2 *spec = nullptr, *specA = nullptr, *S = nullptr;
+    cdd* specDD = nullptr;
+    int Tmax = 1;
+    for (int v = 0; v < nv; ++v) Tmax = std::max(Tmax, c->kd[3 * v] * c->kd[3 * v + 1] * c->kd[3 * v + 2]);
+    mvd_status stt = MVD_OK;
+    do {
+        if ((stt = alloc(&work, (size_t)10 * M, "adjoint work")) != MVD_OK) break;
+        if ((stt = alloc(&stage, (size_t)nv * M, "replayed estimates")) != MVD_OK) break;
+        if ((stt = alloc(&kt, (size_t)Tmax, "mirrored kernel")) != MVD_OK) break;
+        if ((stt = alloc(&spec, (size_t)4 * nv * ns, "kernel spectra")) != MVD_OK) break;
+        if ((stt = alloc(&specA, ns, "volume spectrum")) != MVD_OK) break;
+        if ((stt = alloc(&S, ns, "work spectrum")) != MVD_OK) break;
+        float *B = work, *R = work + M, *C = work + 2 * M, *CB = work + 3 * M, *RB = work + 4 * M,
+              *BB = work + 5 * M, *G = work + 6 * M, *G2 = work + 7 * M, *MIR = work + 8 * M, *TMP = work + 9 * M;
+        const FftConv F{c, S, st};
+        const bool dd = c->precise && c->d_KP2 && c->d_S2 && dd_fast_x(g);
+        // double-float spectra of the mirrored kernels: 2v P^*, 2v+1 K^*
+        if (dd && (stt = alloc(reinterpret_cast<float4**>(&specDD), (size_t)2 * nv * ns, "mirrored spectra")) != MVD_OK)
+            break;
+        for (int v = 0; v < nv && dd && stt == MVD_OK; ++v) {
+            const int* kd = &c->kd[3 * v];
+            for (int j = 0; j < 2 && stt == MVD_OK; ++j) {
+                cdd* dst = specDD + (size_t)(2 * v + j) * ns;
+                if ((stt = mirror_kernel((j == 0 ? c->d_psf : c->d_comp) + c->koff[v], kd, kt, st)) != MVD_OK) break;
+                if ((stt = place_kernel(c->dims, kt, kd, TMP, st)) != MVD_OK) break;
+                if ((stt = dd_forward_real(g, TMP, dst, st)) != MVD_OK) break;
+                if ((stt = dd_y(g, dst, 0, st)) != MVD_OK) break;
+                stt = dd_z_forward_scaled(g, dst, 1.0 / (double)M, st);
+            }
+        }
+        if (stt != MVD_OK) break;
+        auto dd_conv = [&](const float* in, const cdd* K2, float* out) -> mvd_status {
+            MVD_TRY(dd_forward_real(g, in, c->d_S2, st));
+            MVD_TRY(dd_y(g, c->d_S2, 0, st));
+            MVD_TRY(dd_z_mul(g, c->d_S2, K2, st));
+            MVD_TRY(dd_y(g, c->d_S2, 1, st));
+            return dd_x_inverse_real(g, c->d_S2, out, st);
+        };
+        // spectra per view: 4v P, 4v+1 K, 4v+2 P^*, 4v+3 K^*
+        for (int v = 0; v < nv && stt == MVD_OK; ++v) {
+            const int* kd = &c->kd[3 * v];
+            const float* ks[2] = {c->d_psf + c->koff[v], c->d_comp + c->koff[v]};
+            for (int j = 0; j < 4 && stt == MVD_OK; ++j) {
+                const float* k = ks[j & 1];
+                if (j >= 2) {
+                    if ((stt = mirror_kernel(k, kd, kt, st)) != MVD_OK) break;
+                    k = kt;
+                }
+                if ((stt = place_kernel(c->dims, k, kd, TMP, st)) != MVD_OK) break;
+                stt = F.spectrum(TMP, spec + (size_t)(4 * v + j) * ns);
+            }
+        }
+        if (stt != MVD_OK) break;
+        cudaMemsetAsync(Kb, 0, sizeof(float) * c->ktotal, st);
+        cudaMemsetAsync(Pb, 0, sizeof(float) * c->ktotal, st);
+        for (int v = 0; v < nv; ++v) cudaMemsetAsync(grad_views[v], 0, sizeof(float) * M, st);
+        if ((stt = copy_volume(G, grad_psi, M, st)) != MVD_OK) break;
+        for (long u = (long)c->ckpt_iters * nv - 1; u >= 0 && stt == MVD_OK; --u) {
+            const int v = (int)(u % nv);
+            if (v == nv - 1) {  // replay iteration u / nv from its checkpoint with the forward's engine
+                stt = copy_volume(c->d_psi, c->d_ckpt + (size_t)(u / nv) * M, M, st);
+                for (int w = 0; w < nv && stt == MVD_OK; ++w) {
+                    stt = copy_volume(stage + (size_t)w * M, c->d_psi, M, st);
+                    if (stt == MVD_OK && w < nv - 1) stt = one_update(c, w);
+                }
+                if (stt != MVD_OK) break;
+            }
+            const KBox box = kbox(&c->kd[3 * v]);
+            const float* psi = stage + (size_t)v * M;
+            const float* phi = c->d_views + (size_t)v * M;
+            const float2* sP = spec + (size_t)(4 * v) * ns;
+            const float2* sK = sP + ns;
+            const float2* sPm = sP + 2 * ns;
+            const float2* sKm = sP + 3 * ns;
+            // forward intermediates
+            if (dd) {
+                const cdd* Kp2 = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_KP2) + ns * (2 * v));
+                if ((stt = dd_conv(psi, Kp2, B)) != MVD_OK) break;
+            } else if ((stt = F.conv(psi, sP, B)) != MVD_OK) {
+                break;
+            }
+            k_ratio_m1<<<grid_stride(M), kThreads, 0, st>>>(B, phi, c->eps, R, TMP, M);
+            count_launch();
+            if ((stt = F.conv(TMP, sK, C)) != MVD_OK) break;
+            k_add_one<<<grid_stride(M), kThreads, 0, st>>>(C, M);
+            count_launch();
+            // adjoint
+            k_adj_update<<<grid_stride(M), kThreads, 0, st>>>(psi, C, G, c->eps, G2, CB, M);
+            count_launch();
+            if ((stt = dd ? dd_conv(CB, specDD + (size_t)(2 * v + 1) * ns, RB) : F.conv(CB, sKm, RB)) != MVD_OK) break;
+            k_mirror_volume<<<grid_stride(M), kThreads, 0, st>>>(R, c->dims[0], c->dims[1], c->dims[2], MIR);
+            count_launch();
+            if ((stt = F.spectrum(MIR, specA)) != MVD_OK) break;
+            if ((stt = F.conv(CB, specA, TMP)) != MVD_OK) break;
+            k_crop_add<<<blocks_for(box.kx * box.ky * box.kz), kThreads, 0, st>>>(
+                TMP, c->dims[0], c->dims[1], c->dims[2], box, Kb + c->koff[v]);
+            count_launch();
+            k_adj_ratio<<<grid_stride(M), kThreads, 0, st>>>(RB, B, R, c->eps, grad_views[v], BB, M);
+            count_launch();
+            if ((stt = dd ? dd_conv(BB, specDD + (size_t)(2 * v) * ns, TMP) : F.conv(BB, sPm, TMP)) != MVD_OK) break;
+            k_add_volume<<<grid_stride(M), kThreads, 0, st>>>(G2, TMP, M);
+            count_launch();
+            k_mirror_volume<<<grid_stride(M), kThreads, 0, st>>>(psi, c->dims[0], c->dims[1], c->dims[2], MIR);
+            count_launch();
+            if ((stt = F.spectrum(MIR, specA)) != MVD_OK) break;
+            if ((stt = F.conv(BB, specA, TMP)) != MVD_OK) break;
+            k_crop_add<<<blocks_for(box.kx * box.ky * box.kz), kThreads, 0, st>>>(
+                TMP, c->dims[0], c->dims[1], c->dims[2], box, Pb + c->koff[v]);
+            count_launch();
+            if ((stt = check_launch("adjoint step")) != MVD_OK) break;
+            std::swap(G, G2);
+        }
+        if (stt != MVD_OK) break;
+        if (c->ckpt_flat) {  // psi0 = mean of all views
+            cudaMemsetAsync(dsum, 0, sizeof(double), st);
+            k_sum<<<grid_stride(M), kThreads, 0, st>>>(G, M, dsum);
+            count_launch();
+            for (int v = 0; v < nv; ++v) {
+                k_add_mean<<<grid_stride(M), kThreads, 0, st>>>(grad_views[v], M, dsum, (double)M * nv);
+                count_launch();
+            }
+            stt = check_launch("flat start");
+        }
+    } while (false);
     const cudaError_t se = cudaStreamSynchronize(st);
-    if (stt == MVD_OK && se != cudaSuccess) stt = cuda_status(se, "vjp sync");
-    cleanup();
+    if (stt == MVD_OK && se != cudaSuccess) stt = cuda_status(se, "adjoint sync");
+    cudaFree(work);
+    cudaFree(stage);
+    cudaFree(kt);
+    cudaFree(spec);
+    cudaFree(specA);
+    cudaFree(S);
+    cudaFree(specDD);
     return stt;
 }
 
@@ -511,11 +743,13 @@ mvd_status mvd_unrolled_backward(mvd_ctx* c, const float* grad_psi, float* const
             set_error("mvd_unrolled_backward: gradient buffer %d is NULL", v);
             return MVD_ERR_ARG;
         }
-        if (!direct_supported(&c->kd[3 * v]) || corr_smem(&c->kd[3 * v]) > kCorrMaxSmem) {
+        if (c->path != MVD_PATH_FFT &&
+            (!direct_supported(&c->kd[3 * v]) || corr_smem(&c->kd[3 * v]) > kCorrMaxSmem)) {
             set_error("mvd_unrolled_backward: PSF %d too large for the direct engine", v);
             return MVD_ERR_UNSUPPORTED;
         }
     }
+    const bool use_fft = c->path == MVD_PATH_FFT;
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != c->device) cudaSetDevice(c->device);
@@ -529,67 +763,75 @@ mvd_status mvd_unrolled_backward(mvd_ctx* c, const float* grad_psi, float* const
     double* dsum = nullptr;
     mvd_status stt = MVD_OK;
     do {
-        if ((stt = alloc(&work, (size_t)8 * M, "adjoint work")) != MVD_OK) break;
-        if ((stt = alloc(&stage, (size_t)nv * M, "replayed estimates")) != MVD_OK) break;
-        if ((stt = alloc(&partial, (size_t)ntiles * Tmax, "correlation partials")) != MVD_OK) break;
         if ((stt = alloc(&Kb, (size_t)c->ktotal, "kernel gradients")) != MVD_OK) break;
         if ((stt = alloc(&Pb, (size_t)c->ktotal, "PSF gradients")) != MVD_OK) break;
-        if ((stt = alloc(&mir, (size_t)2 * Tmax, "mirrored kernels")) != MVD_OK) break;
         if ((stt = alloc(&dsum, 1, "sum")) != MVD_OK) break;
-        float *B = work, *R = work + M, *C = work + 2 * M, *CB = work + 3 * M, *RB = work + 4 * M,
-              *BB = work + 5 * M, *G = work + 6 * M, *G2 = work + 7 * M;
-        cudaMemsetAsync(Kb, 0, sizeof(float) * c->ktotal, st);
-        cudaMemsetAsync(Pb, 0, sizeof(float) * c->ktotal, st);
-        for (int v = 0; v < nv; ++v) cudaMemsetAsync(grad_views[v], 0, sizeof(float) * M, st);
-        cudaMemcpyAsync(G, grad_psi, sizeof(float) * M, cudaMemcpyDeviceToDevice, st);
-        for (long u = (long)c->ckpt_iters * nv - 1; u >= 0 && stt == MVD_OK; --u) {
-            const int v = (int)(u % nv);
-            if (v == nv - 1) {  // replay iteration u / nv from its checkpoint
-                stt = copy_volume(c->d_psi, c->d_ckpt + (size_t)(u / nv) * M, M, st);
-                for (int w = 0; w < nv && stt == MVD_OK; ++w) {
-                    stt = copy_volume(stage + (size_t)w * M, c->d_psi, M, st);
-                    if (stt == MVD_OK && w < nv - 1) stt = one_update(c, w);
+        if (use_fft) {
+            if ((stt = backward_fft(c, grad_psi, grad_views, Kb, Pb, dsum)) != MVD_OK) break;
+        } else {
+            if ((stt = alloc(&work, (size_t)8 * M, "adjoint work")) != MVD_OK) break;
+            if ((stt = alloc(&stage, (size_t)nv * M, "replayed estimates")) != MVD_OK) break;
+            if ((stt = alloc(&partial, (size_t)ntiles * Tmax, "correlation partials")) != MVD_OK) break;
+            if ((stt = alloc(&mir, (size_t)2 * Tmax, "mirrored kernels")) != MVD_OK) break;
+            float *B = work, *R = work + M, *C = work + 2 * M, *CB = work + 3 * M, *RB = work + 4 * M,
+                  *BB = work + 5 * M, *G = work + 6 * M, *G2 = work + 7 * M;
+            cudaMemsetAsync(Kb, 0, sizeof(float) * c->ktotal, st);
+            cudaMemsetAsync(Pb, 0, sizeof(float) * c->ktotal, st);
+            for (int v = 0; v < nv; ++v) cudaMemsetAsync(grad_views[v], 0, sizeof(float) * M, st);
+            cudaMemcpyAsync(G, grad_psi, sizeof(float) * M, cudaMemcpyDeviceToDevice, st);
+            for (long u = (long)c->ckpt_iters * nv - 1; u >= 0 && stt == MVD_OK; --u) {
+                const int v = (int)(u % nv);
+                if (v == nv - 1) {  // replay iteration u / nv from its checkpoint
+                    stt = copy_volume(c->d_psi, c->d_ckpt + (size_t)(u / nv) * M, M, st);
+                    for (int w = 0; w < nv && stt == MVD_OK; ++w) {
+                        stt = copy_volume(stage + (size_t)w * M, c->d_psi, M, st);
+                        if (stt == MVD_OK && w < nv - 1) stt = one_update(c, w);
+                    }
+                    if (stt != MVD_OK) break;
                 }
-                if (stt != MVD_OK) break;
-            }
-            const int* kd = &c->kd[3 * v];
-            const float* psi = stage + (size_t)v * M;
-            const float* phi = c->d_views + (size_t)v * M;
-            const float* P = c->d_psf + c->koff[v];
-            const float* K = c->d_comp + c->koff[v];
-            float* Ks = mir;
-            float* Ps = mir + Tmax;
-            if ((stt = mirror_kernel(K, kd, Ks, st)) != MVD_OK) break;
-            if ((stt = mirror_kernel(P, kd, Ps, st)) != MVD_OK) break;
-            // forward intermediates
-            if ((stt = direct_conv(c->dims, psi, P, kd, B, st)) != MVD_OK) break;
-            k_ratio<<<grid_stride(M), kThreads, 0, st>>>(B, phi, c->eps, R, M);
-            count_launch();
-            if ((stt = direct_conv(c->dims, R, K, kd, C, st)) != MVD_OK) break;
-            // adjoint
-            k_adj_update<<<grid_stride(M), kThreads, 0, st>>>(psi, C, G, c->eps, G2, CB, M);
-            count_launch();
-            if ((stt = direct_conv(c->dims, CB, Ks, kd, RB, st)) != MVD_OK) break;
-            if ((stt = corr_to_box(CB, R, c->dims, kd, Kb + c->koff[v], partial, st)) != MVD_OK) break;
-            k_adj_ratio<<<grid_stride(M), kThreads, 0, st>>>(RB, B, R, c->eps, grad_views[v], BB, M);
-            count_launch();
-            if ((stt = direct_conv_add(c->dims, BB, Ps, kd, G2, st)) != MVD_OK) break;
-            if ((stt = corr_to_box(BB, psi, c->dims, kd, Pb + c->koff[v], partial, st)) != MVD_OK) break;
-            if ((stt = check_launch("adjoint step")) != MVD_OK) break;
-            std::swap(G, G2);
-        }
-        if (stt != MVD_OK) break;
-        if (c->ckpt_flat) {  // psi0 = mean of all views
-            cudaMemsetAsync(dsum, 0, sizeof(double), st);
-            k_sum<<<grid_stride(M), kThreads, 0, st>>>(G, M, dsum);
-            count_launch();
-            for (int v = 0; v < nv; ++v) {
-                k_add_mean<<<grid_stride(M), kThreads, 0, st>>>(grad_views[v], M, dsum, (double)M * nv);
+                const int* kd = &c->kd[3 * v];
+                const float* psi = stage + (size_t)v * M;
+                const float* phi = c->d_views + (size_t)v * M;
+                const float* P = c->d_psf + c->koff[v];
+                const float* K = c->d_comp + c->koff[v];
+                float* Ks = mir;
+                float* Ps = mir + Tmax;
+                if ((stt = mirror_kernel(K, kd, Ks, st)) != MVD_OK) break;
+                if ((stt = mirror_kernel(P, kd, Ps, st)) != MVD_OK) break;
+                // forward intermediates
+                if ((stt = direct_conv(c->dims, psi, P, kd, B, st)) != MVD_OK) break;
+                k_ratio<<<grid_stride(M), kThreads, 0, st>>>(B, phi, c->eps, R, M);
                 count_launch();
+                if ((stt = direct_conv(c->dims, R, K, kd, C, st)) != MVD_OK) break;
+                // adjoint
+                k_adj_update<<<grid_stride(M), kThreads, 0, st>>>(psi, C, G, c->eps, G2, CB, M);
+                count_launch();
+                if ((stt = direct_conv(c->dims, CB, Ks, kd, RB, st)) != MVD_OK) break;
+                if ((stt = corr_to_box(CB, R, c->dims, kd, Kb + c->koff[v], partial, st)) != MVD_OK) break;
+                k_adj_ratio<<<grid_stride(M), kThreads, 0, st>>>(RB, B, R, c->eps, grad_views[v], BB, M);
+                count_launch();
+                if ((stt = direct_conv_add(c->dims, BB, Ps, kd, G2, st)) != MVD_OK) break;
+                if ((stt = corr_to_box(BB, psi, c->dims, kd, Pb + c->koff[v], partial, st)) != MVD_OK) break;
+                if ((stt = check_launch("adjoint step")) != MVD_OK) break;
+                std::swap(G, G2);
             }
-            if ((stt = check_launch("flat start")) != MVD_OK) break;
-        }
-        for (int v = 0; v < nv && stt == MVD_OK; ++v) stt = compound_vjp(c, v, Kb + c->koff[v], Pb, st);
+            if (stt != MVD_OK) break;
+            if (c->ckpt_flat) {  // psi0 = mean of all views
+                cudaMemsetAsync(dsum, 0, sizeof(double), st);
+                k_sum<<<grid_stride(M), kThreads, 0, st>>>(G, M, dsum);
+                count_launch();
+                for (int v = 0; v < nv; ++v) {
+                    k_add_mean<<<grid_stride(M), kThreads, 0, st>>>(grad_views[v], M, dsum, (double)M * nv);
+                    count_launch();
+                }
+                if ((stt = check_launch("flat start")) != MVD_OK) break;
+            }
+        }  // direct engine
+        VjpScratch sc;
+        stt = sc.alloc_for(c);
+        for (int v = 0; v < nv && stt == MVD_OK; ++v) stt = compound_vjp(c, v, Kb + c->koff[v], Pb, sc, st);
+        cudaStreamSynchronize(st);
+        sc.release();
         if (stt != MVD_OK) break;
         // PSF normalisation Pn = p / sum(p), on the host in FP64
         std::vector<float> pb(c->ktotal), pn(c->ktotal);

@@ -38,6 +38,8 @@ enum KernelClass {
     KC_DD_Z_MUL,
     KC_DD_X_RATIO,
     KC_SETUP,
+    KC_DIRECT_CONV,  // plain direct convolutions (adjoint)
+    KC_KERNEL_GRAD,  // kernel-gradient correlations (adjoint)
     KC_COUNT
 };
 void prof_begin(int cls, cudaStream_t st);
@@ -104,6 +106,9 @@ mvd_status dd_y(const FftGeom& g, cdd* S2, int inverse, cudaStream_t st);
 mvd_status dd_z_mul(const FftGeom& g, cdd* S2, const cdd* K2, cudaStream_t st);
 mvd_status dd_z_forward_scaled(const FftGeom& g, cdd* S2, double scale, cudaStream_t st);
 mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cudaStream_t st);
+// double-float spectrum -> real volume (x inverse, rounded to FP32); X of 32..1024, a power of two
+mvd_status dd_x_inverse_real(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st);
+bool dd_fast_x(const FftGeom& g);
 // update pass reading the double-float spectrum (rounded to FP32)
 mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st);
 

@@ -109,7 +109,7 @@ mvd_status launch_ty(const DArgs& a, size_t sm, cudaStream_t st, const char* nam
     cudaError_t e = cudaFuncSetAttribute(k_direct<MODE, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_status(e, name);
     dim3 grid((a.X + TX - 1) / TX, (a.Y + TY - 1) / TY, (a.Z + TZ - 1) / TZ);
-    const int cls = MODE == 0 ? KC_DIRECT_RATIO : MODE == 1 ? KC_DIRECT_UPDATE : KC_SETUP;
+    const int cls = MODE == 0 ? KC_DIRECT_RATIO : MODE == 1 ? KC_DIRECT_UPDATE : KC_DIRECT_CONV;
     prof_begin(cls, st);
     k_direct<MODE, TY><<<grid, TX * TY, sm, st>>>(a);
     prof_end(cls, st);

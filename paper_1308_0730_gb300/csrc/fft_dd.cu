@@ -52,6 +52,12 @@ __global__ void __launch_bounds__(kDdThreads) k_ddf_x_forward(DdXFast a) {
 }
 
 template <int L>
+__global__ void __launch_bounds__(kDdThreads) k_ddf_x_inverse(DdXFast a) {
+    extern __shared__ cdd smd[];
+    ddf_x_inverse_tile<L, false>(a, blockIdx.x, smd);
+}
+
+template <int L>
 __global__ void __launch_bounds__(kDdThreads) k_ddf_x_ratio(DdXFast a) {
     extern __shared__ cdd smd[];
     ddf_x_ratio_tile<L, false>(a, blockIdx.x, smd);
@@ -120,6 +126,25 @@ mvd_status dd_forward_real(const FftGeom& g, const float* src, cdd* S2, cudaStre
     a.src = src;
     a.S2 = S2;
     return launch(k_dd_x_forward, a, dd_x_tiles(g.X, g.YZ), dd_x_smem(g.X), st, "dd x forward", KC_DD_X_FORWARD);
+}
+
+bool dd_fast_x(const FftGeom& g) { return g.fast && dd_fast_length(g.X); }
+
+mvd_status dd_x_inverse_real(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st) {
+    if (!(g.fast && dd_fast_length(g.X))) {
+        set_error("dd x inverse: length %d has no register-resident double-float transform", g.X);
+        return MVD_ERR_UNSUPPORTED;
+    }
+    mvd_status rc = MVD_ERR_UNSUPPORTED;
+    DdXFast a = ddf_args(g);
+    a.S2 = const_cast<cdd*>(S2);
+    a.dst = dst;
+    with_dd_len(g.X, [&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        rc = launch_raw(k_ddf_x_inverse<L>, gen_div_up(g.YZ, 2 * ddf_pairs(L)), kDdThreads, ddf_x_smem(L), st,
+                        "dd x inverse (fast)", KC_DD_X_RATIO, a);
+    });
+    return rc;
 }
 
 mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cudaStream_t st) {

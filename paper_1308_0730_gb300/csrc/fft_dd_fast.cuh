@@ -227,6 +227,7 @@ struct DdXFast {
     float eps;
     const cdd* tw2;
     FftPlan plan;      // FP32 plan of X (radices + FP32 twiddles) for the r - 1 transform
+    float* dst;        // real rows written by the plain inverse
 };
 
 // unpack the packed forward double-float spectra (natural order in registers
@@ -275,23 +276,19 @@ __device__ __forceinline__ void ddf_x_forward_tile(const DdXFast& a, long tile, 
     ddf_store_halves<L>(a, v, sm, p, t, rho0, nrows);
 }
 
-// double-float spectrum -> inverse x -> b -> r - 1 = phi / max(b, eps) - 1
-// -> FP32 forward x (shared-memory Stockham) -> back into S2 as double-float
+// gather the half spectra of rows rho0 + p (A) and rho0 + P + p (B) of a
+// tile and form the full spectrum of the complex line A + iB in v
 template <int L, bool CO>
-__device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cdd* sm) {
+__device__ __forceinline__ void ddf_gather_pair(const DdXFast& a, long rho0, int nrows, int p, int t, cdd* sm,
+                                                cdd (&v)[kE8]) {
     constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L), XH = L / 2 + 1;
-    const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
-    const long rho0 = tile * 2 * P;
-    const int nrows = (int)min((long)2 * P, a.YZ - rho0);
-    const bool oka = p < nrows, okb = P + p < nrows;
-    // gather both half spectra: rows < P -> line p (A), rows >= P -> line P + p (B)
+    // rows < P -> line p (A), rows >= P -> line P + p (B)
     for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
         const int k = idx / (2 * P), row = idx - k * 2 * P;
         const cdd val = row < nrows ? ld_cdd<CO>(a.S2 + (long)k * a.YZ + rho0 + row) : czero_dd();
         cdd_store(sm + row * LS + pad8(k), val);
     }
     __syncthreads();
-    cdd v[kE8];
 #pragma unroll
     for (int q = 0; q < kE8; ++q) {
         const int k = t + TPL * q;
@@ -300,6 +297,39 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
         v[q] = k <= L / 2 ? cdd{dd_sub(A.re, B.im), dd_add(A.im, B.re)}    // A + iB
                           : cdd{dd_add(A.re, B.im), dd_sub(B.re, A.im)};   // conj(A) + i conj(B)
     }
+}
+
+// double-float spectrum -> inverse x -> real rows (rounded to FP32) in dst
+template <int L, bool CO>
+__device__ __forceinline__ void ddf_x_inverse_tile(const DdXFast& a, long tile, cdd* sm) {
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L);
+    const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
+    const long rho0 = tile * 2 * P;
+    const int nrows = (int)min((long)2 * P, a.YZ - rho0);
+    cdd v[kE8];
+    ddf_gather_pair<L, CO>(a, rho0, nrows, p, t, sm, v);
+    __syncthreads();
+    LineFFTDD<L, +1, true>::run(v, sm + p * LS, t, a.tw2);
+    const long ra = (rho0 + p) * L, rb = (rho0 + P + p) * L;
+#pragma unroll
+    for (int q = 0; q < kE8; ++q) {
+        const int n = t + TPL * q;
+        if (p < nrows) a.dst[ra + n] = v[q].re.hi + v[q].re.lo;
+        if (P + p < nrows) a.dst[rb + n] = v[q].im.hi + v[q].im.lo;
+    }
+}
+
+// double-float spectrum -> inverse x -> b -> r - 1 = phi / max(b, eps) - 1
+// -> FP32 forward x -> back into S2 as double-float
+template <int L, bool CO>
+__device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cdd* sm) {
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L), XH = L / 2 + 1;
+    const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
+    const long rho0 = tile * 2 * P;
+    const int nrows = (int)min((long)2 * P, a.YZ - rho0);
+    const bool oka = p < nrows, okb = P + p < nrows;
+    cdd v[kE8];
+    ddf_gather_pair<L, CO>(a, rho0, nrows, p, t, sm, v);
     // the observed rows, fetched now to overlap the inverse transform
     float2 w[kE8];
     const long ra = (rho0 + p) * L, rb = (rho0 + P + p) * L;

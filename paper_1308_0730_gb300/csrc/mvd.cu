@@ -57,7 +57,8 @@ thread_local int t_open_cls = -1;
 thread_local cudaEvent_t t_open_ev = nullptr;
 const char* kClassNames[KC_COUNT] = {"x_forward", "y",        "z_mul",        "x_ratio",
                                      "x_update",  "direct_ratio", "direct_update", "dd_x_forward",
-                                     "dd_y",      "dd_z_mul", "dd_x_ratio",   "setup"};
+                                     "dd_y",      "dd_z_mul", "dd_x_ratio",   "setup",
+                                     "direct_conv", "kernel_grad"};
 
 cudaEvent_t next_event() {
     std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -6,6 +6,7 @@
 // (P_v^* * P_w * P_w^*) is linear convolution of those small functions. The
 // compound kernel of view v is zero outside P_v^*'s box, so every factor is
 // evaluated on that box only.
+#include "box_sum.cuh"
 #include "common.cuh"
 
 namespace mvd {
@@ -31,35 +32,6 @@ __device__ __forceinline__ void offset_of(const Box& b, int i, int& dx, int& dy,
     const int r = i / b.kx;
     dy = r % b.ky - b.hy();
     dz = r / b.ky - b.hz();
-}
-
-// Sum over the box [xlo,xhi] x [ylo,yhi] x [zlo,zhi] of the terms that
-// f(ex, ey, ez, acc) adds to acc (one FMA each), by one
-// warp: lanes stride over the flattened (ey, ex) plane (stepped incrementally,
-// no division in the loop), z runs serially; the lanes' partial sums are
-// combined with shuffles. Every lane returns the total.
-template <typename F>
-__device__ __forceinline__ float warp_box_sum(int xlo, int xhi, int ylo, int yhi, int zlo, int zhi, F&& f) {
-    const int lane = threadIdx.x & 31;
-    const int nx = xhi - xlo + 1, ny = yhi - ylo + 1;
-    float s = 0.f;
-    if (nx > 0 && ny > 0) {
-        const int n2 = nx * ny;
-        for (int ez = zlo; ez <= zhi; ++ez) {
-            int ey = ylo + lane / nx, ex = xlo + lane % nx;
-            for (int i = lane; i < n2; i += 32) {
-                s = f(ex, ey, ez, s);
-                ex += 32;
-                while (ex > xhi) {
-                    ex -= nx;
-                    ++ey;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
 }
 
 // Q(d) = sum_e P(e) P(e - d)   (P * P^*), on the box of size 2K-1; one warp per d

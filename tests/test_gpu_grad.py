@@ -62,9 +62,10 @@ def test_unrolled_forward_equals_iterate(env, small, path):
     assert np.array_equal(psi, want)
 
 
+@pytest.mark.parametrize("path", ["direct", "fft"])
 @pytest.mark.parametrize("variant", ["efficient", "opt1", "opt2", "plain"])
-def test_adjoint_matches_oracle_gradient(env, small, variant):
-    loss, psi, gv, gp = _gpu_run(env, small, small.psfs, small.n_iter, variant)
+def test_adjoint_matches_oracle_gradient(env, small, variant, path):
+    loss, psi, gv, gp = _gpu_run(env, small, small.psfs, small.n_iter, variant, path)
     oloss, ogv, ogp, opsi = oracle.unrolled_grad(small.views, small.psfs, small.n_iter, small.truth, variant)
     assert abs(loss - oloss) <= 1e-4 * oloss
     err_v = _rel(np.stack(gv), np.stack(ogv))
@@ -95,7 +96,7 @@ def test_backward_needs_a_forward_run(env, small):
         assert e.value.status == mvd.MVD_ERR_STATE
 
 
-def _sigma_chain(env, w, sigmas, n_iter):
+def _sigma_chain(env, w, sigmas, n_iter, path="auto"):
     """Full calibration chain on the GPU: sigma -> Gaussian PSFs -> K iterations -> MSE; returns dL/dsigma."""
     torch, _, ag = env
     box, angles = w.meta["box"], w.meta["angles"]
@@ -104,14 +105,15 @@ def _sigma_chain(env, w, sigmas, n_iter):
     sig = [torch.tensor(s, dtype=torch.float64, requires_grad=True) for s in sigmas]
     psfs = [ag.gaussian_psf(s, rotated_box(box, a), a, "z") for s, a in zip(sig, angles)]
     views = torch.from_numpy(np.stack(w.views)).cuda()
-    psi = ag.unrolled_deconvolve(views, psfs, n_iter)
+    psi = ag.unrolled_deconvolve(views, psfs, n_iter, path=path)
     truth = torch.from_numpy(w.truth).cuda()
     loss = torch.mean((psi.double() - truth.double()) ** 2)
     loss.backward()
     return float(loss.detach()), np.array([s.grad.numpy() for s in sig])
 
 
-def test_sigma_gradient_matches_finite_differences_24cubed(env):
+@pytest.mark.parametrize("path", ["direct", "fft"])
+def test_sigma_gradient_matches_finite_differences_24cubed(env, path):
     """The 24^3 copy of the calibration workload: FP64 central differences (step 1e-4) of the oracle run."""
     w = synth.config5_crop()
     sig0 = config5_sigmas(w.n_views)
@@ -132,7 +134,7 @@ def test_sigma_gradient_matches_finite_differences_24cubed(env):
             sp[v][k] += h
             sm[v][k] -= h
             fd[v, k] = (oracle_loss(sp) - oracle_loss(sm)) / (2 * h)
-    loss, g = _sigma_chain(env, w, sig0, w.n_iter)
+    loss, g = _sigma_chain(env, w, sig0, w.n_iter, path)
     assert abs(loss - oracle_loss(sig0)) <= 1e-4 * loss
     err = _rel(g, fd)
     assert err < GRAD_TOL, f"sigma gradient vs finite differences: {err:.3e}\n{g}\n{fd}"
@@ -152,13 +154,13 @@ def test_full_size_gradients_match_stored_oracle(env):
     w = synth.config5()
     sig0 = config5_sigmas(w.n_views)
     assert mg.input_digest(w, mg.model_psfs(w, sig0)) == ref["digest"], "inputs differ from the stored run"
-    loss, g = _sigma_chain(env, w, sig0, w.n_iter)
+    loss, g = _sigma_chain(env, w, sig0, w.n_iter, "fft")
     assert abs(loss - ref["loss"]) <= 1e-4 * ref["loss"]
     assert _rel(g, ref["dsigma_fd"]) < GRAD_TOL, (g, ref["dsigma_fd"])
     assert _rel(g, ref["dsigma_adjoint"]) < GRAD_TOL, (g, ref["dsigma_adjoint"])
     psfs = [mvd.mvd_gaussian_psf(s[0], s[1], synth.workloads.rotated_box(w.meta["box"], a), a, "z")
             for s, a in zip(sig0, w.meta["angles"])]
-    _, _, gv, gp = _gpu_run(env, w, psfs, w.n_iter)
+    _, _, gv, gp = _gpu_run(env, w, psfs, w.n_iter, path="fft")
     for v in range(w.n_views):
         idx, val = ref["dview"][v]
         e = np.abs(gv[v].ravel()[idx] - val).max() / ref["max_abs_dview"][v]
