@@ -137,9 +137,12 @@ mvd_status direct_conv(const int dims[3], const float* in, const float* k, const
                        float* out, cudaStream_t st);
 
 // Compound-kernel precompute and helpers.
-mvd_status build_compound(int n_views, const float* d_psf, const long* koff_h, const int* kd_h,
-                          int v, int variant, float* d_out, float* d_tmp, double* d_red,
-                          cudaStream_t st);
+// compound kernel of view v into d_out; for MVD_EFFICIENT d_q holds Q_w = P_w * P_w^*
+// of every view w (autocorr_all) at stride qstride
+mvd_status build_compound(int n_views, const float* d_psf, const long* koff_h, const int* kd_h, int v,
+                          int variant, float* d_out, const float* d_q, long qstride, cudaStream_t st);
+mvd_status autocorr_all(int n_views, const float* d_psf, const long* koff_h, const int* kd_h, float* d_q,
+                        long qstride, cudaStream_t st);
 mvd_status normalize_kernel(float* d_k, int n, int* d_bad, cudaStream_t st);
 mvd_status mirror_kernel(const float* k, const int kd[3], float* out, cudaStream_t st);
 mvd_status autocorr_kernel(const float* P, const int kd[3], float* Q, cudaStream_t st);  // Q box = 2K-1

@@ -660,12 +660,14 @@ mvd_status mvd_precompute_kernels(mvd_ctx* c, int variant) {
         const int* k = &c->kd[3 * v];
         qmax = std::max(qmax, (size_t)(2 * k[0] - 1) * (2 * k[1] - 1) * (2 * k[2] - 1));
     }
-    MVD_TRY(dev_alloc(&c->d_ktmp, qmax, "precompute scratch"));
+    MVD_TRY(dev_alloc(&c->d_ktmp, qmax * (size_t)c->nv, "precompute scratch"));
+    if (variant == MVD_EFFICIENT)
+        MVD_TRY(autocorr_all(c->nv, c->d_psf, c->koff.data(), c->kd.data(), c->d_ktmp, (long)qmax, c->stream));
     MVD_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
     for (int v = 0; v < c->nv; ++v) {
         float* dst = c->d_comp + c->koff[v];
         MVD_TRY(build_compound(c->nv, c->d_psf, c->koff.data(), c->kd.data(), v, variant, dst, c->d_ktmp,
-                               c->d_red, c->stream));
+                               (long)qmax, c->stream));
         const int* k = &c->kd[3 * v];
         MVD_TRY(normalize_kernel(dst, k[0] * k[1] * k[2], c->d_flag, c->stream));
     }

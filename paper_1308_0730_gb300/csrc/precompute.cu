@@ -155,9 +155,14 @@ inline int grid_stride_blocks(long n) {
 
 }  // namespace
 
+mvd_status autocorr_all(int n_views, const float* d_psf, const long* koff, const int* kd, float* d_q, long qstride,
+                        cudaStream_t st) {
+    for (int w = 0; w < n_views; ++w) MVD_TRY(autocorr_kernel(d_psf + koff[w], kd + 3 * w, d_q + (size_t)w * qstride, st));
+    return MVD_OK;
+}
+
 mvd_status build_compound(int n_views, const float* d_psf, const long* koff, const int* kd, int v,
-                          int variant, float* d_out, float* d_tmp, double* /*d_red*/,
-                          cudaStream_t st) {
+                          int variant, float* d_out, const float* d_q, long qstride, cudaStream_t st) {
     const Box bv = box_of(kd + 3 * v);
     const float* Pv = d_psf + koff[v];
     k_mirror<<<blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, d_out);
@@ -168,12 +173,10 @@ mvd_status build_compound(int n_views, const float* d_psf, const long* koff, con
             if (w == v) continue;
             const Box bw = box_of(kd + 3 * w);
             const float* Pw = d_psf + koff[w];
-            if (variant == MVD_EFFICIENT) {
+            if (variant == MVD_EFFICIENT) {  // Q_w = P_w * P_w^*, computed once per view by autocorr_all
                 const Box bq{2 * bw.kx - 1, 2 * bw.ky - 1, 2 * bw.kz - 1};
-                k_autocorr<<<warp_blocks_for((long)bq.kx * bq.ky * bq.kz), kThreads, 0, st>>>(Pw, bw, d_tmp, bq);
-                count_launch();
-                MVD_TRY(check_launch("compound autocorrelation"));
-                k_mul_conv<<<warp_blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, d_tmp, bq, d_out);
+                k_mul_conv<<<warp_blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, d_q + (size_t)w * qstride,
+                                                                                        bq, d_out);
             } else if (variant == MVD_OPT1) {
                 k_mul_conv<<<warp_blocks_for(bv.kx * bv.ky * bv.kz), kThreads, 0, st>>>(Pv, bv, Pw, bw, d_out);
             } else {
