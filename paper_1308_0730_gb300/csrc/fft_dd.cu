@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kDdThreads) k_ddf_x_inverse(DdXFast a) {
 }
 
 template <int L>
-__global__ void __launch_bounds__(kDdThreads) k_ddf_x_ratio(DdXFast a) {
+__global__ void __launch_bounds__(kDdThreads, 4) k_ddf_x_ratio(DdXFast a) {
     extern __shared__ cdd smd[];
     ddf_x_ratio_tile<L, false>(a, blockIdx.x, smd);
 }

@@ -155,8 +155,15 @@ __host__ __device__ constexpr int ddf_y_lines(int L) { return kDdThreads / (L / 
 __host__ __device__ constexpr int ddf_z_cols(int L) {
     return (kDdThreads / (L / kE8)) >= 4 ? kDdThreads / (L / kE8) : 4;
 }
+// half-spectrum rows (XH = L/2 + 1 padded values) of the x-pass gather
+__host__ __device__ constexpr int half_stride8(int L) { return L / 2 + L / 16 + 1; }
+// x passes: the 2P gathered half-spectrum rows, or the P transformed lines
+// (the two phases are separated by a barrier and share the buffer)
 __host__ __device__ constexpr size_t ddf_x_smem(int L) {
-    return (size_t)2 * ddf_pairs(L) * line_stride8(L) * sizeof(cdd);
+    return (size_t)(2 * ddf_pairs(L) * half_stride8(L) > ddf_pairs(L) * line_stride8(L)
+                        ? 2 * ddf_pairs(L) * half_stride8(L)
+                        : ddf_pairs(L) * line_stride8(L)) *
+           sizeof(cdd);
 }
 __host__ __device__ constexpr size_t ddf_y_smem(int L) { return (size_t)ddf_y_lines(L) * line_stride8(L) * sizeof(cdd); }
 __host__ __device__ constexpr size_t ddf_z_smem(int L) { return (size_t)ddf_z_cols(L) * line_stride8(L) * sizeof(cdd); }
@@ -281,19 +288,19 @@ __device__ __forceinline__ void ddf_x_forward_tile(const DdXFast& a, long tile, 
 template <int L, bool CO>
 __device__ __forceinline__ void ddf_gather_pair(const DdXFast& a, long rho0, int nrows, int p, int t, cdd* sm,
                                                 cdd (&v)[kE8]) {
-    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L), XH = L / 2 + 1;
-    // rows < P -> line p (A), rows >= P -> line P + p (B)
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), HS = half_stride8(L), XH = L / 2 + 1;
+    // rows < P -> row p (A), rows >= P -> row P + p (B), at stride HS
     for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
         const int k = idx / (2 * P), row = idx - k * 2 * P;
         const cdd val = row < nrows ? ld_cdd<CO>(a.S2 + (long)k * a.YZ + rho0 + row) : czero_dd();
-        cdd_store(sm + row * LS + pad8(k), val);
+        cdd_store(sm + row * HS + pad8(k), val);
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kE8; ++q) {
         const int k = t + TPL * q;
         const int kk = k <= L / 2 ? k : L - k;
-        const cdd A = cdd_load(sm + p * LS + pad8(kk)), B = cdd_load(sm + (P + p) * LS + pad8(kk));
+        const cdd A = cdd_load(sm + p * HS + pad8(kk)), B = cdd_load(sm + (P + p) * HS + pad8(kk));
         v[q] = k <= L / 2 ? cdd{dd_sub(A.re, B.im), dd_add(A.im, B.re)}    // A + iB
                           : cdd{dd_add(A.re, B.im), dd_sub(B.re, A.im)};   // conj(A) + i conj(B)
     }
