@@ -329,6 +329,12 @@ def run_gpu(args):
     ev5.synchronize()
     ms_fast = ev4.elapsed_time(ev5)
     psi_fast = fast.result()
+    # per-kernel events of the FP32 passes (HBM-bound): one more step, launched one by one
+    mvd.mvd_profile_enable(True)
+    fast_step()
+    fast.synchronize()
+    prof_fast = mvd.mvd_profile_read()
+    mvd.mvd_profile_enable(False)
     fast.close()
 
     # --- end to end through the public API from pinned host buffers ---
@@ -387,6 +393,20 @@ def run_gpu(args):
             roofline = {"bound": "hbm", "kernel": dom, "achieved": per_kernel[dom]["GBps"], "peak": peak,
                         "unit": "GB/s", "frac": per_kernel[dom]["GBps"] / peak, "traffic": traffic,
                         "peak_source": peak_kind}
+        kbf = _kernel_bytes(X, Y, Z, precise=False)
+        tot_fast = sum(t for (_, t) in prof_fast.values())
+        fast_kernels = {}
+        for name, (n, tot) in prof_fast.items():
+            if n and name in kbf:
+                gbps = kbf[name] / (tot / n * 1e-3) / 1e9
+                fast_kernels[name] = {"launches": n, "avg_us": 1e3 * tot / n, "share": tot / max(1e-9, tot_fast),
+                                      "GBps": gbps, "hbm_frac": gbps / peak}
+        fast_roof = None
+        if fast_kernels:
+            fd = max(fast_kernels, key=lambda k: prof_fast[k][1])
+            fast_roof = {"bound": "hbm", "kernel": fd, "achieved": fast_kernels[fd]["GBps"], "peak": peak,
+                         "unit": "GB/s", "frac": fast_kernels[fd]["hbm_frac"], "traffic": None,
+                         "peak_source": peak_kind}
         value = _job_value(ws, units_per_step * args.steps, t_max * 1e-3)
         # about 10 s of host work: view updates of the same workload, one after another
         cpu_times, cores = _cpu_baseline(w, 1e-4 * float(np.mean([v.mean(dtype=np.float64) for v in w.views])),
@@ -412,6 +432,7 @@ def run_gpu(args):
             "precision": "double-float (pairs of FP32) for the forward blur and the back-projection's y and z passes; FP32 x passes of the back-projection",
             "fast_fp32": {"value": ws * units_per_step * args.steps / (ms_fast * 1e-3) / 1e9, "unit": UNIT,
                           "ms_per_step": ms_fast / args.steps,
+                          "kernels": fast_kernels, "roofline": fast_roof,
                           "max_rel_diff_vs_precise": float(np.max(np.abs(psi_fast.astype(np.float64) - psi_dev)
                                                                   / np.maximum(np.abs(psi_dev.astype(np.float64)),
                                                                                1e-3 * np.abs(psi_dev).max())))},

@@ -201,33 +201,33 @@ struct DftDD<5, S> {
 
 // one Stockham butterfly and the multi-line driver, as in fft.cuh
 template <int R, int S>
-__device__ __forceinline__ void stockham_bfly_dd(const cdd* __restrict__ A, cdd* __restrict__ B, int j, int Ns,
-                                                 int L, const cdd* __restrict__ tw) {
-    const int nb = L / R;
-    const int k = j % Ns;
+__device__ __forceinline__ void stockham_bfly_dd(const cdd* __restrict__ A, cdd* __restrict__ B, int j,
+                                                 const StageIdx& si, const cdd* __restrict__ tw) {
+    const int jq = small_div(j, si.inv_ns);
+    const int k = j - jq * si.Ns;
     cdd v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = A[j + r * nb];
-    if (Ns > 1) {
-        const int step = k * (L / (Ns * R));
+    for (int r = 0; r < R; ++r) v[r] = A[j + r * si.nb];
+    if (si.Ns > 1) {
+        const int step = k * si.lstep;
 #pragma unroll
         for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle_dd<S>(tw, r * step));
     }
     DftDD<R, S>::run(v);
-    const int d = (j / Ns) * Ns * R + k;
+    const int d = jq * si.Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) B[d + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) B[d + r * si.Ns] = v[r];
 }
 
 template <int R, int S>
 __device__ __forceinline__ void stockham_stage_dd(const cdd* __restrict__ A, cdd* __restrict__ B, int nlines, int ls,
                                                   int L, int Ns, const cdd* __restrict__ tw) {
-    const int nb = L / R;
-    const int total = nlines * nb;
+    const StageIdx si(L, R, Ns);
+    const int total = nlines * si.nb;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int line = t / nb;
-        const int j = t - line * nb;
-        stockham_bfly_dd<R, S>(A + line * ls, B + line * ls, j, Ns, L, tw);
+        const int line = small_div(t, si.inv_nb);
+        const int j = t - line * si.nb;
+        stockham_bfly_dd<R, S>(A + line * ls, B + line * ls, j, si, tw);
     }
 }
 

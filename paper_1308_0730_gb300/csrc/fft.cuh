@@ -129,23 +129,39 @@ struct Dft<5, S> {
 // ---------------------------------------------------------------------------
 // one Stockham butterfly (see the file header)
 // ---------------------------------------------------------------------------
+
+// floor(n / d) for 0 <= n and n + d < 2^22, from inv = the FP32 reciprocal of d
+// (correctly rounded): (n + 1/2) / d lies at least 1/(2d) from an integer and
+// the two roundings move it by less than (n/d + 1) 2^-23, so the truncation is
+// exact. Replaces the integer divisions of the butterfly indexing.
+__device__ __forceinline__ int small_div(int n, float inv) { return __float2int_rz(((float)n + 0.5f) * inv); }
+
+// Per-stage constants of the Stockham indexing: nb = L / R butterflies per
+// line, Ns combined so far, lstep = L / (Ns R) the twiddle index stride.
+struct StageIdx {
+    int nb, Ns, lstep;
+    float inv_nb, inv_ns;
+    __device__ __forceinline__ StageIdx(int L, int R, int ns)
+        : nb(L / R), Ns(ns), lstep(L / (ns * R)), inv_nb(1.0f / (float)(L / R)), inv_ns(1.0f / (float)ns) {}
+};
+
 template <int R, int S>
 __device__ __forceinline__ void stockham_bfly(const float2* __restrict__ A, float2* __restrict__ B, int j,
-                                              int Ns, int L, const float2* __restrict__ tw) {
-    const int nb = L / R;
-    const int k = j % Ns;
+                                              const StageIdx& si, const float2* __restrict__ tw) {
+    const int jq = small_div(j, si.inv_ns);
+    const int k = j - jq * si.Ns;
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = A[j + r * nb];
-    if (Ns > 1) {
-        const int step = k * (L / (Ns * R));
+    for (int r = 0; r < R; ++r) v[r] = A[j + r * si.nb];
+    if (si.Ns > 1) {
+        const int step = k * si.lstep;
 #pragma unroll
         for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<S>(tw, r * step));
     }
     Dft<R, S>::run(v);
-    const int d = (j / Ns) * Ns * R + k;
+    const int d = jq * si.Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) B[d + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) B[d + r * si.Ns] = v[r];
 }
 
 // All butterflies of one stage (radix R, Ns combined so far) over `nlines`
@@ -153,12 +169,12 @@ __device__ __forceinline__ void stockham_bfly(const float2* __restrict__ A, floa
 template <int R, int S>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ A, float2* __restrict__ B, int nlines,
                                                int ls, int L, int Ns, const float2* __restrict__ tw) {
-    const int nb = L / R;
-    const int total = nlines * nb;
+    const StageIdx si(L, R, Ns);
+    const int total = nlines * si.nb;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int line = t / nb;
-        const int j = t - line * nb;
-        stockham_bfly<R, S>(A + line * ls, B + line * ls, j, Ns, L, tw);
+        const int line = small_div(t, si.inv_nb);
+        const int j = t - line * si.nb;
+        stockham_bfly<R, S>(A + line * ls, B + line * ls, j, si, tw);
     }
 }
 
