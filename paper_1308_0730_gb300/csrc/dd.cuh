@@ -231,6 +231,88 @@ __device__ __forceinline__ void stockham_stage_dd(const cdd* __restrict__ A, cdd
     }
 }
 
+// A stage whose input comes straight from global memory (line l at gin + l*L,
+// lines >= nl read as zero; L2-only loads when CO) and/or whose output goes
+// straight to global memory (gout + l*L, lines >= nl skipped); the other side
+// is the shared-memory line buffer (stride ls).
+template <int R, int S, bool GIN, bool GOUT, bool CO>
+__device__ __forceinline__ void stockham_stage_dd_io(const cdd* __restrict__ A, cdd* __restrict__ B,
+                                                     const cdd* gin, cdd* gout, int nlines, int nl, int ls, int L,
+                                                     int Ns, const cdd* __restrict__ tw) {
+    const StageIdx si(L, R, Ns);
+    const int total = nlines * si.nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int line = small_div(t, si.inv_nb);
+        const int j = t - line * si.nb;
+        const int jq = small_div(j, si.inv_ns);
+        const int k = j - jq * si.Ns;
+        const bool ok = line < nl;
+        cdd v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (GIN) {
+                const cdd* q = gin + (long)line * L + j + r * si.nb;
+                v[r] = ok ? (CO ? cdd_load_cg(q) : cdd_load(q)) : czero_dd();
+            } else {
+                v[r] = A[line * ls + j + r * si.nb];
+            }
+        }
+        if (si.Ns > 1) {
+            const int step = k * si.lstep;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle_dd<S>(tw, r * step));
+        }
+        DftDD<R, S>::run(v);
+        const int d = jq * si.Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (GOUT) {
+                if (ok) cdd_store(gout + (long)line * L + d + r * si.Ns, v[r]);
+            } else {
+                B[line * ls + d + r * si.Ns] = v[r];
+            }
+        }
+    }
+}
+
+template <int S, bool GIN, bool GOUT, bool CO>
+__device__ __forceinline__ void stage_dd_io(int R, const cdd* A, cdd* B, const cdd* gin, cdd* gout, int nlines, int nl,
+                                            int ls, int L, int Ns, const cdd* tw) {
+    switch (R) {
+        case 8: stockham_stage_dd_io<8, S, GIN, GOUT, CO>(A, B, gin, gout, nlines, nl, ls, L, Ns, tw); break;
+        case 4: stockham_stage_dd_io<4, S, GIN, GOUT, CO>(A, B, gin, gout, nlines, nl, ls, L, Ns, tw); break;
+        case 2: stockham_stage_dd_io<2, S, GIN, GOUT, CO>(A, B, gin, gout, nlines, nl, ls, L, Ns, tw); break;
+        case 3: stockham_stage_dd_io<3, S, GIN, GOUT, CO>(A, B, gin, gout, nlines, nl, ls, L, Ns, tw); break;
+        default: stockham_stage_dd_io<5, S, GIN, GOUT, CO>(A, B, gin, gout, nlines, nl, ls, L, Ns, tw); break;
+    }
+}
+
+// Transforms nl (<= nlines) contiguous lines of length p.L from global memory
+// (g + l*L) in place: the first stage reads global memory, the last writes it,
+// the stages between go through the shared-memory buffers A/B (nlines lines at
+// stride ls). Needs p.nst >= 2 (a single stage would read and write the same
+// global elements in one pass). Starts and ends with all threads synchronised
+// with respect to shared memory.
+template <int S, bool CO>
+__device__ void fft_lines_dd_global(cdd* g, cdd* A, cdd* B, int nlines, int nl, int ls, const FftPlan& p,
+                                    const cdd* tw) {
+    int Ns = 1;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.radix[s];
+        if (s == 0)
+            stage_dd_io<S, true, false, CO>(R, A, B, g, g, nlines, nl, ls, p.L, Ns, tw);
+        else if (s == p.nst - 1)
+            stage_dd_io<S, false, true, CO>(R, A, B, g, g, nlines, nl, ls, p.L, Ns, tw);
+        else
+            stage_dd_io<S, false, false, CO>(R, A, B, g, g, nlines, nl, ls, p.L, Ns, tw);
+        __syncthreads();
+        cdd* t = A;
+        A = B;
+        B = t;
+        Ns *= R;
+    }
+}
+
 // plan radices as FftPlan, twiddles from a double-float table of length L
 template <int S>
 __device__ cdd* fft_lines_dd(cdd* A, cdd* B, int nlines, int ls, const FftPlan& p, const cdd* tw) {

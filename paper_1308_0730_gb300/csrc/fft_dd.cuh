@@ -183,6 +183,10 @@ __device__ void dd_y_tile(const DdY& a, long tile, cdd* sm) {
     cdd* B = sm + a.P * a.ls;
     const long l0 = tile * a.P;
     const int nl = (int)min((long)a.P, a.nlines - l0);
+    if (a.plan.nst >= 2) {  // first stage from global memory, last stage to it
+        fft_lines_dd_global<S, CO>(a.S2 + l0 * a.L, A, B, a.P, nl, a.ls, a.plan, a.tw2);
+        return;
+    }
     for (int t = threadIdx.x; t < a.P * a.L; t += blockDim.x) {
         const int line = t / a.L, y = t - line * a.L;
         cdd v = czero_dd();
