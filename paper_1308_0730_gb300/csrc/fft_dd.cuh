@@ -34,7 +34,9 @@ __host__ __device__ inline long dd_y_tiles(int Y, int Xh, int Z) { return gen_di
 __host__ __device__ inline long dd_z_tiles(int Z, int Y, int Xh) { return (long)Xh * gen_div_up(Y, dd_z_cols(Z, Y)); }
 __host__ __device__ inline size_t dd_x_smem(int X) { return (size_t)2 * dd_x_pairs(X) * (X + 1) * sizeof(cdd); }
 __host__ __device__ inline size_t dd_y_smem(int Y) { return (size_t)2 * dd_y_lines(Y) * (Y + 1) * sizeof(cdd); }
-__host__ __device__ inline size_t dd_z_smem(int Z, int Y) { return (size_t)2 * dd_z_cols(Z, Y) * (Z + 1) * sizeof(cdd); }
+// z line stride: odd, so that 16-byte accesses of consecutive lines hit distinct banks
+__host__ __device__ inline int dd_z_ls(int Z) { return (Z + 1) | 1; }
+__host__ __device__ inline size_t dd_z_smem(int Z, int Y) { return (size_t)2 * dd_z_cols(Z, Y) * dd_z_ls(Z) * sizeof(cdd); }
 
 struct DdX {
     int X, Xh, P, ls;
@@ -184,7 +186,7 @@ __device__ void dd_y_tile(const DdY& a, long tile, cdd* sm) {
     const long l0 = tile * a.P;
     const int nl = (int)min((long)a.P, a.nlines - l0);
     if (a.plan.nst >= 2) {  // first stage from global memory, last stage to it
-        fft_lines_dd_global<S, CO>(a.S2 + l0 * a.L, A, B, a.P, nl, a.ls, a.plan, a.tw2);
+        fft_lines_dd_io<S, true, true, CO, false>(a.S2 + l0 * a.L, a.L, 1, A, B, a.P, nl, a.ls, a.plan, a.tw2);
         return;
     }
     for (int t = threadIdx.x; t < a.P * a.L; t += blockDim.x) {
@@ -217,7 +219,7 @@ __host__ __device__ inline DdZ dd_z_args(int Z, int Y, long YZ, const FftPlan& p
     a.Z = Z;
     a.Y = Y;
     a.Q = dd_z_cols(Z, Y);
-    a.ls = Z + 1;
+    a.ls = dd_z_ls(Z);
     a.ntiles_y = (int)gen_div_up(Y, a.Q);
     a.YZ = YZ;
     a.plan = plan;
@@ -237,6 +239,17 @@ __device__ void dd_z_tile(const DdZ& a, long tile, cdd* sm) {
     const int nq = min(a.Q, a.Y - y0);
     const long base = (long)kx * a.YZ + y0;
     const int n = a.Z * a.Q;
+    if (MUL && a.plan.nst >= 1) {  // columns: element z of column q at base + z*Y + q; threads run along q
+        cdd* F = fft_lines_dd_io<-1, true, false, CO, true>(a.S2 + base, 1, a.Y, A, B, a.Q, nq, a.ls, a.plan, a.tw2);
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int z = t / a.Q, q = t - z * a.Q;
+            if (q < nq) F[q * a.ls + z] = cmul(F[q * a.ls + z], cdd_load_nc(a.K2 + base + (long)z * a.Y + q));
+        }
+        __syncthreads();
+        fft_lines_dd_io<+1, false, true, CO, true>(a.S2 + base, 1, a.Y, F, F == A ? B : A, a.Q, nq, a.ls, a.plan,
+                                                   a.tw2);
+        return;
+    }
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const int z = t / a.Q, q = t - z * a.Q;
         cdd v = czero_dd();
