@@ -16,12 +16,14 @@
 // replays the iteration's view updates from its checkpoint with the same
 // engine as the forward (keeping the N estimates before the updates) and then
 // recomputes each update's intermediates (b, r, c) in the adjoint step, so
-// device memory is (iterations + views + 9) volumes.
+// device memory is (iterations + 1) checkpoints, N replayed estimates and a
+// few work volumes and kernel spectra.
 // K_bar flows back through the compound kernel (Eq. 222 / 230 / 240 and its
 // normalisation) to every PSF, P_bar through the PSF normalisation to the raw
 // PSF values; the gradient of the flat start psi0 = mean of the views is
-// spread over every view voxel. All volume work here uses the direct
-// (spatial) engine in FP32.
+// spread over every view voxel. Contexts on the FFT engine run the volume
+// work through the FFT passes (backward_fft); contexts on the direct engine
+// use direct convolutions and a tiled correlation.
 #include <cmath>
 #include <vector>
 
@@ -187,9 +189,6 @@ struct KBox {
     __device__ __forceinline__ int hy() const { return (ky - 1) / 2; }
     __device__ __forceinline__ int hz() const { return (kz - 1) / 2; }
     __device__ __forceinline__ int size() const { return kx * ky * kz; }
-    __device__ __forceinline__ bool in(int dx, int dy, int dz) const {
-        return dx >= -hx() && dx <= hx() && dy >= -hy() && dy <= hy() && dz >= -hz() && dz <= hz();
-    }
     __device__ __forceinline__ int index(int dx, int dy, int dz) const {
         return (dx + hx()) + kx * ((dy + hy()) + ky * (dz + hz()));
     }
