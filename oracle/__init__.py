@@ -18,6 +18,7 @@ from .oracle import (  # noqa: F401
     update,
     update_at,
     deconvolve,
+    deconvolve_combined,
     mean_views,
     num_threads,
     unrolled_grad,

@@ -269,6 +269,70 @@ double mvdo_deconvolve(int n_views, const double* const* views, const double* co
     return eps;
 }
 
+/* Combined (simultaneous) update of Eq. 50 / Eq. 220: every view's factor
+ *   c_v = (phi_v / max(psi * P_v, eps)) * K_v
+ * is computed from the same psi, then psi <- max(psi . prod_v c_v, eps). With
+ * root != 0 the product's |V|-th root is taken (the geometric mean of the
+ * factors, as in the convergence proof, Section "Proof of convergence").
+ * PSF normalisation, compound kernels, psi0 and eps as in mvdo_deconvolve.
+ * Returns the eps used, or -1 on error. */
+double mvdo_deconvolve_combined(int n_views, const double* const* views, const double* const* psfs,
+                                const int* pdims, const int dims[3], int variant, int n_iter, int root,
+                                double eps, int init, double* psi) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double psi0 = mvdo_mean_views(n_views, views, dims);
+    if (eps <= 0.0) eps = 1e-4 * psi0;
+    if (!init)
+        for (long i = 0; i < M; ++i) psi[i] = psi0;
+    double** pn = (double**)malloc(sizeof(double*) * n_views);
+    double** comp = (double**)malloc(sizeof(double*) * n_views);
+    int bad = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        double s = 0.0;
+        for (long i = 0; i < T; ++i) s += psfs[v][i];
+        pn[v] = (double*)malloc(sizeof(double) * T);
+        for (long i = 0; i < T; ++i) pn[v][i] = psfs[v][i] / s;
+    }
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        comp[v] = (double*)malloc(sizeof(double) * T);
+        if (mvdo_compound(n_views, (const double* const*)pn, pdims, v, variant, comp[v]) != 0) bad = 1;
+    }
+    double* b = (double*)malloc(sizeof(double) * M);
+    double* r = (double*)malloc(sizeof(double) * M);
+    double* c = (double*)malloc(sizeof(double) * M);
+    double* prod = (double*)malloc(sizeof(double) * M);
+    for (int it = 0; it < n_iter && !bad; ++it) {
+        for (long i = 0; i < M; ++i) prod[i] = 1.0;
+        for (int v = 0; v < n_views; ++v) {
+            const int* pd = pdims + 3 * v;
+            mvdo_conv(psi, dims, pn[v], pd, b);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) r[i] = views[v][i] / fmax(b[i], eps);
+            mvdo_conv(r, dims, comp[v], pd, c);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) prod[i] *= c[i];
+        }
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < M; ++i) {
+            const double f = root ? pow(prod[i], 1.0 / n_views) : prod[i];
+            psi[i] = fmax(psi[i] * f, eps);
+        }
+    }
+    for (int v = 0; v < n_views; ++v) {
+        free(comp[v]);
+        free(pn[v]);
+    }
+    free(comp);
+    free(pn);
+    free(b);
+    free(r);
+    free(c);
+    free(prod);
+    return bad ? -1.0 : eps;
+}
+
 /* One view update evaluated only at the listed voxels (flat indices):
  *   out[i] = max(psi(x_i) * c(x_i), eps), with c, r, b computed from the
  * definitions above on the neighbourhood each sample needs. */

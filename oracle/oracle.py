@@ -57,6 +57,10 @@ def _load():
                                             _I, ctypes.c_int, ctypes.c_int, _I, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_int, _D]
             lib.mvdo_deconvolve.restype = ctypes.c_double
+            lib.mvdo_deconvolve_combined.argtypes = [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D), _I, _I,
+                                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                     ctypes.c_int, _D]
+            lib.mvdo_deconvolve_combined.restype = ctypes.c_double
             lib.mvdo_update_at.argtypes = [_D, _D, _D, _I, _D, _I, _I, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_long), ctypes.c_int, _D]
             lib.mvdo_num_threads.restype = ctypes.c_int
@@ -183,6 +187,27 @@ def deconvolve(views, psfs, n_iter, variant="efficient", schedule=None, eps=0.0,
         slen = len(schedule)
     used = _load().mvdo_deconvolve(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), sched,
                                    slen, float(eps), init, _dptr(psi))
+    if used < 0:
+        raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
+    return psi, used
+
+
+def deconvolve_combined(views, psfs, n_iter, variant="efficient", root=True, eps=0.0, psi_init=None):
+    """Combined (simultaneous) update, Eq. 50 / Eq. 220: every view's factor from the same psi,
+    their product (or with ``root`` its |V|-th root, the geometric mean) applied at once.
+
+    Returns ``(psi, eps_used)``; ``eps <= 0`` selects ``1e-4 * psi0``.
+    """
+    var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    vs = [_f64(v) for v in views]
+    ps, parr, pd = _psf_arrays(psfs)
+    varr = (_D * len(vs))(*[_dptr(v) for v in vs])
+    if psi_init is None:
+        psi, init = np.empty_like(vs[0]), 0
+    else:
+        psi, init = _f64(psi_init).copy(), 1
+    used = _load().mvdo_deconvolve_combined(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter),
+                                            1 if root else 0, float(eps), init, _dptr(psi))
     if used < 0:
         raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
     return psi, used
