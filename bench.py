@@ -683,6 +683,50 @@ def run_grad(args):
     return 0
 
 
+def run_combined(args):
+    """The combined (simultaneous) update of Eq. 50 / Eq. 220 with the |V|-th root on the
+    256x256x128 four-view workload, 20 iterations, device-resident, precise mode."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1308_0730_gb300 import mvd
+
+    w = _workload(0)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dviews = [torch.from_numpy(v).cuda() for v in w.views]
+    stream.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft") as d:
+        for _ in range(args.warmup):
+            d.set_estimate(None)
+            d.iterate_combined(w.n_iter)
+        d.synchronize()
+        launches0 = mvd.mvd_launch_count()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                d.set_estimate(None)
+                d.iterate_combined(w.n_iter)
+            ev1.record(stream)
+            ev1.synchronize()
+        launches = (mvd.mvd_launch_count() - launches0) / args.steps
+    ms = ev0.elapsed_time(ev1) / args.steps
+    units = w.voxels * w.n_views * w.n_iter
+    X, Y, Z = w.dims
+    print(json.dumps({
+        "metric": METRIC, "value": units / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "volume": [X, Y, Z], "views": w.n_views, "iterations": w.n_iter,
+                   "update": "combined, geometric mean of the view factors", "variant": "efficient",
+                   "engine": "fft", "precision": "precise", "l2": "inputs larger than L2"},
+        "gpu_launches": launches, "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -691,6 +735,8 @@ def main():
     ap.add_argument("--impl", default="mvd", choices=["mvd", "reference"])
     ap.add_argument("--quick", action="store_true",
                     help="only the device-resident timing (no FP32 comparison, end-to-end or CPU legs)")
+    ap.add_argument("--combined", action="store_true",
+                    help="time the combined (simultaneous) update with the geometric mean instead")
     ap.add_argument("--grad", action="store_true",
                     help="time the PSF-calibration step (8 unrolled iterations, forward + adjoint) instead")
     ap.add_argument("--large", action="store_true",
@@ -706,6 +752,8 @@ def main():
         return run_large(args)
     if args.grad:
         return run_grad(args)
+    if args.combined:
+        return run_combined(args)
     return run_gpu(args)
 
 

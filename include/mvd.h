@@ -144,6 +144,18 @@ mvd_status mvd_set_estimate(mvd_ctx* ctx, const float* psi, int on_device);
  */
 mvd_status mvd_iterate(mvd_ctx* ctx, int n_iter, const int* schedule, int schedule_len);
 
+/*
+ * Runs n_iter iterations of the combined (simultaneous) update of Eq. 50 /
+ * Eq. 220: every view's factor c_v = (phi_v / max(psi * P_v, eps)) * P_v^comp
+ * is computed from the same psi, then
+ *   psi = max(psi . prod_v c_v, eps)               (root == 0, Eq. 50 as printed)
+ *   psi = max(psi . (prod_v c_v)^(1/N), eps)       (root != 0, the geometric
+ *        mean of the factors, as in the paper's convergence proof).
+ * Needs one more volume on the device (the product, allocated on first use).
+ * Enqueues work only; graph capture as in mvd_iterate.
+ */
+mvd_status mvd_iterate_combined(mvd_ctx* ctx, int n_iter, int root);
+
 /* Copies psi (X*Y*Z floats) to host memory `out`; n_elems must be >= X*Y*Z.
  * Synchronises the context's stream. */
 mvd_status mvd_result(mvd_ctx* ctx, float* out, size_t n_elems);

@@ -11,6 +11,7 @@ from .mvd import (  # noqa: F401
     mvd_precompute_kernels,
     mvd_set_estimate,
     mvd_iterate,
+    mvd_iterate_combined,
     mvd_result,
     mvd_result_device,
     mvd_synchronize,

@@ -257,7 +257,7 @@ __device__ void run_tile(const VolDesc& d, int pass, int view, long tile, float2
                 a.S2in = S2;
                 a.psi = d.psi;
                 a.eps = d.eps;
-                gen_x_inverse_tile<true, true>(a, tile, sm);
+                gen_x_inverse_tile<true, 1>(a, tile, sm);
             }
             break;
         }

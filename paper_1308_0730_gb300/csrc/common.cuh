@@ -99,6 +99,12 @@ mvd_status fft_z_forward_scaled(const FftGeom& g, float2* S, float scale, cudaSt
 mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
 mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st);
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
+// combined update: acc *= c, c the back-projected factor of the spectrum of (r - 1) * K (+ 1)
+mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st);
+mvd_status fft_x_accumulate_dd(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st);
+mvd_status fft_x_accumulate_generic(const FftGeom& g, const float2* S, const cdd* S2, float* acc, cudaStream_t st);
+mvd_status fft_x_accumulate_fast(const FftGeom& g, const float2* S, float* acc, cudaStream_t st);
+mvd_status fft_x_accumulate_dd_fast(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st);
 
 // double-float forward blur (fft_dd.cu): spectrum of complex double-float
 mvd_status dd_forward_real(const FftGeom& g, const float* src, cdd* S2, cudaStream_t st);
@@ -133,6 +139,9 @@ mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, con
 mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
                          float* psi, float eps, cudaStream_t st, int ty = 0);
 int direct_tile_heights(const int kd[3], int out[4]);  // tile heights that fit, largest first
+// prod *= r * k (the combined update's product of view factors)
+mvd_status direct_accumulate(const int dims[3], const float* r, const float* k, const int kd[3], float* prod,
+                             cudaStream_t st, int ty = 0);
 mvd_status direct_conv(const int dims[3], const float* in, const float* k, const int kd[3],
                        float* out, cudaStream_t st);
 
@@ -149,10 +158,14 @@ mvd_status autocorr_kernel(const float* P, const int kd[3], float* Q, cudaStream
 mvd_status direct_conv_add(const int dims[3], const float* in, const float* k, const int kd[3], float* out,
                            cudaStream_t st);
 mvd_status one_update(mvd_ctx* c, int v);
+// view v's pass from the current estimate: with prod == nullptr the
+// sequential update psi = max(psi . c_v, eps); else prod *= c_v
+mvd_status view_pass(mvd_ctx* c, int v, float* prod);
 mvd_status place_kernel(const int dims[3], const float* k, const int kd[3], float* vol,
                         cudaStream_t st);
 mvd_status view_stats(const float* views, long n, double* d_sum, int* d_bad, cudaStream_t st);
 mvd_status fill(float* p, long n, float v, cudaStream_t st);
+mvd_status apply_product(float* psi, const float* prod, long n, float e, float eps, cudaStream_t st);
 mvd_status check_positive(const float* p, long n, int* d_bad, cudaStream_t st);
 
 }  // namespace mvd
@@ -209,6 +222,7 @@ struct mvd_ctx {
     int variant = -1;
     int path_opt = MVD_PATH_AUTO;
     int direct_ty = 0;  // direct-engine tile height chosen by the autotuner (0 = default)
+    float* d_prod = nullptr;  // combined update: product of the view factors (M)
     int path = MVD_PATH_AUTO;
     float psi0 = 0.f, eps = 0.f;
 };

@@ -40,7 +40,7 @@ struct DArgs {
 };
 
 // MODE 0: out = phi / max(conv, eps); MODE 1: out = max(out . conv, eps); MODE 2: out = conv;
-// MODE 3: out += conv
+// MODE 3: out += conv; MODE 4: out *= conv (the combined update's product)
 template <int MODE, int TY>
 __global__ void __launch_bounds__(TX * TY) k_direct(DArgs a) {
     extern __shared__ float smem[];
@@ -99,8 +99,10 @@ __global__ void __launch_bounds__(TX * TY) k_direct(DArgs a) {
             a.out[g] = fmaxf(a.out[g] * acc[o], a.eps);
         else if (MODE == 2)
             a.out[g] = acc[o];
-        else
+        else if (MODE == 3)
             a.out[g] += acc[o];
+        else  // MODE 4: combined update, multiply this view's factor into the product
+            a.out[g] *= acc[o];
     }
 }
 
@@ -109,7 +111,7 @@ mvd_status launch_ty(const DArgs& a, size_t sm, cudaStream_t st, const char* nam
     cudaError_t e = cudaFuncSetAttribute(k_direct<MODE, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_status(e, name);
     dim3 grid((a.X + TX - 1) / TX, (a.Y + TY - 1) / TY, (a.Z + TZ - 1) / TZ);
-    const int cls = MODE == 0 ? KC_DIRECT_RATIO : MODE == 1 ? KC_DIRECT_UPDATE : KC_DIRECT_CONV;
+    const int cls = MODE == 0 ? KC_DIRECT_RATIO : (MODE == 1 || MODE == 4) ? KC_DIRECT_UPDATE : KC_DIRECT_CONV;
     prof_begin(cls, st);
     k_direct<MODE, TY><<<grid, TX * TY, sm, st>>>(a);
     prof_end(cls, st);
@@ -174,6 +176,13 @@ mvd_status direct_update(const int dims[3], const float* r, const float* k, cons
     a.out = psi;
     a.eps = eps;
     return launch<1>(a, kd, st, "direct update", ty);
+}
+
+mvd_status direct_accumulate(const int dims[3], const float* r, const float* k, const int kd[3], float* prod,
+                             cudaStream_t st, int ty) {
+    DArgs a = make(dims, r, k, kd);
+    a.out = prod;
+    return launch<4>(a, kd, st, "direct accumulate", ty);
 }
 
 mvd_status direct_conv(const int dims[3], const float* in, const float* k, const int kd[3], float* out,

@@ -146,6 +146,9 @@ static mvd_status x_fast(const FftGeom& g, int mode, const float* src, float2* S
         } else if (mode == 1) {
             kern = k_x_inverse_fast<L, 1>;
             cls = KC_X_UPDATE;
+        } else if (mode == 4) {
+            kern = k_x_inverse_fast<L, 4>;
+            cls = KC_X_UPDATE;
         } else {
             kern = k_x_inverse_fast<L, 2>;
         }
@@ -174,6 +177,12 @@ mvd_status fft_x_update_fast(const FftGeom& g, const float2* S, float* psi, floa
 }
 mvd_status fft_x_update_dd_fast(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st) {
     return x_fast(g, 1, nullptr, nullptr, nullptr, psi, eps, st, S2);
+}
+mvd_status fft_x_accumulate_fast(const FftGeom& g, const float2* S, float* acc, cudaStream_t st) {
+    return x_fast(g, 4, nullptr, const_cast<float2*>(S), nullptr, acc, 0.f, st);
+}
+mvd_status fft_x_accumulate_dd_fast(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st) {
+    return x_fast(g, 4, nullptr, nullptr, nullptr, acc, 0.f, st, S2);
 }
 mvd_status fft_inverse_real_fast(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
     return x_fast(g, 2, nullptr, const_cast<float2*>(S), nullptr, dst, 0.f, st);

@@ -186,7 +186,8 @@ __device__ __forceinline__ void fast_x_forward_tile(const XFast& a, long tile, f
     x_store_halves<L>(a, v, sm, p, t, rho0, nrows);
 }
 
-// MODE 0: ratio -> forward ; 1: psi update ; 2: plain real output
+// MODE 0: ratio -> forward ; 1: psi update ; 2: plain real output ;
+// 4: acc *= c (the combined update's product of view factors; acc in a.psi)
 template <int L, int MODE, bool CO>
 __device__ __forceinline__ void fast_x_inverse_tile(const XFast& a, long tile, float2* sm) {
     constexpr int TPL = L / kE, P = kFastThreads / TPL, LS = line_stride(L);
@@ -206,7 +207,7 @@ __device__ __forceinline__ void fast_x_inverse_tile(const XFast& a, long tile, f
             const int n = t + TPL * q;
             w[q] = make_float2(oka ? __ldg(a.phi + ra + n) : 0.f, okb ? __ldg(a.phi + rb + n) : 0.f);
         }
-    } else if (MODE == 1) {
+    } else if (MODE == 1 || MODE == 4) {
 #pragma unroll
         for (int q = 0; q < kE; ++q) {
             const int n = t + TPL * q;
@@ -231,6 +232,9 @@ __device__ __forceinline__ void fast_x_inverse_tile(const XFast& a, long tile, f
             if (MODE == 1) {
                 if (oka) a.psi[ra + n] = fmaxf(w[q].x * (v[q].x + 1.f), a.eps);
                 if (okb) a.psi[rb + n] = fmaxf(w[q].y * (v[q].y + 1.f), a.eps);
+            } else if (MODE == 4) {  // combined update: multiply this view's factor into the product
+                if (oka) a.psi[ra + n] = w[q].x * (v[q].x + 1.f);
+                if (okb) a.psi[rb + n] = w[q].y * (v[q].y + 1.f);
             } else {
                 if (oka) a.psi[ra + n] = v[q].x;
                 if (okb) a.psi[rb + n] = v[q].y;

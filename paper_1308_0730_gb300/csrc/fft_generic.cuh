@@ -176,7 +176,9 @@ __device__ void gen_x_ratio_tile(const GenX& a, long tile, float2* sm) {
 }
 
 // UPDATE: spectrum -> inverse x -> psi = max(psi . c, eps); else plain real output
-template <bool CO, bool UPDATE>
+// MODE 0: plain real output ; 1: psi update ; 4: acc *= c (the combined
+// update's product of view factors; acc in a.psi)
+template <bool CO, int MODE>
 __device__ void gen_x_inverse_tile(const GenX& a, long tile, float2* sm) {
     float2* A = sm;
     float2* B = sm + a.P * a.ls;
@@ -190,8 +192,10 @@ __device__ void gen_x_inverse_tile(const GenX& a, long tile, float2* sm) {
         const int p = row < a.P ? row : row - a.P;
         const float c = reinterpret_cast<const float*>(R + p * a.ls + n)[row < a.P ? 0 : 1];
         float* dst = a.psi + (rho0 + row) * a.X + n;
-        if (UPDATE)
+        if (MODE == 1)
             *dst = fmaxf(ld1<CO>(dst) * (c + 1.f), a.eps);  // c = (r - 1) * K + 1 (K sums to 1)
+        else if (MODE == 4)
+            *dst = ld1<CO>(dst) * (c + 1.f);
         else
             *dst = c;
     }

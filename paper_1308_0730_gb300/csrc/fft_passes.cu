@@ -35,10 +35,10 @@ __global__ void __launch_bounds__(kGenThreads) k_x_ratio(GenX a) {
     gen_x_ratio_tile<false>(a, blockIdx.x, sm);
 }
 
-template <bool UPDATE>
+template <int MODE>
 __global__ void __launch_bounds__(kGenThreads) k_x_inverse(GenX a) {
     extern __shared__ float2 sm[];
-    gen_x_inverse_tile<false, UPDATE>(a, blockIdx.x, sm);
+    gen_x_inverse_tile<false, MODE>(a, blockIdx.x, sm);
 }
 
 template <int S>
@@ -88,7 +88,7 @@ mvd_status fft_x_update_generic(const FftGeom& g, const float2* S, float* psi, f
     a.S = const_cast<float2*>(S);
     a.psi = psi;
     a.eps = eps;
-    return launch(k_x_inverse<true>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
+    return launch(k_x_inverse<1>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
 }
 
 mvd_status fft_x_update_dd_generic(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st) {
@@ -96,14 +96,22 @@ mvd_status fft_x_update_dd_generic(const FftGeom& g, const cdd* S2, float* psi, 
     a.S2in = S2;
     a.psi = psi;
     a.eps = eps;
-    return launch(k_x_inverse<true>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
+    return launch(k_x_inverse<1>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
+}
+
+mvd_status fft_x_accumulate_generic(const FftGeom& g, const float2* S, const cdd* S2, float* acc, cudaStream_t st) {
+    GenX a = make_x(g);
+    a.S = const_cast<float2*>(S);
+    a.S2in = S2;
+    a.psi = acc;
+    return launch(k_x_inverse<4>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x accumulate", KC_X_UPDATE);
 }
 
 mvd_status fft_inverse_real_generic(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
     GenX a = make_x(g);
     a.S = const_cast<float2*>(S);
     a.psi = dst;
-    return launch(k_x_inverse<false>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x inverse", KC_SETUP);
+    return launch(k_x_inverse<0>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x inverse", KC_SETUP);
 }
 
 mvd_status fft_y_generic(const FftGeom& g, float2* S, int inverse, cudaStream_t st) {
@@ -141,6 +149,14 @@ mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps
 mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st) {
     if (g.fast && fft_fast_supported(g.X)) return fft_x_update_dd_fast(g, S2, psi, eps, st);
     return fft_x_update_dd_generic(g, S2, psi, eps, st);
+}
+mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st) {
+    if (g.fast && fft_fast_supported(g.X)) return fft_x_accumulate_fast(g, S, acc, st);
+    return fft_x_accumulate_generic(g, S, nullptr, acc, st);
+}
+mvd_status fft_x_accumulate_dd(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st) {
+    if (g.fast && fft_fast_supported(g.X)) return fft_x_accumulate_dd_fast(g, S2, acc, st);
+    return fft_x_accumulate_generic(g, nullptr, S2, acc, st);
 }
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
     if (g.fast && fft_fast_supported(g.X)) return fft_inverse_real_fast(g, S, dst, st);

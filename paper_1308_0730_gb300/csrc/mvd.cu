@@ -178,6 +178,7 @@ void free_fft(mvd_ctx* c) {
 void free_all(mvd_ctx* c) {
     drop_graphs(c);
     dev_free(c->d_ckpt);
+    dev_free(c->d_prod);
     free_fft(c);
     dev_free(c->d_views);
     dev_free(c->d_psi);
@@ -399,12 +400,15 @@ mvd_status time_updates(mvd_ctx* c, float* psi_save, double cutoff_ms, double* m
 
 }  // namespace
 
-mvd_status mvd::one_update(mvd_ctx* c, int v) {
+mvd_status mvd::one_update(mvd_ctx* c, int v) { return view_pass(c, v, nullptr); }
+
+mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
     const float* phi = c->d_views + (size_t)v * c->M;
     const int* kd = &c->kd[3 * v];
     if (c->path == MVD_PATH_DIRECT) {
         MVD_TRY(direct_ratio(c->dims, c->d_psi, c->d_psf + c->koff[v], kd, phi, c->eps, c->d_r, c->stream,
                              c->direct_ty));
+        if (prod) return direct_accumulate(c->dims, c->d_r, c->d_comp + c->koff[v], kd, prod, c->stream, c->direct_ty);
         return direct_update(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_psi, c->eps, c->stream,
                              c->direct_ty);
     }
@@ -423,6 +427,7 @@ mvd_status mvd::one_update(mvd_ctx* c, int v) {
         MVD_TRY(dd_y(g, S2, 0, c->stream));
         MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
         MVD_TRY(dd_y(g, S2, 1, c->stream));
+        if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream);
         return fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream);
     }
     const float2* Kp = c->d_K + ns * (2 * v);
@@ -435,10 +440,58 @@ mvd_status mvd::one_update(mvd_ctx* c, int v) {
     MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
     MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
     MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
+    if (prod) return fft_x_accumulate(g, c->d_S, prod, c->stream);
     return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream);
 }
 
 namespace {
+
+// Enqueues n_iter iterations, one iteration being what `one` enqueues. On a
+// non-NULL stream one iteration is captured once as a CUDA graph (kept per
+// key until the next precompute or destroy) and replayed; the host then
+// launches one graph per iteration instead of every kernel. Not on the legacy
+// default stream (it cannot be captured), not while per-kernel timing is on,
+// and not with MVD_NO_GRAPH=1.
+template <typename F>
+mvd_status run_iterations(mvd_ctx* c, const std::vector<int>& key, int n_iter, F&& one) {
+    const char* ng = std::getenv("MVD_NO_GRAPH");
+    const bool use_graph = n_iter > 0 && c->stream != nullptr && !g_prof_on.load() && !(ng && ng[0] == '1');
+    if (!use_graph) {
+        for (int i = 0; i < n_iter; ++i) MVD_TRY(one());
+        return MVD_OK;
+    }
+    cudaGraphExec_t exec = nullptr;
+    unsigned nodes = 0;
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end()) {
+        exec = it->second.exec;
+        nodes = it->second.nodes;
+    } else {
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_status(e, "begin capture");
+        const unsigned long long before = g_launches.load();
+        const mvd_status st = one();
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(c->stream, &graph);
+        nodes = (unsigned)(g_launches.load() - before);
+        g_launches.fetch_sub(nodes);  // captured, not launched
+        if (st != MVD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_status(e, "end capture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_status(e, "instantiate graph");
+        c->graphs[key] = {exec, nodes};
+    }
+    for (int i = 0; i < n_iter; ++i) {
+        const cudaError_t e = cudaGraphLaunch(exec, c->stream);
+        if (e != cudaSuccess) return cuda_status(e, "graph launch");
+        count_launch(nodes);
+    }
+    return MVD_OK;
+}
 
 mvd_status read_flag(mvd_ctx* c, int* flag) {
     MVD_CUDA(cudaMemcpyAsync(flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -770,49 +823,35 @@ mvd_status mvd_iterate(mvd_ctx* c, int n_iter, const int* schedule, int schedule
     DeviceGuard dg(c->device);
     std::vector<int> sched(L);
     for (int s = 0; s < L; ++s) sched[s] = schedule_len > 0 ? schedule[s] : s;
-    // One iteration of the schedule is captured once as a CUDA graph and
-    // replayed: the host launches one graph per iteration instead of 9
-    // kernels per view update. Not on the legacy default stream (it cannot be
-    // captured), not while per-kernel timing is on, and not with MVD_NO_GRAPH=1.
-    const char* ng = std::getenv("MVD_NO_GRAPH");
-    const bool use_graph = n_iter > 0 && c->stream != nullptr && !g_prof_on.load() && !(ng && ng[0] == '1');
-    if (use_graph) {
-        cudaGraphExec_t exec = nullptr;
-        unsigned nodes = 0;
-        auto it = c->graphs.find(sched);
-        if (it != c->graphs.end()) {
-            exec = it->second.exec;
-            nodes = it->second.nodes;
-        } else {
-            cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-            if (e != cudaSuccess) return cuda_status(e, "mvd_iterate: begin capture");
-            const unsigned long long before = g_launches.load();
-            mvd_status st = MVD_OK;
-            for (int s = 0; s < L && st == MVD_OK; ++s) st = one_update(c, sched[s]);
-            cudaGraph_t graph = nullptr;
-            e = cudaStreamEndCapture(c->stream, &graph);
-            nodes = (unsigned)(g_launches.load() - before);
-            g_launches.fetch_sub(nodes);  // captured, not launched
-            if (st != MVD_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                return st;
-            }
-            if (e != cudaSuccess) return cuda_status(e, "mvd_iterate: end capture");
-            e = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) return cuda_status(e, "mvd_iterate: instantiate graph");
-            c->graphs[sched] = {exec, nodes};
-        }
-        for (int i = 0; i < n_iter; ++i) {
-            cudaError_t e = cudaGraphLaunch(exec, c->stream);
-            if (e != cudaSuccess) return cuda_status(e, "mvd_iterate: graph launch");
-            count_launch(nodes);
-        }
-        return MVD_OK;
-    }
-    for (int i = 0; i < n_iter; ++i)
+    return run_iterations(c, sched, n_iter, [&]() -> mvd_status {
         for (int s = 0; s < L; ++s) MVD_TRY(one_update(c, sched[s]));
-    return MVD_OK;
+        return MVD_OK;
+    });
+}
+
+mvd_status mvd_iterate_combined(mvd_ctx* c, int n_iter, int root) {
+    clear_error();
+    if (!c) {
+        set_error("mvd_iterate_combined: NULL context");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 2) {
+        set_error("mvd_iterate_combined: kernels not precomputed");
+        return MVD_ERR_STATE;
+    }
+    if (n_iter < 0) {
+        set_error("mvd_iterate_combined: n_iter < 0");
+        return MVD_ERR_ARG;
+    }
+    DeviceGuard dg(c->device);
+    if (!c->d_prod) MVD_TRY(dev_alloc(&c->d_prod, (size_t)c->M, "combined-update product"));
+    const float e = root ? (float)(1.0 / (double)c->nv) : 1.f;
+    // graph key: schedule entries are >= 0, so {-1} and {-2} name the two combined forms
+    return run_iterations(c, {root ? -2 : -1}, n_iter, [&]() -> mvd_status {
+        MVD_TRY(fill(c->d_prod, c->M, 1.f, c->stream));
+        for (int v = 0; v < c->nv; ++v) MVD_TRY(view_pass(c, v, c->d_prod));
+        return apply_product(c->d_psi, c->d_prod, c->M, e, c->eps, c->stream);
+    });
 }
 
 mvd_status mvd_result(mvd_ctx* c, float* out, size_t n_elems) {

@@ -141,6 +141,16 @@ __global__ void k_check_positive(const float* v, long n, int* bad) {
     if (b) atomicOr(bad, 1);
 }
 
+// combined update: psi = max(psi . prod^e, eps) (e = 1/N for the geometric mean,
+// 1 for the plain product); rounding can leave a factor slightly below 0
+__global__ void k_apply_product(float* psi, const float* prod, long n, float e, float eps) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float p = fmaxf(prod[i], 0.f);
+        const float f = e == 1.f ? p : powf(p, e);
+        psi[i] = fmaxf(psi[i] * f, eps);
+    }
+}
+
 __global__ void k_fill(float* p, long n, float v) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -229,6 +239,12 @@ mvd_status check_positive(const float* p, long n, int* d_bad, cudaStream_t st) {
     k_check_positive<<<grid_stride_blocks(n), kThreads, 0, st>>>(p, n, d_bad);
     count_launch();
     return check_launch("check estimate");
+}
+
+mvd_status apply_product(float* psi, const float* prod, long n, float e, float eps, cudaStream_t st) {
+    k_apply_product<<<grid_stride_blocks(n), kThreads, 0, st>>>(psi, prod, n, e, eps);
+    count_launch();
+    return check_launch("apply product");
 }
 
 mvd_status fill(float* p, long n, float v, cudaStream_t st) {

@@ -31,7 +31,7 @@ EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_s
            "mvd_profile_enable", "mvd_profile_read", "mvd_update_direct_noalloc", "mvd_batch_create",
            "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy", "mvd_unrolled_forward",
            "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp", "mvd_autotune",
-           "mvd_batch_create_mode", "mvd_batch_mode"]
+           "mvd_batch_create_mode", "mvd_batch_mode", "mvd_iterate_combined"]
 
 
 class MvdError(RuntimeError):
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_precompute_kernels.argtypes = [vp, ci]
     lib.mvd_set_estimate.argtypes = [vp, vp, ci]
     lib.mvd_iterate.argtypes = [vp, ci, ctypes.POINTER(ci), ci]
+    lib.mvd_iterate_combined.argtypes = [vp, ci, ci]
+    lib.mvd_iterate_combined.restype = ci
     lib.mvd_result.argtypes = [vp, _FP, sz]
     lib.mvd_result_device.argtypes = [vp, ctypes.POINTER(vp)]
     lib.mvd_synchronize.argtypes = [vp]
@@ -224,6 +226,11 @@ def mvd_iterate(ctx, n_iter: int, schedule=None):
     else:
         s = (ctypes.c_int * len(schedule))(*[int(v) for v in schedule])
         _check(lib.mvd_iterate(ctx, int(n_iter), s, len(schedule)))
+
+
+def mvd_iterate_combined(ctx, n_iter: int, root: bool = True):
+    """Combined update (all views' factors from the same estimate); ``root`` takes their geometric mean."""
+    _check(load().mvd_iterate_combined(ctx, int(n_iter), 1 if root else 0))
 
 
 def mvd_result(ctx, out: np.ndarray):
@@ -381,6 +388,9 @@ class Deconvolver:
 
     def iterate(self, n_iter, schedule=None):
         mvd_iterate(self.ctx, n_iter, schedule)
+
+    def iterate_combined(self, n_iter, root=True):
+        mvd_iterate_combined(self.ctx, n_iter, root)
 
     def set_estimate(self, psi=None):
         mvd_set_estimate(self.ctx, psi)
