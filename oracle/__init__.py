@@ -19,6 +19,9 @@ from .oracle import (  # noqa: F401
     update_at,
     deconvolve,
     deconvolve_combined,
+    deconvolve_weighted,
+    normalize_weights,
+    WEIGHT_NORMS,
     mean_views,
     num_threads,
     unrolled_grad,

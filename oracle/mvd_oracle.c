@@ -333,6 +333,100 @@ double mvdo_deconvolve_combined(int n_views, const double* const* views, const d
     return bad ? -1.0 : eps;
 }
 
+/* Partially overlapping views (Suppl. Note "Partially overlapping datasets").
+ * Each view carries a weight image w_v in [0, 1] (a blending function: 1 in
+ * the view's central part, falling to 0 towards its boundary). Normalisation:
+ * per voxel, with S = sum_v w_v, every weight is scaled by min(1, T / S), so
+ * the sum is at most T and no weight ever grows; T is 1 (norm 0), the minimal
+ * number of views overlapping at a voxel (norm 1), the average number (norm
+ * 2), or `value` (norm 3). The number of views overlapping at a voxel counts
+ * the views with w_v > 0; the minimum and the average run over the voxels at
+ * least one view covers. Returns T, or -1 on a bad argument. */
+double mvdo_normalize_weights(int n_views, const double* const* w, const int dims[3], int norm, double value,
+                              double* const* out) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double T = 1.0;
+    if (norm == 1 || norm == 2) {
+        long covered = 0, sum = 0;
+        int mn = n_views + 1;
+        for (long i = 0; i < M; ++i) {
+            int n = 0;
+            for (int v = 0; v < n_views; ++v) n += w[v][i] > 0.0;
+            if (n == 0) continue;
+            ++covered;
+            sum += n;
+            if (n < mn) mn = n;
+        }
+        if (covered == 0) return -1.0;
+        T = norm == 1 ? (double)mn : (double)sum / (double)covered;
+    } else if (norm == 3) {
+        if (!(value > 0.0)) return -1.0;
+        T = value;
+    } else if (norm != 0) {
+        return -1.0;
+    }
+    for (long i = 0; i < M; ++i) {
+        double S = 0.0;
+        for (int v = 0; v < n_views; ++v) S += w[v][i];
+        const double f = S > T ? T / S : 1.0;
+        for (int v = 0; v < n_views; ++v) out[v][i] = w[v][i] * f;
+    }
+    return T;
+}
+
+/* Sequential deconvolution with (already normalised) view weights: each view
+ * update applies the fraction w_v of the change the Richardson-Lucy step
+ * suggests, psi <- max(psi + w_v (psi c_v - psi), eps) = max(psi (1 + w_v (c_v - 1)), eps).
+ * Otherwise as mvdo_deconvolve (default schedule). Returns eps, or -1. */
+double mvdo_deconvolve_weighted(int n_views, const double* const* views, const double* const* psfs,
+                                const int* pdims, const int dims[3], int variant, int n_iter,
+                                const double* const* weights, double eps, int init, double* psi) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double psi0 = mvdo_mean_views(n_views, views, dims);
+    if (eps <= 0.0) eps = 1e-4 * psi0;
+    if (!init)
+        for (long i = 0; i < M; ++i) psi[i] = psi0;
+    double** pn = (double**)malloc(sizeof(double*) * n_views);
+    double** comp = (double**)malloc(sizeof(double*) * n_views);
+    int bad = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        double s = 0.0;
+        for (long i = 0; i < T; ++i) s += psfs[v][i];
+        pn[v] = (double*)malloc(sizeof(double) * T);
+        for (long i = 0; i < T; ++i) pn[v][i] = psfs[v][i] / s;
+    }
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        comp[v] = (double*)malloc(sizeof(double) * T);
+        if (mvdo_compound(n_views, (const double* const*)pn, pdims, v, variant, comp[v]) != 0) bad = 1;
+    }
+    double* b = (double*)malloc(sizeof(double) * M);
+    double* r = (double*)malloc(sizeof(double) * M);
+    double* c = (double*)malloc(sizeof(double) * M);
+    for (int it = 0; it < n_iter && !bad; ++it) {
+        for (int v = 0; v < n_views; ++v) {
+            const int* pd = pdims + 3 * v;
+            mvdo_conv(psi, dims, pn[v], pd, b);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) r[i] = views[v][i] / fmax(b[i], eps);
+            mvdo_conv(r, dims, comp[v], pd, c);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) psi[i] = fmax(psi[i] + weights[v][i] * (psi[i] * c[i] - psi[i]), eps);
+        }
+    }
+    for (int v = 0; v < n_views; ++v) {
+        free(comp[v]);
+        free(pn[v]);
+    }
+    free(comp);
+    free(pn);
+    free(b);
+    free(r);
+    free(c);
+    return bad ? -1.0 : eps;
+}
+
 /* One view update evaluated only at the listed voxels (flat indices):
  *   out[i] = max(psi(x_i) * c(x_i), eps), with c, r, b computed from the
  * definitions above on the neighbourhood each sample needs. */

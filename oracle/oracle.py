@@ -61,6 +61,13 @@ def _load():
                                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                      ctypes.c_int, _D]
             lib.mvdo_deconvolve_combined.restype = ctypes.c_double
+            lib.mvdo_normalize_weights.argtypes = [ctypes.c_int, ctypes.POINTER(_D), _I, ctypes.c_int,
+                                                   ctypes.c_double, ctypes.POINTER(_D)]
+            lib.mvdo_normalize_weights.restype = ctypes.c_double
+            lib.mvdo_deconvolve_weighted.argtypes = [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D), _I, _I,
+                                                     ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D),
+                                                     ctypes.c_double, ctypes.c_int, _D]
+            lib.mvdo_deconvolve_weighted.restype = ctypes.c_double
             lib.mvdo_update_at.argtypes = [_D, _D, _D, _I, _D, _I, _I, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_long), ctypes.c_int, _D]
             lib.mvdo_num_threads.restype = ctypes.c_int
@@ -208,6 +215,42 @@ def deconvolve_combined(views, psfs, n_iter, variant="efficient", root=True, eps
         psi, init = _f64(psi_init).copy(), 1
     used = _load().mvdo_deconvolve_combined(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter),
                                             1 if root else 0, float(eps), init, _dptr(psi))
+    if used < 0:
+        raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
+    return psi, used
+
+
+WEIGHT_NORMS = {"sum1": 0, "min_overlap": 1, "avg_overlap": 2, "user": 3}
+
+
+def normalize_weights(weights, norm="sum1", value=0.0):
+    """Per-voxel normalisation of view weights (Suppl. Note "Partially overlapping datasets"):
+    scale by min(1, T / sum_v w_v). Returns ``(normalised weights, T)``."""
+    ws = [_f64(w) for w in weights]
+    out = [np.empty_like(w) for w in ws]
+    n = WEIGHT_NORMS[norm] if isinstance(norm, str) else int(norm)
+    T = _load().mvdo_normalize_weights(len(ws), (_D * len(ws))(*[_dptr(w) for w in ws]), _dims_xyz(ws[0]), n,
+                                       float(value), (_D * len(out))(*[_dptr(o) for o in out]))
+    if T < 0:
+        raise ValueError("bad weight normalisation")
+    return out, T
+
+
+def deconvolve_weighted(views, psfs, n_iter, weights, variant="efficient", eps=0.0, psi_init=None):
+    """Sequential deconvolution where view v's update applies the fraction weights[v] (normalised)
+    of the Richardson-Lucy change. Returns ``(psi, eps_used)``."""
+    var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    vs = [_f64(v) for v in views]
+    ws = [_f64(w) for w in weights]
+    ps, parr, pd = _psf_arrays(psfs)
+    varr = (_D * len(vs))(*[_dptr(v) for v in vs])
+    warr = (_D * len(ws))(*[_dptr(w) for w in ws])
+    if psi_init is None:
+        psi, init = np.empty_like(vs[0]), 0
+    else:
+        psi, init = _f64(psi_init).copy(), 1
+    used = _load().mvdo_deconvolve_weighted(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), warr,
+                                            float(eps), init, _dptr(psi))
     if used < 0:
         raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
     return psi, used
