@@ -145,6 +145,35 @@ mvd_status mvd_set_estimate(mvd_ctx* ctx, const float* psi, int on_device);
 mvd_status mvd_iterate(mvd_ctx* ctx, int n_iter, const int* schedule, int schedule_len);
 
 /*
+ * Partially overlapping views (Suppl. Note "Partially overlapping datasets").
+ * weights: n_views pointers to X*Y*Z floats in [0, 1] (host, or device if
+ * on_device), each view's blending image (1 where the view has data, falling
+ * to 0 towards its boundary; else MVD_ERR_ARG). They are copied and, per
+ * voxel, scaled by min(1, T / sum_v w_v), so the sum over views is at most T
+ * and no weight ever grows; T (written to *target when non-NULL) is
+ *   MVD_WEIGHTS_SUM_ONE     1 (the most uniform update),
+ *   MVD_WEIGHTS_MIN_OVERLAP the minimal number of views overlapping at a voxel,
+ *   MVD_WEIGHTS_AVG_OVERLAP the average number,
+ *   MVD_WEIGHTS_USER        value (> 0),
+ * counting at each voxel covered by some view the views with w_v > 0.
+ * From then on every view update of mvd_iterate applies the fraction w_v of
+ * the change of the Richardson-Lucy step: psi = max(psi (1 + w_v (c_v - 1)), eps).
+ * weights == NULL removes them. The combined update, the unrolled
+ * differentiation and the persistent batch kernel return MVD_ERR_UNSUPPORTED
+ * for a context with weights. Synchronises the stream.
+ * mvd_get_weights copies view v's normalised weights (X*Y*Z floats) to host.
+ */
+typedef enum {
+    MVD_WEIGHTS_SUM_ONE = 0,
+    MVD_WEIGHTS_MIN_OVERLAP = 1,
+    MVD_WEIGHTS_AVG_OVERLAP = 2,
+    MVD_WEIGHTS_USER = 3
+} mvd_weight_norm;
+mvd_status mvd_set_weights(mvd_ctx* ctx, const float* const* weights, int on_device, int norm, float value,
+                           float* target);
+mvd_status mvd_get_weights(mvd_ctx* ctx, int v, float* out, size_t n_elems);
+
+/*
  * Runs n_iter iterations of the combined (simultaneous) update of Eq. 50 /
  * Eq. 220: every view's factor c_v = (phi_v / max(psi * P_v, eps)) * P_v^comp
  * is computed from the same psi, then

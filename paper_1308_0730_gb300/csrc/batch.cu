@@ -527,10 +527,17 @@ mvd_status mvd_batch_create_mode(mvd_ctx* const* ctxs, int n, int n_iter, int mo
                 return MVD_ERR_ARG;
             }
     }
-    bool all_fft = true;
-    for (int i = 0; i < n; ++i) all_fft = all_fft && ctxs[i]->path == MVD_PATH_FFT;
+    bool all_fft = true, any_weights = false;
+    for (int i = 0; i < n; ++i) {
+        all_fft = all_fft && ctxs[i]->path == MVD_PATH_FFT;
+        any_weights = any_weights || ctxs[i]->d_w != nullptr;
+    }
     const bool branches_ok = ctxs[0]->stream != nullptr && !profiling_on();
     if (mode == MVD_BATCH_AUTO) mode = branches_ok ? MVD_BATCH_BRANCHES : MVD_BATCH_PERSISTENT;
+    if (mode == MVD_BATCH_PERSISTENT && any_weights) {
+        set_error("mvd_batch_create: the persistent kernel does not apply view weights");
+        return MVD_ERR_UNSUPPORTED;
+    }
     if (mode == MVD_BATCH_PERSISTENT && !all_fft) {
         set_error("mvd_batch_create: the persistent kernel needs every context on the FFT engine");
         return MVD_ERR_UNSUPPORTED;

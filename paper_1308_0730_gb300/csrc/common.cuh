@@ -97,7 +97,8 @@ mvd_status fft_y(const FftGeom& g, float2* S, int inverse, cudaStream_t st);
 mvd_status fft_z_mul(const FftGeom& g, float2* S, const float2* K, cudaStream_t st);
 mvd_status fft_z_forward_scaled(const FftGeom& g, float2* S, float scale, cudaStream_t st);
 mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
-mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st);
+mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
+                        const float* wt = nullptr);  // wt: per-voxel weights of the change, or none
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
 // combined update: acc *= c, c the back-projected factor of the spectrum of (r - 1) * K (+ 1)
 mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st);
@@ -116,7 +117,8 @@ mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cu
 mvd_status dd_x_inverse_real(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st);
 bool dd_fast_x(const FftGeom& g);
 // update pass reading the double-float spectrum (rounded to FP32)
-mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st);
+mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
+                           const float* wt = nullptr);
 
 // register-resident variants for power-of-two lengths (fft_fast.cu)
 bool fft_fast_supported(int L);
@@ -126,9 +128,11 @@ mvd_status fft_y_fast(const FftGeom& g, float2* S, int inverse, cudaStream_t st)
 mvd_status fft_z_mul_fast(const FftGeom& g, float2* S, const float2* K, cudaStream_t st);
 mvd_status fft_z_forward_scaled_fast(const FftGeom& g, float2* S, float scale, cudaStream_t st);
 mvd_status fft_x_ratio_fast(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
-mvd_status fft_x_update_fast(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st);
+mvd_status fft_x_update_fast(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
+                             const float* wt = nullptr);
 mvd_status fft_inverse_real_fast(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
-mvd_status fft_x_update_dd_fast(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st);
+mvd_status fft_x_update_dd_fast(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
+                                const float* wt = nullptr);
 
 // Direct (spatial) periodic convolution with fused epilogues.
 bool direct_supported(const int kd[3]);
@@ -137,7 +141,7 @@ bool direct_supported(const int kd[3]);
 mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, const int kd[3],
                         const float* phi, float eps, float* r, cudaStream_t st, int ty = 0);
 mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
-                         float* psi, float eps, cudaStream_t st, int ty = 0);
+                         float* psi, float eps, cudaStream_t st, int ty = 0, const float* wt = nullptr);
 int direct_tile_heights(const int kd[3], int out[4]);  // tile heights that fit, largest first
 // prod *= r * k (the combined update's product of view factors)
 mvd_status direct_accumulate(const int dims[3], const float* r, const float* k, const int kd[3], float* prod,
@@ -166,6 +170,10 @@ mvd_status place_kernel(const int dims[3], const float* k, const int kd[3], floa
 mvd_status view_stats(const float* views, long n, double* d_sum, int* d_bad, cudaStream_t st);
 mvd_status fill(float* p, long n, float v, cudaStream_t st);
 mvd_status apply_product(float* psi, const float* prod, long n, float e, float eps, cudaStream_t st);
+// partial overlap weights: range check, overlap counts, per-voxel normalisation
+mvd_status weights_check(const float* w, long n, int* d_bad, cudaStream_t st);
+mvd_status weights_overlap(const float* w, int nv, long M, unsigned long long* d_stats, int* d_min, cudaStream_t st);
+mvd_status weights_normalize(float* w, int nv, long M, float T, cudaStream_t st);
 mvd_status check_positive(const float* p, long n, int* d_bad, cudaStream_t st);
 
 }  // namespace mvd
@@ -223,6 +231,8 @@ struct mvd_ctx {
     int path_opt = MVD_PATH_AUTO;
     int direct_ty = 0;  // direct-engine tile height chosen by the autotuner (0 = default)
     float* d_prod = nullptr;  // combined update: product of the view factors (M)
+    float* d_w = nullptr;     // partial overlap: normalised weights of every view (nv * M), or none
+    float weight_norm = 0.f;  // the normalisation target T of the weights
     int path = MVD_PATH_AUTO;
     float psi0 = 0.f, eps = 0.f;
 };

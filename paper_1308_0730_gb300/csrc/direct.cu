@@ -37,6 +37,7 @@ struct DArgs {
     const float* phi;
     float* out;  // r (ratio), psi (update) or plain output
     float eps;
+    const float* wt;  // update: when set, apply the fraction wt of the change (partial overlap)
 };
 
 // MODE 0: out = phi / max(conv, eps); MODE 1: out = max(out . conv, eps); MODE 2: out = conv;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(TX * TY) k_direct(DArgs a) {
         if (MODE == 0)
             a.out[g] = __ldg(a.phi + g) / fmaxf(acc[o], a.eps);
         else if (MODE == 1)
-            a.out[g] = fmaxf(a.out[g] * acc[o], a.eps);
+            a.out[g] = fmaxf(a.out[g] * (a.wt ? 1.f + __ldg(a.wt + g) * (acc[o] - 1.f) : acc[o]), a.eps);
         else if (MODE == 2)
             a.out[g] = acc[o];
         else if (MODE == 3)
@@ -171,10 +172,11 @@ mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, con
 }
 
 mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
-                         float* psi, float eps, cudaStream_t st, int ty) {
+                         float* psi, float eps, cudaStream_t st, int ty, const float* wt) {
     DArgs a = make(dims, r, k, kd);
     a.out = psi;
     a.eps = eps;
+    a.wt = wt;
     return launch<1>(a, kd, st, "direct update", ty);
 }
 

@@ -179,6 +179,7 @@ void free_all(mvd_ctx* c) {
     drop_graphs(c);
     dev_free(c->d_ckpt);
     dev_free(c->d_prod);
+    dev_free(c->d_w);
     free_fft(c);
     dev_free(c->d_views);
     dev_free(c->d_psi);
@@ -405,12 +406,13 @@ mvd_status mvd::one_update(mvd_ctx* c, int v) { return view_pass(c, v, nullptr);
 mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
     const float* phi = c->d_views + (size_t)v * c->M;
     const int* kd = &c->kd[3 * v];
+    const float* wt = c->d_w ? c->d_w + (size_t)v * c->M : nullptr;  // partial overlap (sequential update only)
     if (c->path == MVD_PATH_DIRECT) {
         MVD_TRY(direct_ratio(c->dims, c->d_psi, c->d_psf + c->koff[v], kd, phi, c->eps, c->d_r, c->stream,
                              c->direct_ty));
         if (prod) return direct_accumulate(c->dims, c->d_r, c->d_comp + c->koff[v], kd, prod, c->stream, c->direct_ty);
         return direct_update(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_psi, c->eps, c->stream,
-                             c->direct_ty);
+                             c->direct_ty, wt);
     }
     const FftGeom& g = c->geom;
     const size_t ns = (size_t)g.Xh * g.YZ;
@@ -428,7 +430,7 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
         MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
         MVD_TRY(dd_y(g, S2, 1, c->stream));
         if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream);
-        return fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream);
+        return fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt);
     }
     const float2* Kp = c->d_K + ns * (2 * v);
     const float2* Kc = c->d_K + ns * (2 * v + 1);
@@ -441,7 +443,7 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
     MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
     MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
     if (prod) return fft_x_accumulate(g, c->d_S, prod, c->stream);
-    return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream);
+    return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream, wt);
 }
 
 namespace {
@@ -492,6 +494,8 @@ mvd_status run_iterations(mvd_ctx* c, const std::vector<int>& key, int n_iter, F
     }
     return MVD_OK;
 }
+
+mvd_status cuda_ok(cudaError_t e, const char* what) { return e == cudaSuccess ? MVD_OK : cuda_status(e, what); }
 
 mvd_status read_flag(mvd_ctx* c, int* flag) {
     MVD_CUDA(cudaMemcpyAsync(flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -829,6 +833,111 @@ mvd_status mvd_iterate(mvd_ctx* c, int n_iter, const int* schedule, int schedule
     });
 }
 
+mvd_status mvd_set_weights(mvd_ctx* c, const float* const* weights, int on_device, int norm, float value,
+                           float* target) {
+    clear_error();
+    if (!c) {
+        set_error("mvd_set_weights: NULL context");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 1) {
+        set_error("mvd_set_weights: context not created");
+        return MVD_ERR_STATE;
+    }
+    DeviceGuard dg(c->device);
+    drop_graphs(c);  // the captured update passes carry the weight pointers
+    if (!weights) {
+        dev_free(c->d_w);
+        c->weight_norm = 0.f;
+        return MVD_OK;
+    }
+    if (norm < MVD_WEIGHTS_SUM_ONE || norm > MVD_WEIGHTS_USER || (norm == MVD_WEIGHTS_USER && !(value > 0.f))) {
+        set_error("mvd_set_weights: unknown normalisation %d or bad value", norm);
+        return MVD_ERR_ARG;
+    }
+    for (int v = 0; v < c->nv; ++v)
+        if (!weights[v]) {
+            set_error("mvd_set_weights: weight image %d is NULL", v);
+            return MVD_ERR_ARG;
+        }
+    const long M = c->M;
+    const int nv = c->nv;
+    float* w = nullptr;
+    MVD_TRY(dev_alloc(&w, (size_t)nv * M, "view weights"));
+    mvd_status st = MVD_OK;
+    unsigned long long* stats = nullptr;
+    do {
+        for (int v = 0; v < nv && st == MVD_OK; ++v) {
+            const cudaError_t e = cudaMemcpyAsync(w + (size_t)v * M, weights[v], sizeof(float) * M,
+                                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                                  c->stream);
+            if (e != cudaSuccess) st = cuda_status(e, "mvd_set_weights: copy");
+        }
+        if (st != MVD_OK) break;
+        int bad = 0;
+        if ((st = cuda_ok(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream), "flag")) != MVD_OK) break;
+        if ((st = weights_check(w, (long)nv * M, c->d_flag, c->stream)) != MVD_OK) break;
+        if ((st = read_flag(c, &bad)) != MVD_OK) break;
+        if (bad) {
+            set_error("mvd_set_weights: weights must lie in [0, 1]");
+            st = MVD_ERR_ARG;
+            break;
+        }
+        double T = 1.0;
+        if (norm == MVD_WEIGHTS_USER) {
+            T = value;
+        } else if (norm != MVD_WEIGHTS_SUM_ONE) {
+            if ((st = dev_alloc(&stats, 2, "overlap counts")) != MVD_OK) break;
+            const int big = 1 << 30;
+            unsigned long long h[2] = {0, 0};
+            int mn = big;
+            cudaMemcpyAsync(stats, h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+            cudaMemcpyAsync(c->d_flag, &mn, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+            if ((st = weights_overlap(w, nv, M, stats, c->d_flag, c->stream)) != MVD_OK) break;
+            cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+            cudaMemcpyAsync(&mn, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+            if ((st = cuda_ok(cudaStreamSynchronize(c->stream), "overlap counts")) != MVD_OK) break;
+            if (h[0] == 0) {
+                set_error("mvd_set_weights: no voxel is covered by any view");
+                st = MVD_ERR_ARG;
+                break;
+            }
+            T = norm == MVD_WEIGHTS_MIN_OVERLAP ? (double)mn : (double)h[1] / (double)h[0];
+        }
+        if ((st = weights_normalize(w, nv, M, (float)T, c->stream)) != MVD_OK) break;
+        if ((st = cuda_ok(cudaStreamSynchronize(c->stream), "normalise weights")) != MVD_OK) break;
+        dev_free(c->d_w);
+        c->d_w = w;
+        w = nullptr;
+        c->weight_norm = (float)T;
+        if (target) *target = (float)T;
+    } while (false);
+    dev_free(w);
+    dev_free(stats);
+    return st;
+}
+
+mvd_status mvd_get_weights(mvd_ctx* c, int v, float* out, size_t n_elems) {
+    clear_error();
+    if (!c || !out) {
+        set_error("mvd_get_weights: NULL argument");
+        return MVD_ERR_ARG;
+    }
+    if (!c->d_w) {
+        set_error("mvd_get_weights: no weights set");
+        return MVD_ERR_STATE;
+    }
+    if (v < 0 || v >= c->nv || n_elems < (size_t)c->M) {
+        set_error("mvd_get_weights: bad view or buffer size");
+        return MVD_ERR_ARG;
+    }
+    DeviceGuard dg(c->device);
+    MVD_CUDA(cudaMemcpyAsync(out, c->d_w + (size_t)v * c->M, sizeof(float) * c->M, cudaMemcpyDeviceToHost,
+                             c->stream));
+    MVD_CUDA(cudaStreamSynchronize(c->stream));
+    return MVD_OK;
+}
+
 mvd_status mvd_iterate_combined(mvd_ctx* c, int n_iter, int root) {
     clear_error();
     if (!c) {
@@ -842,6 +951,10 @@ mvd_status mvd_iterate_combined(mvd_ctx* c, int n_iter, int root) {
     if (n_iter < 0) {
         set_error("mvd_iterate_combined: n_iter < 0");
         return MVD_ERR_ARG;
+    }
+    if (c->d_w) {
+        set_error("mvd_iterate_combined: view weights apply to the sequential update only");
+        return MVD_ERR_UNSUPPORTED;
     }
     DeviceGuard dg(c->device);
     if (!c->d_prod) MVD_TRY(dev_alloc(&c->d_prod, (size_t)c->M, "combined-update product"));

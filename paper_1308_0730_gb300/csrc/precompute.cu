@@ -151,6 +151,61 @@ __global__ void k_apply_product(float* psi, const float* prod, long n, float e, 
     }
 }
 
+// partial overlap: weights must lie in [0, 1]
+__global__ void k_check_unit(const float* w, long n, int* bad) {
+    int b = 0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float x = w[i];
+        if (!(x >= 0.f && x <= 1.f)) b = 1;
+    }
+    if (b) atomicOr(bad, 1);
+}
+
+// per voxel the number of views with w > 0: sums over the covered voxels
+// (stats[0] covered voxels, stats[1] sum of counts) and the minimum count
+__global__ void k_overlap_stats(const float* w, int nv, long M, unsigned long long* stats, int* mincount) {
+    __shared__ unsigned long long s_cov, s_sum;
+    __shared__ int s_min;
+    if (threadIdx.x == 0) {
+        s_cov = 0;
+        s_sum = 0;
+        s_min = 1 << 30;
+    }
+    __syncthreads();
+    unsigned long long cov = 0, sum = 0;
+    int mn = 1 << 30;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < M; i += (long)gridDim.x * blockDim.x) {
+        int n = 0;
+        for (int v = 0; v < nv; ++v) n += w[(size_t)v * M + i] > 0.f;
+        if (n > 0) {
+            ++cov;
+            sum += n;
+            mn = min(mn, n);
+        }
+    }
+    atomicAdd(&s_cov, cov);
+    atomicAdd(&s_sum, sum);
+    atomicMin(&s_min, mn);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(stats, s_cov);
+        atomicAdd(stats + 1, s_sum);
+        atomicMin(mincount, s_min);
+    }
+}
+
+// w_v *= min(1, T / sum_v w_v) per voxel
+__global__ void k_normalize_weights(float* w, int nv, long M, float T) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < M; i += (long)gridDim.x * blockDim.x) {
+        float S = 0.f;
+        for (int v = 0; v < nv; ++v) S += w[(size_t)v * M + i];
+        if (S > T) {
+            const float f = T / S;
+            for (int v = 0; v < nv; ++v) w[(size_t)v * M + i] *= f;
+        }
+    }
+}
+
 __global__ void k_fill(float* p, long n, float v) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -245,6 +300,24 @@ mvd_status apply_product(float* psi, const float* prod, long n, float e, float e
     k_apply_product<<<grid_stride_blocks(n), kThreads, 0, st>>>(psi, prod, n, e, eps);
     count_launch();
     return check_launch("apply product");
+}
+
+mvd_status weights_check(const float* w, long n, int* d_bad, cudaStream_t st) {
+    k_check_unit<<<grid_stride_blocks(n), kThreads, 0, st>>>(w, n, d_bad);
+    count_launch();
+    return check_launch("check weights");
+}
+
+mvd_status weights_overlap(const float* w, int nv, long M, unsigned long long* d_stats, int* d_min, cudaStream_t st) {
+    k_overlap_stats<<<grid_stride_blocks(M), kThreads, 0, st>>>(w, nv, M, d_stats, d_min);
+    count_launch();
+    return check_launch("overlap counts");
+}
+
+mvd_status weights_normalize(float* w, int nv, long M, float T, cudaStream_t st) {
+    k_normalize_weights<<<grid_stride_blocks(M), kThreads, 0, st>>>(w, nv, M, T);
+    count_launch();
+    return check_launch("normalise weights");
 }
 
 mvd_status fill(float* p, long n, float v, cudaStream_t st) {

@@ -31,7 +31,8 @@ EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_s
            "mvd_profile_enable", "mvd_profile_read", "mvd_update_direct_noalloc", "mvd_batch_create",
            "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy", "mvd_unrolled_forward",
            "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp", "mvd_autotune",
-           "mvd_batch_create_mode", "mvd_batch_mode", "mvd_iterate_combined"]
+           "mvd_batch_create_mode", "mvd_batch_mode", "mvd_iterate_combined",
+           "mvd_set_weights", "mvd_get_weights"]
 
 
 class MvdError(RuntimeError):
@@ -77,6 +78,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_iterate.argtypes = [vp, ci, ctypes.POINTER(ci), ci]
     lib.mvd_iterate_combined.argtypes = [vp, ci, ci]
     lib.mvd_iterate_combined.restype = ci
+    lib.mvd_set_weights.argtypes = [vp, ctypes.POINTER(vp), ci, ci, ctypes.c_float, _FP]
+    lib.mvd_set_weights.restype = ci
+    lib.mvd_get_weights.argtypes = [vp, ci, _FP, sz]
+    lib.mvd_get_weights.restype = ci
     lib.mvd_result.argtypes = [vp, _FP, sz]
     lib.mvd_result_device.argtypes = [vp, ctypes.POINTER(vp)]
     lib.mvd_synchronize.argtypes = [vp]
@@ -231,6 +236,32 @@ def mvd_iterate(ctx, n_iter: int, schedule=None):
 def mvd_iterate_combined(ctx, n_iter: int, root: bool = True):
     """Combined update (all views' factors from the same estimate); ``root`` takes their geometric mean."""
     _check(load().mvd_iterate_combined(ctx, int(n_iter), 1 if root else 0))
+
+
+WEIGHT_NORMS = {"sum1": 0, "min_overlap": 1, "avg_overlap": 2, "user": 3}
+
+
+def mvd_set_weights(ctx, weights, norm="sum1", value: float = 0.0) -> float:
+    """Per-view weight images in [0, 1] (partial overlap), normalised on the device; returns the
+    normalisation target T. ``weights=None`` removes them."""
+    lib = load()
+    if weights is None:
+        _check(lib.mvd_set_weights(ctx, None, 0, 0, 0.0, None))
+        return 0.0
+    n = WEIGHT_NORMS[norm] if isinstance(norm, str) else int(norm)
+    on_dev = _is_device(weights[0])
+    keep = [w if on_dev else _host_f32(w) for w in weights]
+    ptrs = (ctypes.c_void_p * len(keep))(*[ctypes.c_void_p(int(w.data_ptr()) if on_dev else w.ctypes.data)
+                                            for w in keep])
+    T = ctypes.c_float()
+    _check(lib.mvd_set_weights(ctx, ptrs, 1 if on_dev else 0, n, float(value), ctypes.byref(T)))
+    return float(T.value)
+
+
+def mvd_get_weights(ctx, v: int, shape_zyx) -> np.ndarray:
+    out = np.empty(shape_zyx, dtype=np.float32)
+    _check(load().mvd_get_weights(ctx, int(v), out.ctypes.data_as(_FP), out.size))
+    return out
 
 
 def mvd_result(ctx, out: np.ndarray):
@@ -388,6 +419,12 @@ class Deconvolver:
 
     def iterate(self, n_iter, schedule=None):
         mvd_iterate(self.ctx, n_iter, schedule)
+
+    def set_weights(self, weights, norm="sum1", value=0.0) -> float:
+        return mvd_set_weights(self.ctx, weights, norm, value)
+
+    def weights(self, v):
+        return mvd_get_weights(self.ctx, v, self.shape)
 
     def iterate_combined(self, n_iter, root=True):
         mvd_iterate_combined(self.ctx, n_iter, root)

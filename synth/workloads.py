@@ -234,6 +234,21 @@ def ellipsoids_truth(rng, dims, n, radii_range, intensity_range, workers: int = 
     return vol
 
 
+def blend_weights(dims, lo, hi, border) -> np.ndarray:
+    """Blending image of a view that covers the box [lo, hi) of the volume
+    (x, y, z): 1 inside, rising from 0 over `border` voxels at each face of the
+    box following half a cosine period, 0 outside; the product over the axes.
+    Returns float32 [Z][Y][X]."""
+    axes = []
+    for n, a, b, w in zip(dims, lo, hi, border):
+        i = np.arange(n)
+        d = np.minimum(i - a, b - 1 - i).astype(np.float64)  # voxels from the nearest face, inside
+        ramp = 0.5 * (1.0 - np.cos(np.pi * (d + 1.0) / (w + 1.0))) if w > 0 else np.ones(n)
+        axes.append(np.where(d < 0, 0.0, np.where(d < w, ramp, 1.0)))
+    wx, wy, wz = axes
+    return (wz[:, None, None] * wy[None, :, None] * wx[None, None, :]).astype(np.float32)
+
+
 # ----------------------------------------------------------------------------
 # imaging model
 # ----------------------------------------------------------------------------
