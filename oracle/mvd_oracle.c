@@ -374,13 +374,18 @@ double mvdo_normalize_weights(int n_views, const double* const* w, const int dim
     return T;
 }
 
-/* Sequential deconvolution with (already normalised) view weights: each view
- * update applies the fraction w_v of the change the Richardson-Lucy step
- * suggests, psi <- max(psi + w_v (psi c_v - psi), eps) = max(psi (1 + w_v (c_v - 1)), eps).
- * Otherwise as mvdo_deconvolve (default schedule). Returns eps, or -1. */
+/* Sequential deconvolution with (already normalised) view weights and an
+ * optional Tikhonov regularisation. The paper applies Tikhonov regularisation
+ * (lambda) without printing its update; this oracle takes the one-step-late
+ * MAP-EM of P. J. Green (IEEE Trans. Med. Imaging 9, 1990) with the quadratic
+ * prior lambda/2 |psi|^2, whose factor for a view is f_v = c_v / (1 + lambda psi).
+ * Each view update applies the fraction w_v of that change:
+ *   psi <- max(psi + w_v (psi f_v - psi), eps) = max(psi (1 + w_v (f_v - 1)), eps).
+ * weights == NULL means w_v = 1. Otherwise as mvdo_deconvolve (default
+ * schedule). Returns eps, or -1. */
 double mvdo_deconvolve_weighted(int n_views, const double* const* views, const double* const* psfs,
                                 const int* pdims, const int dims[3], int variant, int n_iter,
-                                const double* const* weights, double eps, int init, double* psi) {
+                                const double* const* weights, double lambda, double eps, int init, double* psi) {
     const long M = (long)dims[0] * dims[1] * dims[2];
     double psi0 = mvdo_mean_views(n_views, views, dims);
     if (eps <= 0.0) eps = 1e-4 * psi0;
@@ -412,7 +417,11 @@ double mvdo_deconvolve_weighted(int n_views, const double* const* views, const d
             for (long i = 0; i < M; ++i) r[i] = views[v][i] / fmax(b[i], eps);
             mvdo_conv(r, dims, comp[v], pd, c);
 #pragma omp parallel for schedule(static)
-            for (long i = 0; i < M; ++i) psi[i] = fmax(psi[i] + weights[v][i] * (psi[i] * c[i] - psi[i]), eps);
+            for (long i = 0; i < M; ++i) {
+                const double f = c[i] / (1.0 + lambda * psi[i]);
+                const double w = weights ? weights[v][i] : 1.0;
+                psi[i] = fmax(psi[i] + w * (psi[i] * f - psi[i]), eps);
+            }
         }
     }
     for (int v = 0; v < n_views; ++v) {

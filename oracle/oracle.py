@@ -66,7 +66,7 @@ def _load():
             lib.mvdo_normalize_weights.restype = ctypes.c_double
             lib.mvdo_deconvolve_weighted.argtypes = [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D), _I, _I,
                                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D),
-                                                     ctypes.c_double, ctypes.c_int, _D]
+                                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]
             lib.mvdo_deconvolve_weighted.restype = ctypes.c_double
             lib.mvdo_update_at.argtypes = [_D, _D, _D, _I, _D, _I, _I, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_long), ctypes.c_int, _D]
@@ -236,21 +236,26 @@ def normalize_weights(weights, norm="sum1", value=0.0):
     return out, T
 
 
-def deconvolve_weighted(views, psfs, n_iter, weights, variant="efficient", eps=0.0, psi_init=None):
-    """Sequential deconvolution where view v's update applies the fraction weights[v] (normalised)
-    of the Richardson-Lucy change. Returns ``(psi, eps_used)``."""
+def deconvolve_weighted(views, psfs, n_iter, weights=None, variant="efficient", eps=0.0, psi_init=None,
+                        lam=0.0):
+    """Sequential deconvolution where view v's update applies the fraction weights[v] (normalised;
+    None = all 1) of the change, with the Tikhonov regularisation ``lam`` in Green's one-step-late
+    form (factor c / (1 + lam psi)). Returns ``(psi, eps_used)``."""
     var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     vs = [_f64(v) for v in views]
-    ws = [_f64(w) for w in weights]
     ps, parr, pd = _psf_arrays(psfs)
     varr = (_D * len(vs))(*[_dptr(v) for v in vs])
-    warr = (_D * len(ws))(*[_dptr(w) for w in ws])
+    if weights is None:
+        ws, warr = [], None
+    else:
+        ws = [_f64(w) for w in weights]
+        warr = (_D * len(ws))(*[_dptr(w) for w in ws])
     if psi_init is None:
         psi, init = np.empty_like(vs[0]), 0
     else:
         psi, init = _f64(psi_init).copy(), 1
     used = _load().mvdo_deconvolve_weighted(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), warr,
-                                            float(eps), init, _dptr(psi))
+                                            float(lam), float(eps), init, _dptr(psi))
     if used < 0:
         raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
     return psi, used

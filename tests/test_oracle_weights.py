@@ -89,3 +89,42 @@ def test_noise_free_truth_is_a_fixed_point_for_any_weights():
     ws, _ = oracle.normalize_weights([rng.uniform(0, 1, truth.shape) for _ in views], "min_overlap")
     a, _ = oracle.deconvolve_weighted(views, psfs, 3, ws, "efficient", psi_init=truth)
     assert np.abs(a - truth).max() <= 1e-10 * truth.max()
+
+
+# ---------------------------------------------------------------------------
+# Tikhonov regularisation (Green's one-step-late form, factor c / (1 + lambda psi))
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", ["plain", "efficient"])
+def test_zero_lambda_is_the_unregularised_method(variant):
+    views, psfs, _ = _case()
+    a, _ = oracle.deconvolve_weighted(views, psfs, 3, None, variant, lam=0.0)
+    b, _ = oracle.deconvolve(views, psfs, 3, variant)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("lam", [0.0006, 0.006, 0.06])
+def test_constant_data_converge_to_the_closed_form(lam):
+    """Spatially constant views phi with normalised PSFs: every blur of a constant is the constant,
+    so the update is psi <- phi / (1 + lam psi), whose fixed point solves lam psi^2 + psi - phi = 0."""
+    phi = 40.0
+    views = [np.full((6, 5, 4), phi) for _ in range(2)]
+    psfs = [np.ones((3, 3, 3)), np.ones((1, 3, 5))]
+    psi, _ = oracle.deconvolve_weighted(views, psfs, 200, None, "efficient", lam=lam)
+    want = (-1.0 + np.sqrt(1.0 + 4.0 * lam * phi)) / (2.0 * lam)
+    assert np.abs(psi - want).max() <= 1e-10 * want
+
+
+def test_regularisation_with_weights_applies_the_fraction_of_the_regularised_change():
+    views, psfs, truth = _case(noise_free=True)
+    start = np.full_like(truth, truth.mean())
+    rng = np.random.default_rng(8)
+    wv = rng.uniform(0, 1, truth.shape)
+    zero = np.zeros_like(truth)
+    one = np.ones_like(truth)
+    lam = 0.006
+    full, eps = oracle.deconvolve_weighted(views, psfs, 1, [one, zero, zero], "efficient", psi_init=start, lam=lam)
+    part, _ = oracle.deconvolve_weighted(views, psfs, 1, [wv, zero, zero], "efficient", eps=eps, psi_init=start,
+                                         lam=lam)
+    want = start + wv * (full - start)
+    assert np.abs(part - want).max() <= 1e-12 * np.abs(want).max()
