@@ -163,6 +163,20 @@ mvd_status mvd_iterate(mvd_ctx* ctx, int n_iter, const int* schedule, int schedu
  * for a context with weights. Synchronises the stream.
  * mvd_get_weights copies view v's normalised weights (X*Y*Z floats) to host.
  */
+/*
+ * Tikhonov regularisation of the sequential update (the paper's lambda,
+ * 0.0006 to 0.06 in its experiments; it prints no update rule). This library
+ * uses the one-step-late MAP-EM of P. J. Green (IEEE Trans. Med. Imaging 9,
+ * 1990) with the quadratic prior lambda/2 |psi|^2: each view update's factor
+ * becomes c_v / (1 + lambda psi), i.e.
+ *   psi = max(psi (1 + w_v (c_v / (1 + lambda psi) - 1)), eps)
+ * with the view weight w_v (1 without weights). lambda must be finite and
+ * >= 0 (0 = none, the default). The combined update, the unrolled
+ * differentiation and the persistent batch kernel return MVD_ERR_UNSUPPORTED
+ * for lambda > 0.
+ */
+mvd_status mvd_set_regularization(mvd_ctx* ctx, float lambda);
+
 typedef enum {
     MVD_WEIGHTS_SUM_ONE = 0,
     MVD_WEIGHTS_MIN_OVERLAP = 1,

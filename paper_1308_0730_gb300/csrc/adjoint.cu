@@ -696,8 +696,8 @@ mvd_status mvd_unrolled_forward(mvd_ctx* c, int n_iter) {
         set_error("mvd_unrolled_forward: n_iter < 0");
         return MVD_ERR_ARG;
     }
-    if (c->d_w) {
-        set_error("mvd_unrolled_forward: not defined for a context with view weights");
+    if (c->d_w || c->lambda != 0.f) {
+        set_error("mvd_unrolled_forward: not defined for a context with view weights or regularisation");
         return MVD_ERR_UNSUPPORTED;
     }
     int prev = -1;

@@ -98,7 +98,7 @@ mvd_status fft_z_mul(const FftGeom& g, float2* S, const float2* K, cudaStream_t 
 mvd_status fft_z_forward_scaled(const FftGeom& g, float2* S, float scale, cudaStream_t st);
 mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
 mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
-                        const float* wt = nullptr);  // wt: per-voxel weights of the change, or none
+                        const float* wt = nullptr, float lam = 0.f);  // weights of the change, Tikhonov lambda
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
 // combined update: acc *= c, c the back-projected factor of the spectrum of (r - 1) * K (+ 1)
 mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st);
@@ -118,7 +118,7 @@ mvd_status dd_x_inverse_real(const FftGeom& g, const cdd* S2, float* dst, cudaSt
 bool dd_fast_x(const FftGeom& g);
 // update pass reading the double-float spectrum (rounded to FP32)
 mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                           const float* wt = nullptr);
+                           const float* wt = nullptr, float lam = 0.f);
 
 // register-resident variants for power-of-two lengths (fft_fast.cu)
 bool fft_fast_supported(int L);
@@ -129,10 +129,10 @@ mvd_status fft_z_mul_fast(const FftGeom& g, float2* S, const float2* K, cudaStre
 mvd_status fft_z_forward_scaled_fast(const FftGeom& g, float2* S, float scale, cudaStream_t st);
 mvd_status fft_x_ratio_fast(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
 mvd_status fft_x_update_fast(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
-                             const float* wt = nullptr);
+                             const float* wt = nullptr, float lam = 0.f);
 mvd_status fft_inverse_real_fast(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
 mvd_status fft_x_update_dd_fast(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                                const float* wt = nullptr);
+                                const float* wt = nullptr, float lam = 0.f);
 
 // Direct (spatial) periodic convolution with fused epilogues.
 bool direct_supported(const int kd[3]);
@@ -141,7 +141,8 @@ bool direct_supported(const int kd[3]);
 mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, const int kd[3],
                         const float* phi, float eps, float* r, cudaStream_t st, int ty = 0);
 mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
-                         float* psi, float eps, cudaStream_t st, int ty = 0, const float* wt = nullptr);
+                         float* psi, float eps, cudaStream_t st, int ty = 0, const float* wt = nullptr,
+                         float lam = 0.f);
 int direct_tile_heights(const int kd[3], int out[4]);  // tile heights that fit, largest first
 // prod *= r * k (the combined update's product of view factors)
 mvd_status direct_accumulate(const int dims[3], const float* r, const float* k, const int kd[3], float* prod,
@@ -233,6 +234,7 @@ struct mvd_ctx {
     float* d_prod = nullptr;  // combined update: product of the view factors (M)
     float* d_w = nullptr;     // partial overlap: normalised weights of every view (nv * M), or none
     float weight_norm = 0.f;  // the normalisation target T of the weights
+    float lambda = 0.f;       // Tikhonov regularisation of the sequential update (0 = none)
     int path = MVD_PATH_AUTO;
     float psi0 = 0.f, eps = 0.f;
 };

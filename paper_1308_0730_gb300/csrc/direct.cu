@@ -9,6 +9,7 @@
 // shared memory; every thread accumulates TZ outputs along z, so each input
 // value it loads feeds up to TZ FMAs.
 #include "common.cuh"
+#include "fft.cuh"
 
 namespace mvd {
 
@@ -38,6 +39,7 @@ struct DArgs {
     float* out;  // r (ratio), psi (update) or plain output
     float eps;
     const float* wt;  // update: when set, apply the fraction wt of the change (partial overlap)
+    float lam;        // update: Tikhonov regularisation (0 = none)
 };
 
 // MODE 0: out = phi / max(conv, eps); MODE 1: out = max(out . conv, eps); MODE 2: out = conv;
@@ -97,7 +99,11 @@ __global__ void __launch_bounds__(TX * TY) k_direct(DArgs a) {
         if (MODE == 0)
             a.out[g] = __ldg(a.phi + g) / fmaxf(acc[o], a.eps);
         else if (MODE == 1)
-            a.out[g] = fmaxf(a.out[g] * (a.wt ? 1.f + __ldg(a.wt + g) * (acc[o] - 1.f) : acc[o]), a.eps);
+        {
+            const float p = a.out[g];
+            a.out[g] = fmaxf(p * (a.wt || a.lam != 0.f ? update_factor(acc[o] - 1.f, p, a.wt, g, a.lam) : acc[o]),
+                             a.eps);
+        }
         else if (MODE == 2)
             a.out[g] = acc[o];
         else if (MODE == 3)
@@ -172,11 +178,12 @@ mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, con
 }
 
 mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
-                         float* psi, float eps, cudaStream_t st, int ty, const float* wt) {
+                         float* psi, float eps, cudaStream_t st, int ty, const float* wt, float lam) {
     DArgs a = make(dims, r, k, kd);
     a.out = psi;
     a.eps = eps;
     a.wt = wt;
+    a.lam = lam;
     return launch<1>(a, kd, st, "direct update", ty);
 }
 

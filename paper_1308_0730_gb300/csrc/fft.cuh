@@ -31,6 +31,16 @@ __device__ __forceinline__ float2 mul_si(float2 a) {
     return S < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
 }
 
+// Factor the sequential update multiplies psi by, from v = c - 1 (c the view's
+// back-projected ratio): with view weight w and Tikhonov lambda (one-step-late
+// form, factor c / (1 + lambda psi)) it is 1 + w (c / (1 + lambda psi) - 1)
+// = 1 + w (v - lambda psi) / (1 + lambda psi); plainly 1 + v.
+__device__ __forceinline__ float update_factor(float v, float psi, const float* wt, long i, float lam) {
+    if (!wt && lam == 0.f) return v + 1.f;
+    const float w = wt ? __ldg(wt + i) : 1.f;
+    return lam == 0.f ? 1.f + w * v : 1.f + w * (v - lam * psi) / (1.f + lam * psi);
+}
+
 // exp(s 2 pi i m / L) from the forward table tw[m] = exp(-2 pi i m / L)
 template <int S>
 __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int m) {

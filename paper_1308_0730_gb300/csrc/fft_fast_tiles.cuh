@@ -91,6 +91,7 @@ struct XFast {
     const float2* tw;
     const cdd* spec2;  // when set, the update reads this double-float spectrum (rounded to FP32)
     const float* wt;   // when set, the update applies the fraction wt of the change (partial overlap)
+    float lam;         // Tikhonov regularisation of the update (0 = none)
 };
 
 // write the packed forward spectra (natural order in registers) as the two
@@ -231,11 +232,9 @@ __device__ __forceinline__ void fast_x_inverse_tile(const XFast& a, long tile, f
         for (int q = 0; q < kE; ++q) {
             const int n = t + TPL * q;
             if (MODE == 1) {
-                // v = c - 1; with a weight the fraction wt of the change: psi (1 + wt (c - 1))
-                const float fa = a.wt && oka ? 1.f + __ldg(a.wt + ra + n) * v[q].x : v[q].x + 1.f;
-                const float fb = a.wt && okb ? 1.f + __ldg(a.wt + rb + n) * v[q].y : v[q].y + 1.f;
-                if (oka) a.psi[ra + n] = fmaxf(w[q].x * fa, a.eps);
-                if (okb) a.psi[rb + n] = fmaxf(w[q].y * fb, a.eps);
+                // v = c - 1 (weights and regularisation: update_factor)
+                if (oka) a.psi[ra + n] = fmaxf(w[q].x * update_factor(v[q].x, w[q].x, a.wt, ra + n, a.lam), a.eps);
+                if (okb) a.psi[rb + n] = fmaxf(w[q].y * update_factor(v[q].y, w[q].y, a.wt, rb + n, a.lam), a.eps);
             } else if (MODE == 4) {  // combined update: multiply this view's factor into the product
                 if (oka) a.psi[ra + n] = w[q].x * (v[q].x + 1.f);
                 if (okb) a.psi[rb + n] = w[q].y * (v[q].y + 1.f);

@@ -52,6 +52,7 @@ struct GenX {
     float eps;
     const cdd* S2in;   // when set, the update reads this double-float spectrum (rounded to FP32)
     const float* wt;   // when set, the update applies the fraction wt of the change (partial overlap)
+    float lam;         // Tikhonov regularisation of the update (0 = none)
 };
 
 __host__ __device__ inline GenX gen_x_args(int X, long YZ, const FftPlan& plan) {
@@ -193,8 +194,10 @@ __device__ void gen_x_inverse_tile(const GenX& a, long tile, float2* sm) {
         const int p = row < a.P ? row : row - a.P;
         const float c = reinterpret_cast<const float*>(R + p * a.ls + n)[row < a.P ? 0 : 1];
         float* dst = a.psi + (rho0 + row) * a.X + n;
-        if (MODE == 1)  // c here is (r - 1) * K: the factor is c + 1 (K sums to 1), weighted 1 + wt c
-            *dst = fmaxf(ld1<CO>(dst) * (a.wt ? 1.f + __ldg(a.wt + (rho0 + row) * a.X + n) * c : c + 1.f), a.eps);
+        if (MODE == 1) {  // c here is (r - 1) * K: the factor is c + 1 (K sums to 1), see update_factor
+            const float old = ld1<CO>(dst);
+            *dst = fmaxf(old * update_factor(c, old, a.wt, (rho0 + row) * a.X + n, a.lam), a.eps);
+        }
         else if (MODE == 4)
             *dst = ld1<CO>(dst) * (c + 1.f);
         else

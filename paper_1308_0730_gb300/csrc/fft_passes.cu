@@ -84,22 +84,24 @@ mvd_status fft_x_ratio_generic(const FftGeom& g, float2* S, const float* phi, fl
 }
 
 mvd_status fft_x_update_generic(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
-                                const float* wt) {
+                                const float* wt, float lam) {
     GenX a = make_x(g);
     a.S = const_cast<float2*>(S);
     a.psi = psi;
     a.eps = eps;
     a.wt = wt;
+    a.lam = lam;
     return launch(k_x_inverse<1>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
 }
 
 mvd_status fft_x_update_dd_generic(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                                   const float* wt) {
+                                   const float* wt, float lam) {
     GenX a = make_x(g);
     a.S2in = S2;
     a.psi = psi;
     a.eps = eps;
     a.wt = wt;
+    a.lam = lam;
     return launch(k_x_inverse<1>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
 }
 
@@ -147,14 +149,14 @@ mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps,
     return fft_x_ratio_generic(g, S, phi, eps, st);
 }
 mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
-                        const float* wt) {
-    if (g.fast && fft_fast_supported(g.X)) return fft_x_update_fast(g, S, psi, eps, st, wt);
-    return fft_x_update_generic(g, S, psi, eps, st, wt);
+                        const float* wt, float lam) {
+    if (g.fast && fft_fast_supported(g.X)) return fft_x_update_fast(g, S, psi, eps, st, wt, lam);
+    return fft_x_update_generic(g, S, psi, eps, st, wt, lam);
 }
 mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                           const float* wt) {
-    if (g.fast && fft_fast_supported(g.X)) return fft_x_update_dd_fast(g, S2, psi, eps, st, wt);
-    return fft_x_update_dd_generic(g, S2, psi, eps, st, wt);
+                           const float* wt, float lam) {
+    if (g.fast && fft_fast_supported(g.X)) return fft_x_update_dd_fast(g, S2, psi, eps, st, wt, lam);
+    return fft_x_update_dd_generic(g, S2, psi, eps, st, wt, lam);
 }
 mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st) {
     if (g.fast && fft_fast_supported(g.X)) return fft_x_accumulate_fast(g, S, acc, st);

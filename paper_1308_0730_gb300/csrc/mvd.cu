@@ -412,7 +412,7 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
                              c->direct_ty));
         if (prod) return direct_accumulate(c->dims, c->d_r, c->d_comp + c->koff[v], kd, prod, c->stream, c->direct_ty);
         return direct_update(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_psi, c->eps, c->stream,
-                             c->direct_ty, wt);
+                             c->direct_ty, wt, c->lambda);
     }
     const FftGeom& g = c->geom;
     const size_t ns = (size_t)g.Xh * g.YZ;
@@ -430,7 +430,7 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
         MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
         MVD_TRY(dd_y(g, S2, 1, c->stream));
         if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream);
-        return fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt);
+        return fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt, c->lambda);
     }
     const float2* Kp = c->d_K + ns * (2 * v);
     const float2* Kc = c->d_K + ns * (2 * v + 1);
@@ -443,7 +443,7 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
     MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
     MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
     if (prod) return fft_x_accumulate(g, c->d_S, prod, c->stream);
-    return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream, wt);
+    return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream, wt, c->lambda);
 }
 
 namespace {
@@ -917,6 +917,22 @@ mvd_status mvd_set_weights(mvd_ctx* c, const float* const* weights, int on_devic
     return st;
 }
 
+mvd_status mvd_set_regularization(mvd_ctx* c, float lambda) {
+    clear_error();
+    if (!c) {
+        set_error("mvd_set_regularization: NULL context");
+        return MVD_ERR_ARG;
+    }
+    if (!(lambda >= 0.f) || !(lambda < 1e30f)) {
+        set_error("mvd_set_regularization: lambda must be finite and >= 0");
+        return MVD_ERR_ARG;
+    }
+    DeviceGuard dg(c->device);
+    drop_graphs(c);  // the captured update passes carry lambda
+    c->lambda = lambda;
+    return MVD_OK;
+}
+
 mvd_status mvd_get_weights(mvd_ctx* c, int v, float* out, size_t n_elems) {
     clear_error();
     if (!c || !out) {
@@ -952,8 +968,8 @@ mvd_status mvd_iterate_combined(mvd_ctx* c, int n_iter, int root) {
         set_error("mvd_iterate_combined: n_iter < 0");
         return MVD_ERR_ARG;
     }
-    if (c->d_w) {
-        set_error("mvd_iterate_combined: view weights apply to the sequential update only");
+    if (c->d_w || c->lambda != 0.f) {
+        set_error("mvd_iterate_combined: view weights and regularisation apply to the sequential update only");
         return MVD_ERR_UNSUPPORTED;
     }
     DeviceGuard dg(c->device);

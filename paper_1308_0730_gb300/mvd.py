@@ -32,7 +32,7 @@ EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_s
            "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy", "mvd_unrolled_forward",
            "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp", "mvd_autotune",
            "mvd_batch_create_mode", "mvd_batch_mode", "mvd_iterate_combined",
-           "mvd_set_weights", "mvd_get_weights"]
+           "mvd_set_weights", "mvd_get_weights", "mvd_set_regularization"]
 
 
 class MvdError(RuntimeError):
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_set_weights.argtypes = [vp, ctypes.POINTER(vp), ci, ci, ctypes.c_float, _FP]
     lib.mvd_set_weights.restype = ci
     lib.mvd_get_weights.argtypes = [vp, ci, _FP, sz]
+    lib.mvd_set_regularization.argtypes = [vp, ctypes.c_float]
+    lib.mvd_set_regularization.restype = ci
     lib.mvd_get_weights.restype = ci
     lib.mvd_result.argtypes = [vp, _FP, sz]
     lib.mvd_result_device.argtypes = [vp, ctypes.POINTER(vp)]
@@ -258,6 +260,11 @@ def mvd_set_weights(ctx, weights, norm="sum1", value: float = 0.0) -> float:
     return float(T.value)
 
 
+def mvd_set_regularization(ctx, lam: float):
+    """Tikhonov regularisation of the sequential update (one-step-late form, factor c / (1 + lam psi))."""
+    _check(load().mvd_set_regularization(ctx, float(lam)))
+
+
 def mvd_get_weights(ctx, v: int, shape_zyx) -> np.ndarray:
     out = np.empty(shape_zyx, dtype=np.float32)
     _check(load().mvd_get_weights(ctx, int(v), out.ctypes.data_as(_FP), out.size))
@@ -422,6 +429,9 @@ class Deconvolver:
 
     def set_weights(self, weights, norm="sum1", value=0.0) -> float:
         return mvd_set_weights(self.ctx, weights, norm, value)
+
+    def set_regularization(self, lam):
+        mvd_set_regularization(self.ctx, lam)
 
     def weights(self, v):
         return mvd_get_weights(self.ctx, v, self.shape)

@@ -104,3 +104,48 @@ def test_weights_reject_bad_input_and_unsupported_forms(mvd):
         with pytest.raises(mvd.MvdError) as e:
             mvd.mvd_set_weights(d.ctx, raw, "user", 0.0)
         assert e.value.status == mvd.MVD_ERR_ARG
+
+
+# ---------------------------------------------------------------------------
+# Tikhonov regularisation (one-step-late form)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("path", ["direct", "fft"])
+@pytest.mark.parametrize("lam", [0.0006, 0.006, 0.06])
+def test_regularised_deconvolution_matches_oracle(mvd, path, lam):
+    w = synth.config1()
+    want, _ = oracle.deconvolve_weighted(w.views, w.psfs, w.n_iter, None, "efficient", lam=lam)
+    with mvd.Deconvolver(w.views, w.psfs, "efficient", path=path) as d:
+        d.set_regularization(lam)
+        d.iterate(w.n_iter)
+        got = d.result().astype(np.float64)
+    assert rel_err(got, want) < PARITY_TOL, err_report(got, want)
+
+
+@pytest.mark.parametrize("path", ["direct", "fft"])
+def test_regularised_and_weighted_matches_oracle(mvd, path):
+    w = synth.small_case(52, dims=(30, 24, 20), n_views=3, n_iter=4, asymmetric=True)
+    raw = _layout(w)
+    ws, _ = oracle.normalize_weights(raw, "min_overlap")
+    want, _ = oracle.deconvolve_weighted(w.views, w.psfs, w.n_iter, ws, "efficient", lam=0.006)
+    with mvd.Deconvolver(w.views, w.psfs, "efficient", path=path) as d:
+        d.set_weights(raw, "min_overlap")
+        d.set_regularization(0.006)
+        d.iterate(w.n_iter)
+        got = d.result().astype(np.float64)
+    assert rel_err(got, want) < PARITY_TOL, err_report(got, want)
+
+
+def test_regularisation_rejects_bad_values_and_unsupported_forms(mvd):
+    w = synth.config1()
+    with mvd.Deconvolver(w.views, w.psfs, path="fft") as d:
+        for bad in (-1.0, float("nan"), float("inf")):
+            with pytest.raises(mvd.MvdError) as e:
+                d.set_regularization(bad)
+            assert e.value.status == mvd.MVD_ERR_ARG
+        d.set_regularization(0.006)
+        with pytest.raises(mvd.MvdError) as e:
+            d.iterate_combined(1)
+        assert e.value.status == mvd.MVD_ERR_UNSUPPORTED
+        d.set_regularization(0.0)
+        d.iterate_combined(1)
