@@ -329,3 +329,40 @@ def test_fast_fp32_mode(mvd):
         d.iterate(2)
         got = d.result()
     assert rel_err(got, want) < PARITY_TOL, err_report(got, want)
+
+
+# ---------------------------------------------------------------------------
+# concurrency and extreme shapes
+# ---------------------------------------------------------------------------
+
+def test_two_contexts_on_two_streams_run_concurrently(mvd):
+    """Two problems enqueued on two streams at once give the same results as alone (no shared
+    mutable state between contexts)."""
+    import torch
+
+    wa = synth.small_case(61, dims=(40, 32, 24), n_views=3, n_iter=4, asymmetric=True)
+    wb = synth.config1()
+    alone = []
+    for w in (wa, wb):
+        with mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft") as d:
+            d.iterate(w.n_iter)
+            alone.append(d.result())
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    with mvd.Deconvolver(wa.views, wa.psfs, "efficient", path="fft", stream=sa) as da, \
+            mvd.Deconvolver(wb.views, wb.psfs, "efficient", path="fft", stream=sb) as db:
+        for i in range(max(wa.n_iter, wb.n_iter)):  # interleaved, one iteration at a time
+            if i < wa.n_iter:
+                da.iterate(1)
+            if i < wb.n_iter:
+                db.iterate(1)
+        ra, rb = da.result(), db.result()
+    assert rel_err(ra, alone[0]) < 1e-6 and rel_err(rb, alone[1]) < 1e-6
+
+
+@pytest.mark.parametrize("path", ["direct", "fft"])
+def test_psf_box_as_large_as_the_volume(mvd, path):
+    """PSF boxes spanning the whole (odd) grid: every offset wraps around the periodic volume."""
+    w = synth.small_case(62, dims=(15, 9, 25), n_views=2, boxes=[(15, 9, 25), (15, 9, 25)], n_iter=3)
+    want, _ = oracle.deconvolve(w.views, w.psfs, w.n_iter, "efficient")
+    got, _, _ = _run_gpu(mvd, w, path=path)
+    assert rel_err(got, want) < PARITY_TOL, err_report(got, want)
