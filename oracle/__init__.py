@@ -12,6 +12,7 @@ from .oracle import (  # noqa: F401
     VARIANTS,
     build,
     conv,
+    conv_zero,
     mirror,
     kconv,
     compound,
@@ -19,6 +20,7 @@ from .oracle import (  # noqa: F401
     update_at,
     deconvolve,
     deconvolve_combined,
+    deconvolve_zero,
     deconvolve_weighted,
     normalize_weights,
     WEIGHT_NORMS,

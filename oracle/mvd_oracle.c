@@ -436,6 +436,99 @@ double mvdo_deconvolve_weighted(int n_views, const double* const* views, const d
     return bad ? -1.0 : eps;
 }
 
+/* Convolution with a zero boundary (the volume continued by zeros):
+ *   out(x) = sum_d k(d) in(x - d), terms with x - d outside the grid dropped. */
+void mvdo_conv_zero(const double* in, const int dims[3], const double* k, const int kd[3], double* out) {
+    const int X = dims[0], Y = dims[1], Z = dims[2];
+    const int hx = (kd[0] - 1) / 2, hy = (kd[1] - 1) / 2, hz = (kd[2] - 1) / 2;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < Z; ++z)
+        for (int y = 0; y < Y; ++y)
+            for (int x = 0; x < X; ++x) {
+                double s = 0.0;
+                for (int tz = 0; tz < kd[2]; ++tz) {
+                    const int sz = z - (tz - hz);
+                    if (sz < 0 || sz >= Z) continue;
+                    for (int ty = 0; ty < kd[1]; ++ty) {
+                        const int sy = y - (ty - hy);
+                        if (sy < 0 || sy >= Y) continue;
+                        for (int tx = 0; tx < kd[0]; ++tx) {
+                            const int sx = x - (tx - hx);
+                            if (sx < 0 || sx >= X) continue;
+                            s += k[tx + kd[0] * (ty + kd[1] * tz)] * in[idx3(sx, sy, sz, X, Y)];
+                        }
+                    }
+                }
+                out[idx3(x, y, z, X, Y)] = s;
+            }
+}
+
+/* Sequential deconvolution (default schedule) with zero-boundary image
+ * convolutions: b = psi * P_v and the back-projection r * P_v^comp treat the
+ * volume as surrounded by zeros. The paper's convolutions are periodic; for
+ * this forward model the update is the ML-EM step of Shepp and Vardi (1982),
+ * which divides the back-projection by the sensitivity s_v = 1 * P_v^comp
+ * (the back-projection of a field of ones, 1 in the periodic case):
+ *   psi <- max(psi (r * P_v^comp) / s_v, eps).
+ * Otherwise as mvdo_deconvolve. Returns eps, or -1. */
+double mvdo_deconvolve_zero(int n_views, const double* const* views, const double* const* psfs, const int* pdims,
+                            const int dims[3], int variant, int n_iter, double eps, int init, double* psi) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double psi0 = mvdo_mean_views(n_views, views, dims);
+    if (eps <= 0.0) eps = 1e-4 * psi0;
+    if (!init)
+        for (long i = 0; i < M; ++i) psi[i] = psi0;
+    double** pn = (double**)malloc(sizeof(double*) * n_views);
+    double** comp = (double**)malloc(sizeof(double*) * n_views);
+    int bad = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        double s = 0.0;
+        for (long i = 0; i < T; ++i) s += psfs[v][i];
+        pn[v] = (double*)malloc(sizeof(double) * T);
+        for (long i = 0; i < T; ++i) pn[v][i] = psfs[v][i] / s;
+    }
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        comp[v] = (double*)malloc(sizeof(double) * T);
+        if (mvdo_compound(n_views, (const double* const*)pn, pdims, v, variant, comp[v]) != 0) bad = 1;
+    }
+    double* b = (double*)malloc(sizeof(double) * M);
+    double* r = (double*)malloc(sizeof(double) * M);
+    double* c = (double*)malloc(sizeof(double) * M);
+    double* ones = (double*)malloc(sizeof(double) * M);
+    double** sens = (double**)malloc(sizeof(double*) * n_views);
+    for (long i = 0; i < M; ++i) ones[i] = 1.0;
+    for (int v = 0; v < n_views; ++v) {
+        sens[v] = (double*)malloc(sizeof(double) * M);
+        if (!bad) mvdo_conv_zero(ones, dims, comp[v], pdims + 3 * v, sens[v]);
+    }
+    for (int it = 0; it < n_iter && !bad; ++it) {
+        for (int v = 0; v < n_views; ++v) {
+            const int* pd = pdims + 3 * v;
+            mvdo_conv_zero(psi, dims, pn[v], pd, b);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) r[i] = views[v][i] / fmax(b[i], eps);
+            mvdo_conv_zero(r, dims, comp[v], pd, c);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) psi[i] = fmax(psi[i] * c[i] / sens[v][i], eps);
+        }
+    }
+    for (int v = 0; v < n_views; ++v) {
+        free(comp[v]);
+        free(pn[v]);
+        free(sens[v]);
+    }
+    free(comp);
+    free(pn);
+    free(sens);
+    free(ones);
+    free(b);
+    free(r);
+    free(c);
+    return bad ? -1.0 : eps;
+}
+
 /* One view update evaluated only at the listed voxels (flat indices):
  *   out[i] = max(psi(x_i) * c(x_i), eps), with c, r, b computed from the
  * definitions above on the neighbourhood each sample needs. */
