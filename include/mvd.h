@@ -82,6 +82,21 @@ typedef enum { MVD_PATH_AUTO = 0, MVD_PATH_DIRECT = 1, MVD_PATH_FFT = 2 } mvd_pa
  *     differ from an exact computation by about 1e-3 relative). */
 typedef enum { MVD_PRECISE = 0, MVD_FAST = 1 } mvd_precision;
 
+/* How the image convolutions continue the volume past its faces.
+ *   MVD_BOUNDARY_PERIODIC: periodic (circular) convolution on the X*Y*Z grid.
+ *   MVD_BOUNDARY_ZERO: the volume is continued by zeros (the camera sees
+ *     nothing of the object outside the grid). The context pads every axis
+ *     internally by the largest PSF half-width (to a {2,3,5}-smooth length),
+ *     and the update divides the back-projected ratio by the view's
+ *     sensitivity 1 * P_v^comp, which falls below 1 within a PSF half-width
+ *     of a face: the ML-EM step of Shepp and Vardi (1982) for this forward
+ *     model; inside, far from the faces, the update is the periodic one.
+ *     Estimates and results keep the X*Y*Z layout. The sequential update
+ *     only: mvd_iterate_combined, view weights, regularisation, the unrolled
+ *     (differentiable) form and the persistent batch kernel return
+ *     MVD_ERR_UNSUPPORTED on such a context. */
+typedef enum { MVD_BOUNDARY_PERIODIC = 0, MVD_BOUNDARY_ZERO = 1 } mvd_boundary;
+
 typedef struct {
     float eps;           /* floor of b and psi; <= 0 selects 1e-4 * psi0 */
     int path;            /* mvd_path */
@@ -89,10 +104,11 @@ typedef struct {
     int views_on_device; /* 1: `views` are device pointers (copied device-to-device) */
     int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
     int precision;       /* mvd_precision (FFT engine) */
+    int boundary;        /* mvd_boundary */
 } mvd_options;
 
 /* Fills *opt with eps = 0 (auto), path = AUTO, stream = NULL, host views,
- * device -1, precision = MVD_PRECISE. */
+ * device -1, precision = MVD_PRECISE, boundary = MVD_BOUNDARY_PERIODIC. */
 void mvd_default_options(mvd_options* opt);
 
 /*
@@ -200,11 +216,14 @@ mvd_status mvd_get_weights(mvd_ctx* ctx, int v, float* out, size_t n_elems);
 mvd_status mvd_iterate_combined(mvd_ctx* ctx, int n_iter, int root);
 
 /* Copies psi (X*Y*Z floats) to host memory `out`; n_elems must be >= X*Y*Z.
- * Synchronises the context's stream. */
+ * Synchronises the context's stream. With a zero boundary the estimate is
+ * first cropped out of the padded grid on the device. */
 mvd_status mvd_result(mvd_ctx* ctx, float* out, size_t n_elems);
 
-/* Hands out the device pointer of psi (borrowed; valid until the next call
- * that mutates or destroys the context). Does not synchronise. */
+/* Hands out the device pointer of psi (X*Y*Z floats, borrowed; valid until
+ * the next call that mutates or destroys the context). Does not synchronise;
+ * with a zero boundary it enqueues the crop into a staging volume (whose
+ * pointer it returns) on the context's stream. */
 mvd_status mvd_result_device(mvd_ctx* ctx, const float** dptr);
 
 /* Waits for all work enqueued on the context's stream. */

@@ -696,8 +696,9 @@ mvd_status mvd_unrolled_forward(mvd_ctx* c, int n_iter) {
         set_error("mvd_unrolled_forward: n_iter < 0");
         return MVD_ERR_ARG;
     }
-    if (c->d_w || c->lambda != 0.f) {
-        set_error("mvd_unrolled_forward: not defined for a context with view weights or regularisation");
+    if (c->d_w || c->lambda != 0.f || c->boundary != MVD_BOUNDARY_PERIODIC) {
+        set_error("mvd_unrolled_forward: not defined for a context with view weights, regularisation or a zero "
+                  "boundary");
         return MVD_ERR_UNSUPPORTED;
     }
     int prev = -1;

@@ -530,12 +530,13 @@ mvd_status mvd_batch_create_mode(mvd_ctx* const* ctxs, int n, int n_iter, int mo
     bool all_fft = true, any_weights = false;
     for (int i = 0; i < n; ++i) {
         all_fft = all_fft && ctxs[i]->path == MVD_PATH_FFT;
-        any_weights = any_weights || ctxs[i]->d_w != nullptr || ctxs[i]->lambda != 0.f;
+        any_weights = any_weights || ctxs[i]->d_w != nullptr || ctxs[i]->lambda != 0.f || ctxs[i]->boundary != 0;
     }
     const bool branches_ok = ctxs[0]->stream != nullptr && !profiling_on();
     if (mode == MVD_BATCH_AUTO) mode = branches_ok ? MVD_BATCH_BRANCHES : MVD_BATCH_PERSISTENT;
     if (mode == MVD_BATCH_PERSISTENT && any_weights) {
-        set_error("mvd_batch_create: the persistent kernel applies neither view weights nor regularisation");
+        set_error("mvd_batch_create: the persistent kernel applies neither view weights, regularisation nor the "
+                  "zero boundary");
         return MVD_ERR_UNSUPPORTED;
     }
     if (mode == MVD_BATCH_PERSISTENT && !all_fft) {

@@ -98,14 +98,20 @@ mvd_status fft_z_mul(const FftGeom& g, float2* S, const float2* K, cudaStream_t 
 mvd_status fft_z_forward_scaled(const FftGeom& g, float2* S, float scale, cudaStream_t st);
 mvd_status fft_x_ratio(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
 mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
-                        const float* wt = nullptr, float lam = 0.f);  // weights of the change, Tikhonov lambda
+                        const float* wt = nullptr, float lam = 0.f,
+                        const float* inv_s = nullptr);  // weights of the change, Tikhonov lambda, 1 / sensitivity
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
 // combined update: acc *= c, c the back-projected factor of the spectrum of (r - 1) * K (+ 1)
-mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st);
-mvd_status fft_x_accumulate_dd(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st);
-mvd_status fft_x_accumulate_generic(const FftGeom& g, const float2* S, const cdd* S2, float* acc, cudaStream_t st);
-mvd_status fft_x_accumulate_fast(const FftGeom& g, const float2* S, float* acc, cudaStream_t st);
-mvd_status fft_x_accumulate_dd_fast(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st);
+mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st,
+                            const float* inv_s = nullptr);
+mvd_status fft_x_accumulate_dd(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st,
+                               const float* inv_s = nullptr);
+mvd_status fft_x_accumulate_generic(const FftGeom& g, const float2* S, const cdd* S2, float* acc, cudaStream_t st,
+                                    const float* inv_s = nullptr);
+mvd_status fft_x_accumulate_fast(const FftGeom& g, const float2* S, float* acc, cudaStream_t st,
+                                 const float* inv_s = nullptr);
+mvd_status fft_x_accumulate_dd_fast(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st,
+                                    const float* inv_s = nullptr);
 
 // double-float forward blur (fft_dd.cu): spectrum of complex double-float
 mvd_status dd_forward_real(const FftGeom& g, const float* src, cdd* S2, cudaStream_t st);
@@ -118,7 +124,7 @@ mvd_status dd_x_inverse_real(const FftGeom& g, const cdd* S2, float* dst, cudaSt
 bool dd_fast_x(const FftGeom& g);
 // update pass reading the double-float spectrum (rounded to FP32)
 mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                           const float* wt = nullptr, float lam = 0.f);
+                           const float* wt = nullptr, float lam = 0.f, const float* inv_s = nullptr);
 
 // register-resident variants for power-of-two lengths (fft_fast.cu)
 bool fft_fast_supported(int L);
@@ -129,10 +135,10 @@ mvd_status fft_z_mul_fast(const FftGeom& g, float2* S, const float2* K, cudaStre
 mvd_status fft_z_forward_scaled_fast(const FftGeom& g, float2* S, float scale, cudaStream_t st);
 mvd_status fft_x_ratio_fast(const FftGeom& g, float2* S, const float* phi, float eps, cudaStream_t st);
 mvd_status fft_x_update_fast(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
-                             const float* wt = nullptr, float lam = 0.f);
+                             const float* wt = nullptr, float lam = 0.f, const float* inv_s = nullptr);
 mvd_status fft_inverse_real_fast(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
 mvd_status fft_x_update_dd_fast(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                                const float* wt = nullptr, float lam = 0.f);
+                                const float* wt = nullptr, float lam = 0.f, const float* inv_s = nullptr);
 
 // Direct (spatial) periodic convolution with fused epilogues.
 bool direct_supported(const int kd[3]);
@@ -142,11 +148,11 @@ mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, con
                         const float* phi, float eps, float* r, cudaStream_t st, int ty = 0);
 mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
                          float* psi, float eps, cudaStream_t st, int ty = 0, const float* wt = nullptr,
-                         float lam = 0.f);
+                         float lam = 0.f, const float* inv_s = nullptr);
 int direct_tile_heights(const int kd[3], int out[4]);  // tile heights that fit, largest first
 // prod *= r * k (the combined update's product of view factors)
 mvd_status direct_accumulate(const int dims[3], const float* r, const float* k, const int kd[3], float* prod,
-                             cudaStream_t st, int ty = 0);
+                             cudaStream_t st, int ty = 0, const float* inv_s = nullptr);
 mvd_status direct_conv(const int dims[3], const float* in, const float* k, const int kd[3],
                        float* out, cudaStream_t st);
 
@@ -163,6 +169,11 @@ mvd_status autocorr_kernel(const float* P, const int kd[3], float* Q, cudaStream
 mvd_status direct_conv_add(const int dims[3], const float* in, const float* k, const int kd[3], float* out,
                            cudaStream_t st);
 mvd_status one_update(mvd_ctx* c, int v);
+// zero boundary (boundary.cu)
+mvd_status pad_volume(const mvd_ctx* c, const float* user, float* padded, cudaStream_t st);
+mvd_status crop_volume(const mvd_ctx* c, const float* padded, float* user, cudaStream_t st);
+mvd_status clear_padding(const mvd_ctx* c, float* padded, cudaStream_t st);
+mvd_status compute_inverse_sensitivity(mvd_ctx* c);
 // view v's pass from the current estimate: with prod == nullptr the
 // sequential update psi = max(psi . c_v, eps); else prod *= c_v
 mvd_status view_pass(mvd_ctx* c, int v, float* prod);
@@ -235,6 +246,14 @@ struct mvd_ctx {
     float* d_w = nullptr;     // partial overlap: normalised weights of every view (nv * M), or none
     float weight_norm = 0.f;  // the normalisation target T of the weights
     float lambda = 0.f;       // Tikhonov regularisation of the sequential update (0 = none)
+
+    // zero boundary: the engines run on a padded grid (dims, M); the user's
+    // volume (udims, uM) sits in its low corner
+    int boundary = 0;                 // mvd_boundary
+    int udims[3] = {0, 0, 0};
+    long uM = 0;
+    float* d_invs = nullptr;  // 1 / sensitivity per view (nv padded volumes)
+    float* d_stage = nullptr; // user-layout staging volume (uM)
     int path = MVD_PATH_AUTO;
     float psi0 = 0.f, eps = 0.f;
 };

@@ -40,6 +40,7 @@ struct DArgs {
     float eps;
     const float* wt;  // update: when set, apply the fraction wt of the change (partial overlap)
     float lam;        // update: Tikhonov regularisation (0 = none)
+    const float* inv_s;  // update / accumulate: zero boundary, 1 / sensitivity
 };
 
 // MODE 0: out = phi / max(conv, eps); MODE 1: out = max(out . conv, eps); MODE 2: out = conv;
@@ -101,7 +102,9 @@ __global__ void __launch_bounds__(TX * TY) k_direct(DArgs a) {
         else if (MODE == 1)
         {
             const float p = a.out[g];
-            a.out[g] = fmaxf(p * (a.wt || a.lam != 0.f ? update_factor(acc[o] - 1.f, p, a.wt, g, a.lam) : acc[o]),
+            a.out[g] = fmaxf(p * (a.wt || a.lam != 0.f || a.inv_s ? update_factor(acc[o] - 1.f, p, a.wt, g, a.lam,
+                                                                                    a.inv_s)
+                                                                   : acc[o]),
                              a.eps);
         }
         else if (MODE == 2)
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(TX * TY) k_direct(DArgs a) {
         else if (MODE == 3)
             a.out[g] += acc[o];
         else  // MODE 4: combined update, multiply this view's factor into the product
-            a.out[g] *= acc[o];
+            a.out[g] *= a.inv_s ? acc[o] * __ldg(a.inv_s + g) : acc[o];
     }
 }
 
@@ -178,19 +181,22 @@ mvd_status direct_ratio(const int dims[3], const float* psi, const float* k, con
 }
 
 mvd_status direct_update(const int dims[3], const float* r, const float* k, const int kd[3],
-                         float* psi, float eps, cudaStream_t st, int ty, const float* wt, float lam) {
+                         float* psi, float eps, cudaStream_t st, int ty, const float* wt, float lam,
+                         const float* inv_s) {
     DArgs a = make(dims, r, k, kd);
     a.out = psi;
     a.eps = eps;
     a.wt = wt;
     a.lam = lam;
+    a.inv_s = inv_s;
     return launch<1>(a, kd, st, "direct update", ty);
 }
 
 mvd_status direct_accumulate(const int dims[3], const float* r, const float* k, const int kd[3], float* prod,
-                             cudaStream_t st, int ty) {
+                             cudaStream_t st, int ty, const float* inv_s) {
     DArgs a = make(dims, r, k, kd);
     a.out = prod;
+    a.inv_s = inv_s;
     return launch<4>(a, kd, st, "direct accumulate", ty);
 }
 

@@ -34,8 +34,11 @@ __device__ __forceinline__ float2 mul_si(float2 a) {
 // Factor the sequential update multiplies psi by, from v = c - 1 (c the view's
 // back-projected ratio): with view weight w and Tikhonov lambda (one-step-late
 // form, factor c / (1 + lambda psi)) it is 1 + w (c / (1 + lambda psi) - 1)
-// = 1 + w (v - lambda psi) / (1 + lambda psi); plainly 1 + v.
-__device__ __forceinline__ float update_factor(float v, float psi, const float* wt, long i, float lam) {
+// = 1 + w (v - lambda psi) / (1 + lambda psi); plainly 1 + v. With a zero
+// boundary c is first divided by the sensitivity (inv_s = 1 / s).
+__device__ __forceinline__ float update_factor(float v, float psi, const float* wt, long i, float lam,
+                                               const float* inv_s = nullptr) {
+    if (inv_s) v = (v + 1.f) * __ldg(inv_s + i) - 1.f;
     if (!wt && lam == 0.f) return v + 1.f;
     const float w = wt ? __ldg(wt + i) : 1.f;
     return lam == 0.f ? 1.f + w * v : 1.f + w * (v - lam * psi) / (1.f + lam * psi);

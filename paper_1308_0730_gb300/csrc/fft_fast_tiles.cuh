@@ -92,6 +92,7 @@ struct XFast {
     const cdd* spec2;  // when set, the update reads this double-float spectrum (rounded to FP32)
     const float* wt;   // when set, the update applies the fraction wt of the change (partial overlap)
     float lam;         // Tikhonov regularisation of the update (0 = none)
+    const float* inv_s;  // zero boundary: 1 / sensitivity of the update's view, or none
 };
 
 // write the packed forward spectra (natural order in registers) as the two
@@ -233,11 +234,13 @@ __device__ __forceinline__ void fast_x_inverse_tile(const XFast& a, long tile, f
             const int n = t + TPL * q;
             if (MODE == 1) {
                 // v = c - 1 (weights and regularisation: update_factor)
-                if (oka) a.psi[ra + n] = fmaxf(w[q].x * update_factor(v[q].x, w[q].x, a.wt, ra + n, a.lam), a.eps);
-                if (okb) a.psi[rb + n] = fmaxf(w[q].y * update_factor(v[q].y, w[q].y, a.wt, rb + n, a.lam), a.eps);
+                if (oka)
+                    a.psi[ra + n] = fmaxf(w[q].x * update_factor(v[q].x, w[q].x, a.wt, ra + n, a.lam, a.inv_s), a.eps);
+                if (okb)
+                    a.psi[rb + n] = fmaxf(w[q].y * update_factor(v[q].y, w[q].y, a.wt, rb + n, a.lam, a.inv_s), a.eps);
             } else if (MODE == 4) {  // combined update: multiply this view's factor into the product
-                if (oka) a.psi[ra + n] = w[q].x * (v[q].x + 1.f);
-                if (okb) a.psi[rb + n] = w[q].y * (v[q].y + 1.f);
+                if (oka) a.psi[ra + n] = w[q].x * (v[q].x + 1.f) * (a.inv_s ? __ldg(a.inv_s + ra + n) : 1.f);
+                if (okb) a.psi[rb + n] = w[q].y * (v[q].y + 1.f) * (a.inv_s ? __ldg(a.inv_s + rb + n) : 1.f);
             } else {
                 if (oka) a.psi[ra + n] = v[q].x;
                 if (okb) a.psi[rb + n] = v[q].y;

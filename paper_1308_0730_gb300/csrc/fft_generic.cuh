@@ -53,6 +53,7 @@ struct GenX {
     const cdd* S2in;   // when set, the update reads this double-float spectrum (rounded to FP32)
     const float* wt;   // when set, the update applies the fraction wt of the change (partial overlap)
     float lam;         // Tikhonov regularisation of the update (0 = none)
+    const float* inv_s;  // zero boundary: 1 / sensitivity of the update's view, or none
 };
 
 __host__ __device__ inline GenX gen_x_args(int X, long YZ, const FftPlan& plan) {
@@ -196,10 +197,10 @@ __device__ void gen_x_inverse_tile(const GenX& a, long tile, float2* sm) {
         float* dst = a.psi + (rho0 + row) * a.X + n;
         if (MODE == 1) {  // c here is (r - 1) * K: the factor is c + 1 (K sums to 1), see update_factor
             const float old = ld1<CO>(dst);
-            *dst = fmaxf(old * update_factor(c, old, a.wt, (rho0 + row) * a.X + n, a.lam), a.eps);
+            *dst = fmaxf(old * update_factor(c, old, a.wt, (rho0 + row) * a.X + n, a.lam, a.inv_s), a.eps);
         }
         else if (MODE == 4)
-            *dst = ld1<CO>(dst) * (c + 1.f);
+            *dst = ld1<CO>(dst) * (c + 1.f) * (a.inv_s ? __ldg(a.inv_s + (rho0 + row) * a.X + n) : 1.f);
         else
             *dst = c;
     }

@@ -189,6 +189,8 @@ void free_all(mvd_ctx* c) {
     dev_free(c->d_ktmp);
     dev_free(c->d_red);
     dev_free(c->d_flag);
+    dev_free(c->d_invs);
+    dev_free(c->d_stage);
 }
 
 bool smooth235(int n) {
@@ -407,12 +409,20 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
     const float* phi = c->d_views + (size_t)v * c->M;
     const int* kd = &c->kd[3 * v];
     const float* wt = c->d_w ? c->d_w + (size_t)v * c->M : nullptr;  // partial overlap (sequential update only)
+    const float* inv_s = c->d_invs ? c->d_invs + (size_t)v * c->M : nullptr;  // zero boundary
+    // the update leaves max(0 * c, eps) in a zero boundary's padding: clear it
+    auto done = [&](mvd_status st) {
+        return st == MVD_OK && !prod && c->boundary == MVD_BOUNDARY_ZERO ? clear_padding(c, c->d_psi, c->stream)
+                                                                          : st;
+    };
     if (c->path == MVD_PATH_DIRECT) {
         MVD_TRY(direct_ratio(c->dims, c->d_psi, c->d_psf + c->koff[v], kd, phi, c->eps, c->d_r, c->stream,
                              c->direct_ty));
-        if (prod) return direct_accumulate(c->dims, c->d_r, c->d_comp + c->koff[v], kd, prod, c->stream, c->direct_ty);
-        return direct_update(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_psi, c->eps, c->stream,
-                             c->direct_ty, wt, c->lambda);
+        if (prod)
+            return direct_accumulate(c->dims, c->d_r, c->d_comp + c->koff[v], kd, prod, c->stream, c->direct_ty,
+                                     inv_s);
+        return done(direct_update(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_psi, c->eps, c->stream,
+                                  c->direct_ty, wt, c->lambda, inv_s));
     }
     const FftGeom& g = c->geom;
     const size_t ns = (size_t)g.Xh * g.YZ;
@@ -429,8 +439,8 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
         MVD_TRY(dd_y(g, S2, 0, c->stream));
         MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
         MVD_TRY(dd_y(g, S2, 1, c->stream));
-        if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream);
-        return fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt, c->lambda);
+        if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream, inv_s);
+        return done(fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
     }
     const float2* Kp = c->d_K + ns * (2 * v);
     const float2* Kc = c->d_K + ns * (2 * v + 1);
@@ -442,8 +452,8 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
     MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
     MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
     MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
-    if (prod) return fft_x_accumulate(g, c->d_S, prod, c->stream);
-    return fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream, wt, c->lambda);
+    if (prod) return fft_x_accumulate(g, c->d_S, prod, c->stream, inv_s);
+    return done(fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
 }
 
 namespace {
@@ -515,6 +525,7 @@ void mvd_default_options(mvd_options* opt) {
     opt->views_on_device = 0;
     opt->device = -1;
     opt->precision = MVD_PRECISE;
+    opt->boundary = MVD_BOUNDARY_PERIODIC;
 }
 
 const char* mvd_last_error(void) { return t_err.c_str(); }
@@ -579,6 +590,10 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
         set_error("mvd_create: eps must be finite and >= 0");
         return MVD_ERR_ARG;
     }
+    if (opt.boundary != MVD_BOUNDARY_PERIODIC && opt.boundary != MVD_BOUNDARY_ZERO) {
+        set_error("mvd_create: unknown boundary %d", opt.boundary);
+        return MVD_ERR_ARG;
+    }
     // PSF shapes and values; normalise to sum 1 (Eq. 3)
     std::vector<float> psf_h;
     std::vector<double> psf_sum;
@@ -628,10 +643,22 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     mvd_ctx* c = new mvd_ctx();
     cudaGetDevice(&c->device);
     c->stream = (cudaStream_t)opt.stream;
-    c->dims[0] = dims[0];
-    c->dims[1] = dims[1];
-    c->dims[2] = dims[2];
-    c->M = (long)dims[0] * dims[1] * dims[2];
+    c->boundary = opt.boundary;
+    for (int a = 0; a < 3; ++a) {
+        c->udims[a] = dims[a];
+        c->dims[a] = dims[a];
+        if (opt.boundary == MVD_BOUNDARY_ZERO) {
+            // pad by the largest half-width so no term of a periodic
+            // convolution wraps into the volume; round up to a smooth length
+            int h = 0;
+            for (int v = 0; v < n_views; ++v) h = std::max(h, psf_dims[3 * v + a] / 2);
+            int n = dims[a] + h;
+            while (!smooth235(n)) ++n;
+            c->dims[a] = n;
+        }
+    }
+    c->uM = (long)dims[0] * dims[1] * dims[2];
+    c->M = (long)c->dims[0] * c->dims[1] * c->dims[2];
     c->nv = n_views;
     c->kd.assign(psf_dims, psf_dims + 3 * n_views);
     c->koff = koff;
@@ -654,8 +681,21 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     if ((st = dev_alloc(&c->d_red, 4, "reduction scratch")) != MVD_OK) return fail(st);
     if ((st = dev_alloc(&c->d_flag, 4, "flag")) != MVD_OK) return fail(st);
     const cudaMemcpyKind kind = opt.views_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (c->boundary == MVD_BOUNDARY_ZERO && (st = dev_alloc(&c->d_stage, (size_t)c->uM, "staging volume")) != MVD_OK)
+        return fail(st);
     for (int v = 0; v < n_views; ++v) {
-        cudaError_t e = cudaMemcpyAsync(c->d_views + (size_t)v * c->M, views[v], c->M * sizeof(float), kind, c->stream);
+        float* dst = c->d_views + (size_t)v * c->M;
+        if (c->boundary == MVD_BOUNDARY_ZERO) {
+            const float* src = views[v];
+            if (!opt.views_on_device) {
+                cudaError_t e = cudaMemcpyAsync(c->d_stage, views[v], c->uM * sizeof(float), kind, c->stream);
+                if (e != cudaSuccess) return fail(cuda_status(e, "copying a view"));
+                src = c->d_stage;
+            }
+            if ((st = pad_volume(c, src, dst, c->stream)) != MVD_OK) return fail(st);
+            continue;
+        }
+        cudaError_t e = cudaMemcpyAsync(dst, views[v], c->M * sizeof(float), kind, c->stream);
         if (e != cudaSuccess) return fail(cuda_status(e, "copying a view"));
     }
     {
@@ -678,17 +718,34 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
         set_error("mvd_create: a view holds a negative or non-finite value");
         return fail(MVD_ERR_ARG);
     }
-    c->psi0 = (float)(sum / ((double)c->M * n_views));
+    c->psi0 = (float)(sum / ((double)c->uM * n_views));
     if (!(c->psi0 > 0.f)) {
         set_error("mvd_create: all views are zero");
         return fail(MVD_ERR_ARG);
     }
-    c->eps = opt.eps > 0.f ? opt.eps : (float)(1e-4 * (sum / ((double)c->M * n_views)));
+    c->eps = opt.eps > 0.f ? opt.eps : (float)(1e-4 * (sum / ((double)c->uM * n_views)));
     if ((st = fill(c->d_psi, c->M, c->psi0, c->stream)) != MVD_OK) return fail(st);
+    if (c->boundary == MVD_BOUNDARY_ZERO && (st = clear_padding(c, c->d_psi, c->stream)) != MVD_OK) return fail(st);
     c->state = 1;
     *out = c;
     return MVD_OK;
 }
+
+namespace {
+
+// Last step of mvd_precompute_kernels once the engine is set up: with a zero
+// boundary, the inverse sensitivity 1 / (1 * P_v^comp) of every view.
+mvd_status finish_precompute(mvd_ctx* c, int variant) {
+    if (c->boundary == MVD_BOUNDARY_ZERO) {
+        if (!c->d_invs) MVD_TRY(dev_alloc(&c->d_invs, (size_t)c->nv * c->M, "inverse sensitivities"));
+        MVD_TRY(compute_inverse_sensitivity(c));
+    }
+    c->variant = variant;
+    c->state = 2;
+    return MVD_OK;
+}
+
+}  // namespace
 
 mvd_status mvd_precompute_kernels(mvd_ctx* c, int variant) {
     clear_error();
@@ -748,9 +805,7 @@ mvd_status mvd_precompute_kernels(mvd_ctx* c, int variant) {
                 MVD_TRY(setup_fft(c));
                 c->geom.fast = cached.fast != 0;
             }
-            c->variant = variant;
-            c->state = 2;
-            return MVD_OK;
+            return finish_precompute(c, variant);
         }
     }
     if (path == MVD_PATH_AUTO) {
@@ -771,9 +826,7 @@ mvd_status mvd_precompute_kernels(mvd_ctx* c, int variant) {
     }
     c->path = path;
     if (path == MVD_PATH_FFT) MVD_TRY(setup_fft(c));
-    c->variant = variant;
-    c->state = 2;
-    return MVD_OK;
+    return finish_precompute(c, variant);
 }
 
 mvd_status mvd_set_estimate(mvd_ctx* c, const float* psi, int on_device) {
@@ -787,19 +840,27 @@ mvd_status mvd_set_estimate(mvd_ctx* c, const float* psi, int on_device) {
         return MVD_ERR_STATE;
     }
     DeviceGuard dg(c->device);
-    if (!psi) return fill(c->d_psi, c->M, c->psi0, c->stream);
-    MVD_CUDA(cudaMemcpyAsync(c->d_psi, psi, c->M * sizeof(float),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    const bool zero = c->boundary == MVD_BOUNDARY_ZERO;
+    if (!psi) {
+        MVD_TRY(fill(c->d_psi, c->M, c->psi0, c->stream));
+        return zero ? clear_padding(c, c->d_psi, c->stream) : MVD_OK;
+    }
+    // with a zero boundary: stage the user-layout volume, check it, pad it
+    float* dst = zero ? c->d_stage : c->d_psi;
+    const long n = zero ? c->uM : c->M;
+    MVD_CUDA(cudaMemcpyAsync(dst, psi, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->stream));
     MVD_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
-    MVD_TRY(check_positive(c->d_psi, c->M, c->d_flag, c->stream));
+    MVD_TRY(check_positive(dst, n, c->d_flag, c->stream));
     int bad = 0;
     MVD_TRY(read_flag(c, &bad));
     if (bad) {
         set_error("mvd_set_estimate: the estimate must be finite and > 0");
         fill(c->d_psi, c->M, c->psi0, c->stream);
+        if (zero) clear_padding(c, c->d_psi, c->stream);
         return MVD_ERR_ARG;
     }
-    return MVD_OK;
+    return zero ? pad_volume(c, c->d_stage, c->d_psi, c->stream) : MVD_OK;
 }
 
 mvd_status mvd_iterate(mvd_ctx* c, int n_iter, const int* schedule, int schedule_len) {
@@ -843,6 +904,10 @@ mvd_status mvd_set_weights(mvd_ctx* c, const float* const* weights, int on_devic
     if (c->state < 1) {
         set_error("mvd_set_weights: context not created");
         return MVD_ERR_STATE;
+    }
+    if (weights && c->boundary != MVD_BOUNDARY_PERIODIC) {
+        set_error("mvd_set_weights: view weights need the periodic boundary");
+        return MVD_ERR_UNSUPPORTED;
     }
     DeviceGuard dg(c->device);
     drop_graphs(c);  // the captured update passes carry the weight pointers
@@ -927,6 +992,10 @@ mvd_status mvd_set_regularization(mvd_ctx* c, float lambda) {
         set_error("mvd_set_regularization: lambda must be finite and >= 0");
         return MVD_ERR_ARG;
     }
+    if (lambda != 0.f && c->boundary != MVD_BOUNDARY_PERIODIC) {
+        set_error("mvd_set_regularization: regularisation needs the periodic boundary");
+        return MVD_ERR_UNSUPPORTED;
+    }
     DeviceGuard dg(c->device);
     drop_graphs(c);  // the captured update passes carry lambda
     c->lambda = lambda;
@@ -968,8 +1037,9 @@ mvd_status mvd_iterate_combined(mvd_ctx* c, int n_iter, int root) {
         set_error("mvd_iterate_combined: n_iter < 0");
         return MVD_ERR_ARG;
     }
-    if (c->d_w || c->lambda != 0.f) {
-        set_error("mvd_iterate_combined: view weights and regularisation apply to the sequential update only");
+    if (c->d_w || c->lambda != 0.f || c->boundary != MVD_BOUNDARY_PERIODIC) {
+        set_error("mvd_iterate_combined: view weights, regularisation and the zero boundary apply to the "
+                  "sequential update only");
         return MVD_ERR_UNSUPPORTED;
     }
     DeviceGuard dg(c->device);
@@ -993,12 +1063,18 @@ mvd_status mvd_result(mvd_ctx* c, float* out, size_t n_elems) {
         set_error("mvd_result: context not created");
         return MVD_ERR_STATE;
     }
-    if (n_elems < (size_t)c->M) {
-        set_error("mvd_result: buffer holds %zu elements, need %ld", n_elems, c->M);
+    const long n = c->boundary == MVD_BOUNDARY_ZERO ? c->uM : c->M;
+    if (n_elems < (size_t)n) {
+        set_error("mvd_result: buffer holds %zu elements, need %ld", n_elems, n);
         return MVD_ERR_SHAPE;
     }
     DeviceGuard dg(c->device);
-    MVD_CUDA(cudaMemcpyAsync(out, c->d_psi, c->M * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    const float* src = c->d_psi;
+    if (c->boundary == MVD_BOUNDARY_ZERO) {
+        MVD_TRY(crop_volume(c, c->d_psi, c->d_stage, c->stream));
+        src = c->d_stage;
+    }
+    MVD_CUDA(cudaMemcpyAsync(out, src, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     MVD_CUDA(cudaStreamSynchronize(c->stream));
     return MVD_OK;
 }
@@ -1012,6 +1088,12 @@ mvd_status mvd_result_device(mvd_ctx* c, const float** dptr) {
     if (c->state < 1) {
         set_error("mvd_result_device: context not created");
         return MVD_ERR_STATE;
+    }
+    if (c->boundary == MVD_BOUNDARY_ZERO) {
+        DeviceGuard dg(c->device);
+        MVD_TRY(crop_volume(c, c->d_psi, c->d_stage, c->stream));
+        *dptr = c->d_stage;
+        return MVD_OK;
     }
     *dptr = c->d_psi;
     return MVD_OK;

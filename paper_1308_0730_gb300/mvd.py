@@ -44,6 +44,8 @@ class MvdError(RuntimeError):
 
 MVD_PRECISE, MVD_FAST = 0, 1
 PRECISIONS = {"precise": MVD_PRECISE, "fast": MVD_FAST}
+MVD_BOUNDARY_PERIODIC, MVD_BOUNDARY_ZERO = 0, 1
+BOUNDARIES = {"periodic": MVD_BOUNDARY_PERIODIC, "zero": MVD_BOUNDARY_ZERO}
 
 
 class TuneResult(ctypes.Structure):
@@ -53,7 +55,8 @@ class TuneResult(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("path", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("views_on_device", ctypes.c_int), ("device", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("views_on_device", ctypes.c_int), ("device", ctypes.c_int), ("precision", ctypes.c_int),
+                ("boundary", ctypes.c_int)]
 
 
 _lib = None
@@ -171,12 +174,13 @@ def mvd_profile_read() -> dict:
 
 
 def mvd_create(views, psfs, dims=None, eps: float = 0.0, path="auto", stream=None, device: int = -1,
-               precision="precise"):
+               precision="precise", boundary="periodic"):
     """Creates a context (see mvd_create in include/mvd.h); returns its handle.
 
     ``views``: list of float32 arrays ``[Z][Y][X]`` (numpy on the host, or CUDA
     tensors on the device, contiguous). ``psfs``: list of float32 host arrays
     ``[Kz][Ky][Kx]``. ``stream``: a ``torch.cuda.Stream`` or a raw handle.
+    ``boundary``: ``"periodic"`` or ``"zero"`` (see mvd_boundary).
     """
     lib = load()
     on_dev = _is_device(views[0])
@@ -203,6 +207,7 @@ def mvd_create(views, psfs, dims=None, eps: float = 0.0, path="auto", stream=Non
     opt.views_on_device = 1 if on_dev else 0
     opt.device = int(device)
     opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    opt.boundary = BOUNDARIES[boundary] if isinstance(boundary, str) else int(boundary)
     h = ctypes.c_void_p()
     _check(lib.mvd_create((ctypes.c_void_p * len(ptrs))(*ptrs), len(ptrs),
                           (ctypes.c_void_p * len(hp))(*[ctypes.c_void_p(p.ctypes.data) for p in hp]),
@@ -414,10 +419,11 @@ class Deconvolver:
     """Owns one context: ``with Deconvolver(views, psfs) as d: d.iterate(10); psi = d.result()``."""
 
     def __init__(self, views, psfs, variant="efficient", eps=0.0, path="auto", stream=None, device=-1,
-                 precision="precise"):
+                 precision="precise", boundary="periodic"):
         self.shape = tuple(views[0].shape)
         self.psf_shapes = [tuple(p.shape) for p in psfs]
-        self.ctx = mvd_create(views, psfs, eps=eps, path=path, stream=stream, device=device, precision=precision)
+        self.ctx = mvd_create(views, psfs, eps=eps, path=path, stream=stream, device=device, precision=precision,
+                              boundary=boundary)
         try:
             mvd_precompute_kernels(self.ctx, variant)
         except Exception:

@@ -44,7 +44,7 @@ def test_default_options(lib):
     o = mvd.Options()
     lib.mvd_default_options(ctypes.byref(o))
     assert o.eps == 0.0 and o.path == 0 and o.stream is None and o.views_on_device == 0 and o.device == -1
-    assert o.precision == mvd.MVD_PRECISE
+    assert o.precision == mvd.MVD_PRECISE and o.boundary == mvd.MVD_BOUNDARY_PERIODIC
 
 
 def _good():
@@ -62,6 +62,7 @@ def _good():
     ("no_views", mvd.MVD_ERR_ARG),
     ("bad_path", mvd.MVD_ERR_ARG),
     ("bad_eps", mvd.MVD_ERR_ARG),
+    ("bad_boundary", mvd.MVD_ERR_ARG),
 ])
 def test_create_rejects_invalid_arguments(lib, case, status):
     views, psfs = _good()
@@ -86,6 +87,8 @@ def test_create_rejects_invalid_arguments(lib, case, status):
         kw["path"] = 7
     elif case == "bad_eps":
         kw["eps"] = float("nan")
+    elif case == "bad_boundary":
+        kw["boundary"] = 2
     if case == "no_views":
         h = ctypes.c_void_p()
         opt = mvd.Options()
