@@ -13,6 +13,8 @@ from .oracle import (  # noqa: F401
     build,
     conv,
     conv_zero,
+    conv_mirror,
+    backproject_mirror,
     mirror,
     kconv,
     compound,
@@ -21,6 +23,7 @@ from .oracle import (  # noqa: F401
     deconvolve,
     deconvolve_combined,
     deconvolve_zero,
+    deconvolve_mirror,
     deconvolve_weighted,
     normalize_weights,
     WEIGHT_NORMS,

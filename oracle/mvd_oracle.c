@@ -22,7 +22,8 @@
  *
  * Readings where the paper is silent (same on the CUDA side):
  *   - image convolutions are periodic (circular) on the given grid, i.e. what
- *     the Convolution Theorem computes;
+ *     the Convolution Theorem computes; the zero and mirror boundaries are
+ *     alternatives (mvdo_deconvolve_zero, mvdo_deconvolve_mirror);
  *   - kernel algebra (P_v^* * P_w * P_w^*) is linear convolution of the small
  *     kernels; the compound kernel lives on P_v's own box and is normalised
  *     to sum 1;
@@ -523,6 +524,125 @@ double mvdo_deconvolve_zero(int n_views, const double* const* views, const doubl
     free(pn);
     free(sens);
     free(ones);
+    free(b);
+    free(r);
+    free(c);
+    return bad ? -1.0 : eps;
+}
+
+/* Half-sample symmetric reflection of index i into [0, n): the grid continued
+ * as ... x1 x0 | x0 x1 ... x(n-1) | x(n-1) x(n-2) ... (period 2n). */
+static int reflect(int i, int n) {
+    int m = i % (2 * n);
+    if (m < 0) m += 2 * n;
+    return m < n ? m : 2 * n - 1 - m;
+}
+
+/* Convolution with a mirror boundary (the volume continued by reflection):
+ *   out(x) = sum_d k(d) in(reflect(x - d)). */
+void mvdo_conv_mirror(const double* in, const int dims[3], const double* k, const int kd[3], double* out) {
+    const int X = dims[0], Y = dims[1], Z = dims[2];
+    const int hx = (kd[0] - 1) / 2, hy = (kd[1] - 1) / 2, hz = (kd[2] - 1) / 2;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < Z; ++z)
+        for (int y = 0; y < Y; ++y)
+            for (int x = 0; x < X; ++x) {
+                double s = 0.0;
+                for (int tz = 0; tz < kd[2]; ++tz) {
+                    const int sz = reflect(z - (tz - hz), Z);
+                    for (int ty = 0; ty < kd[1]; ++ty) {
+                        const int sy = reflect(y - (ty - hy), Y);
+                        for (int tx = 0; tx < kd[0]; ++tx)
+                            s += k[tx + kd[0] * (ty + kd[1] * tz)] * in[idx3(reflect(x - (tx - hx), X), sy, sz, X, Y)];
+                    }
+                }
+                out[idx3(x, y, z, X, Y)] = s;
+            }
+}
+
+/* Back-projection with a mirror boundary: each voxel i spreads r(i) k(e) to
+ * i + e, and what lands outside the grid is folded back onto its reflection:
+ *   out(j) = sum_i r(i) sum_{e : reflect(i + e) = j} k(e).
+ * It is the transpose of mvdo_conv_mirror with the mirrored kernel k(-e), and
+ * equals r * k when nothing reaches a face. Serial scatter. */
+void mvdo_backproject_mirror(const double* r, const int dims[3], const double* k, const int kd[3], double* out) {
+    const int X = dims[0], Y = dims[1], Z = dims[2];
+    const int hx = (kd[0] - 1) / 2, hy = (kd[1] - 1) / 2, hz = (kd[2] - 1) / 2;
+    const long M = (long)X * Y * Z;
+    for (long i = 0; i < M; ++i) out[i] = 0.0;
+    for (int z = 0; z < Z; ++z)
+        for (int y = 0; y < Y; ++y)
+            for (int x = 0; x < X; ++x) {
+                const double ri = r[idx3(x, y, z, X, Y)];
+                for (int tz = 0; tz < kd[2]; ++tz) {
+                    const int jz = reflect(z + (tz - hz), Z);
+                    for (int ty = 0; ty < kd[1]; ++ty) {
+                        const int jy = reflect(y + (ty - hy), Y);
+                        for (int tx = 0; tx < kd[0]; ++tx)
+                            out[idx3(reflect(x + (tx - hx), X), jy, jz, X, Y)] += ri * k[tx + kd[0] * (ty + kd[1] * tz)];
+                    }
+                }
+            }
+}
+
+/* Sequential deconvolution (default schedule) with mirror-boundary image
+ * convolutions. The forward blur is b = P_v convolved with the reflected
+ * continuation of psi (mvdo_conv_mirror); the back-projection with P_v^comp
+ * is the folded one (mvdo_backproject_mirror), which for the plain kernel
+ * P_v^* is the exact transpose of the forward blur. As for the zero boundary,
+ * the update is the ML-EM step that divides by the sensitivity s_v (the
+ * back-projection of a field of ones; 1 wherever P_v^comp is symmetric under
+ * the reflection of each face it reaches):
+ *   psi <- max(psi c / s_v, eps),  c = backproject_mirror(r, P_v^comp).
+ * Otherwise as mvdo_deconvolve. Returns eps, or -1. */
+double mvdo_deconvolve_mirror(int n_views, const double* const* views, const double* const* psfs, const int* pdims,
+                              const int dims[3], int variant, int n_iter, double eps, int init, double* psi) {
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double psi0 = mvdo_mean_views(n_views, views, dims);
+    if (eps <= 0.0) eps = 1e-4 * psi0;
+    if (!init)
+        for (long i = 0; i < M; ++i) psi[i] = psi0;
+    double** pn = (double**)malloc(sizeof(double*) * n_views);
+    double** comp = (double**)malloc(sizeof(double*) * n_views);
+    double** sens = (double**)malloc(sizeof(double*) * n_views);
+    int bad = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        double s = 0.0;
+        for (long i = 0; i < T; ++i) s += psfs[v][i];
+        pn[v] = (double*)malloc(sizeof(double) * T);
+        for (long i = 0; i < T; ++i) pn[v][i] = psfs[v][i] / s;
+    }
+    double* b = (double*)malloc(sizeof(double) * M);
+    double* r = (double*)malloc(sizeof(double) * M);
+    double* c = (double*)malloc(sizeof(double) * M);
+    for (long i = 0; i < M; ++i) r[i] = 1.0;
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        comp[v] = (double*)malloc(sizeof(double) * T);
+        sens[v] = (double*)malloc(sizeof(double) * M);
+        if (mvdo_compound(n_views, (const double* const*)pn, pdims, v, variant, comp[v]) != 0) bad = 1;
+        if (!bad) mvdo_backproject_mirror(r, dims, comp[v], pdims + 3 * v, sens[v]);
+    }
+    for (int it = 0; it < n_iter && !bad; ++it) {
+        for (int v = 0; v < n_views; ++v) {
+            const int* pd = pdims + 3 * v;
+            mvdo_conv_mirror(psi, dims, pn[v], pd, b);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) r[i] = views[v][i] / fmax(b[i], eps);
+            mvdo_backproject_mirror(r, dims, comp[v], pd, c);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) psi[i] = fmax(psi[i] * c[i] / sens[v][i], eps);
+        }
+    }
+    for (int v = 0; v < n_views; ++v) {
+        free(comp[v]);
+        free(pn[v]);
+        free(sens[v]);
+    }
+    free(comp);
+    free(pn);
+    free(sens);
     free(b);
     free(r);
     free(c);

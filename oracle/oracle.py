@@ -72,6 +72,11 @@ def _load():
             lib.mvdo_deconvolve_zero.argtypes = [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D), _I, _I,
                                                  ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
             lib.mvdo_deconvolve_zero.restype = ctypes.c_double
+            lib.mvdo_conv_mirror.argtypes = [_D, _I, _D, _I, _D]
+            lib.mvdo_backproject_mirror.argtypes = [_D, _I, _D, _I, _D]
+            lib.mvdo_deconvolve_mirror.argtypes = [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D), _I, _I,
+                                                   ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
+            lib.mvdo_deconvolve_mirror.restype = ctypes.c_double
             lib.mvdo_update_at.argtypes = [_D, _D, _D, _I, _D, _I, _I, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_long), ctypes.c_int, _D]
             lib.mvdo_num_threads.restype = ctypes.c_int
@@ -114,6 +119,22 @@ def conv_zero(vol, k) -> np.ndarray:
     vol, k = _f64(vol), _f64(k)
     out = np.empty_like(vol)
     _load().mvdo_conv_zero(_dptr(vol), _dims_xyz(vol), _dptr(k), _dims_xyz(k), _dptr(out))
+    return out
+
+
+def conv_mirror(vol, k) -> np.ndarray:
+    """Convolution with a mirror boundary: ``sum_d k(d) vol(reflect(x-d))``, half-sample symmetric reflection."""
+    vol, k = _f64(vol), _f64(k)
+    out = np.empty_like(vol)
+    _load().mvdo_conv_mirror(_dptr(vol), _dims_xyz(vol), _dptr(k), _dims_xyz(k), _dptr(out))
+    return out
+
+
+def backproject_mirror(r, k) -> np.ndarray:
+    """Mirror-boundary back-projection ``out(j) = sum_i r(i) sum_{e: reflect(i+e)=j} k(e)``."""
+    r, k = _f64(r), _f64(k)
+    out = np.empty_like(r)
+    _load().mvdo_backproject_mirror(_dptr(r), _dims_xyz(r), _dptr(k), _dims_xyz(k), _dptr(out))
     return out
 
 
@@ -285,6 +306,23 @@ def deconvolve_zero(views, psfs, n_iter, variant="efficient", eps=0.0, psi_init=
         psi, init = _f64(psi_init).copy(), 1
     used = _load().mvdo_deconvolve_zero(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), float(eps),
                                         init, _dptr(psi))
+    if used < 0:
+        raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
+    return psi, used
+
+
+def deconvolve_mirror(views, psfs, n_iter, variant="efficient", eps=0.0, psi_init=None):
+    """Sequential deconvolution whose image convolutions use a mirror boundary. Returns ``(psi, eps)``."""
+    var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    vs = [_f64(v) for v in views]
+    ps, parr, pd = _psf_arrays(psfs)
+    varr = (_D * len(vs))(*[_dptr(v) for v in vs])
+    if psi_init is None:
+        psi, init = np.empty_like(vs[0]), 0
+    else:
+        psi, init = _f64(psi_init).copy(), 1
+    used = _load().mvdo_deconvolve_mirror(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), float(eps),
+                                          init, _dptr(psi))
     if used < 0:
         raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
     return psi, used

@@ -61,3 +61,100 @@ def test_the_boundary_matters():
     a, _ = oracle.deconvolve_zero(views, psfs, 2, "efficient")
     b, _ = oracle.deconvolve(views, psfs, 2, "efficient")
     assert np.abs(a - b).max() > 1e-3 * np.abs(b).max()
+
+
+# ---------------------------------------------------------------------------
+# mirror boundary (half-sample symmetric reflection at every face)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,kshape", [((7, 6, 9), (3, 5, 3)), ((5, 8, 4), (5, 3, 7)), ((4, 4, 4), (7, 7, 7))])
+def test_mirror_convolution_matches_scipy(shape, kshape):
+    """scipy's 'reflect' mode is the half-sample symmetric continuation (d c b a | a b c d | d c b a)."""
+    rng = np.random.default_rng(2)
+    vol = rng.normal(size=shape)
+    k = rng.normal(size=kshape)
+    want = ndimage.convolve(vol, k, mode="reflect")
+    got = oracle.conv_mirror(vol, k)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("shape,kshape", [((7, 6, 9), (3, 5, 3)), ((4, 4, 4), (7, 7, 7))])
+def test_mirror_backprojection_is_the_transpose_of_the_mirrored_blur(shape, kshape):
+    """<conv_mirror(x, k(-e)), y> = <x, backproject_mirror(y, k)> for any x, y and an asymmetric k."""
+    rng = np.random.default_rng(3)
+    x, y = rng.normal(size=shape), rng.normal(size=shape)
+    k = rng.uniform(0.0, 1.0, size=kshape)
+    lhs = float((oracle.conv_mirror(x, oracle.mirror(k)) * y).sum())
+    rhs = float((x * oracle.backproject_mirror(y, k)).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_mirror_backprojection_away_from_the_faces_is_the_convolution():
+    rng = np.random.default_rng(4)
+    k = rng.uniform(0.0, 1.0, size=(3, 5, 3))
+    r = np.zeros((12, 14, 10))
+    r[3:9, 4:10, 2:8] = rng.uniform(size=(6, 6, 6))
+    assert np.abs(oracle.backproject_mirror(r, k) - oracle.conv(r, k)).max() <= 1e-12
+
+
+def _separable_symmetric(kshape):
+    ax = [np.exp(-0.5 * ((np.arange(n) - (n - 1) / 2) / 1.3) ** 2) for n in kshape]
+    k = ax[0][:, None, None] * ax[1][None, :, None] * ax[2][None, None, :]
+    return k / k.sum()
+
+
+def test_mirror_sensitivity():
+    """A kernel symmetric under each face's reflection sends back across the face exactly what
+    crosses it: the sensitivity is 1 everywhere. An asymmetric kernel's is not."""
+    ones = np.ones((9, 8, 7))
+    s = oracle.backproject_mirror(ones, _separable_symmetric((5, 3, 7)))
+    assert np.abs(s - 1.0).max() <= 1e-13
+    k = np.random.default_rng(5).uniform(0.0, 1.0, size=(5, 3, 7))
+    s = oracle.backproject_mirror(ones, k / k.sum())
+    assert np.abs(s - 1.0).max() > 1e-3
+
+
+def _mirror_noise_free(seed=32, dims=(14, 12, 10), background=2.0):
+    w = synth.small_case(seed, dims=dims, n_views=3, n_iter=3, asymmetric=True)
+    truth = w.truth.astype(np.float64) + background
+    psfs = [p.astype(np.float64) / p.astype(np.float64).sum() for p in w.psfs]
+    return [oracle.conv_mirror(truth, p) for p in psfs], psfs, truth
+
+
+def test_mirror_plain_update_conserves_the_sensitivity_weighted_intensity():
+    """ML-EM identity for the mirror model: sum(s psi') = sum(phi) with s the back-projection of ones."""
+    views, psfs, _ = _mirror_noise_free()
+    psi = None
+    for v in (0, 1, 2, 0):
+        s = oracle.backproject_mirror(np.ones_like(views[v]), oracle.mirror(psfs[v]))
+        psi, _ = oracle.deconvolve_mirror([views[v]], [psfs[v]], 1, "plain", psi_init=psi, eps=1e-12)
+        assert abs((s * psi).sum() - views[v].sum()) <= 1e-10 * views[v].sum()
+
+
+@pytest.mark.parametrize("variant", ["plain", "efficient"])
+def test_mirror_noise_free_truth_is_a_fixed_point(variant):
+    views, psfs, truth = _mirror_noise_free()
+    psi, _ = oracle.deconvolve_mirror(views, psfs, 3, variant, psi_init=truth)
+    assert np.abs(psi - truth).max() <= 1e-10 * truth.max()
+
+
+def test_mirror_symmetric_single_view_is_richardson_lucy_with_reflected_convolutions():
+    """One view, a kernel symmetric per axis, plain variant: s = 1 and the back-projection with
+    P^* = P is the mirror convolution itself (P symmetric), so one step is
+    psi * conv_mirror(phi / conv_mirror(psi, P), P)."""
+    rng = np.random.default_rng(6)
+    P = _separable_symmetric((5, 3, 7))
+    phi = rng.uniform(1.0, 3.0, size=(9, 8, 7))
+    psi0 = rng.uniform(1.0, 2.0, size=phi.shape)
+    want = psi0 * oracle.conv_mirror(phi / oracle.conv_mirror(psi0, P), P)
+    got, _ = oracle.deconvolve_mirror([phi], [P], 1, "plain", psi_init=psi0, eps=1e-12)
+    assert np.abs(got - want).max() <= 1e-12 * want.max()
+
+
+def test_the_three_boundaries_differ():
+    views, psfs, _ = _mirror_noise_free()
+    a, _ = oracle.deconvolve_mirror(views, psfs, 2, "efficient")
+    b, _ = oracle.deconvolve_zero(views, psfs, 2, "efficient")
+    c, _ = oracle.deconvolve(views, psfs, 2, "efficient")
+    assert np.abs(a - b).max() > 1e-3 * np.abs(b).max()
+    assert np.abs(a - c).max() > 1e-3 * np.abs(c).max()
