@@ -86,16 +86,22 @@ typedef enum { MVD_PRECISE = 0, MVD_FAST = 1 } mvd_precision;
  *   MVD_BOUNDARY_PERIODIC: periodic (circular) convolution on the X*Y*Z grid.
  *   MVD_BOUNDARY_ZERO: the volume is continued by zeros (the camera sees
  *     nothing of the object outside the grid). The context pads every axis
- *     internally by the largest PSF half-width (to a {2,3,5}-smooth length),
- *     and the update divides the back-projected ratio by the view's
- *     sensitivity 1 * P_v^comp, which falls below 1 within a PSF half-width
- *     of a face: the ML-EM step of Shepp and Vardi (1982) for this forward
- *     model; inside, far from the faces, the update is the periodic one.
- *     Estimates and results keep the X*Y*Z layout. The sequential update
- *     only: mvd_iterate_combined, view weights, regularisation, the unrolled
- *     (differentiable) form and the persistent batch kernel return
- *     MVD_ERR_UNSUPPORTED on such a context. */
-typedef enum { MVD_BOUNDARY_PERIODIC = 0, MVD_BOUNDARY_ZERO = 1 } mvd_boundary;
+ *     internally by the largest PSF half-width h (to a {2,3,5}-smooth
+ *     length), and the update divides the back-projected ratio by the view's
+ *     sensitivity 1 * P_v^comp, which falls below 1 within h of a face: the
+ *     ML-EM step of Shepp and Vardi (1982) for this forward model.
+ *   MVD_BOUNDARY_MIRROR: the volume is continued by its half-sample
+ *     symmetric reflection (... x1 x0 | x0 x1 ... ). Padding 2h; the forward
+ *     blur sees the reflected estimate, the back-projection folds what lands
+ *     past a face back onto the reflected voxel, and the update divides by
+ *     the folded sensitivity (1 wherever P_v^comp is symmetric under the
+ *     face's reflection).
+ *   Far from the faces both updates are the periodic one. Estimates and
+ *   results keep the X*Y*Z layout. The sequential update only:
+ *   mvd_iterate_combined, view weights, regularisation, the unrolled
+ *   (differentiable) form and the persistent batch kernel return
+ *   MVD_ERR_UNSUPPORTED on a context with a zero or mirror boundary. */
+typedef enum { MVD_BOUNDARY_PERIODIC = 0, MVD_BOUNDARY_ZERO = 1, MVD_BOUNDARY_MIRROR = 2 } mvd_boundary;
 
 typedef struct {
     float eps;           /* floor of b and psi; <= 0 selects 1e-4 * psi0 */
@@ -216,14 +222,14 @@ mvd_status mvd_get_weights(mvd_ctx* ctx, int v, float* out, size_t n_elems);
 mvd_status mvd_iterate_combined(mvd_ctx* ctx, int n_iter, int root);
 
 /* Copies psi (X*Y*Z floats) to host memory `out`; n_elems must be >= X*Y*Z.
- * Synchronises the context's stream. With a zero boundary the estimate is
- * first cropped out of the padded grid on the device. */
+ * Synchronises the context's stream. With a zero or mirror boundary the
+ * estimate is first cropped out of the padded grid on the device. */
 mvd_status mvd_result(mvd_ctx* ctx, float* out, size_t n_elems);
 
 /* Hands out the device pointer of psi (X*Y*Z floats, borrowed; valid until
  * the next call that mutates or destroys the context). Does not synchronise;
- * with a zero boundary it enqueues the crop into a staging volume (whose
- * pointer it returns) on the context's stream. */
+ * with a zero or mirror boundary it enqueues the crop into a staging volume
+ * (whose pointer it returns) on the context's stream. */
 mvd_status mvd_result_device(mvd_ctx* ctx, const float** dptr);
 
 /* Waits for all work enqueued on the context's stream. */

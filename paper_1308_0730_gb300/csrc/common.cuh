@@ -101,6 +101,8 @@ mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps
                         const float* wt = nullptr, float lam = 0.f,
                         const float* inv_s = nullptr);  // weights of the change, Tikhonov lambda, 1 / sensitivity
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
+// inverse x of a double-float spectrum to real (after the y and z passes)
+mvd_status fft_x_inverse_dd(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st);
 // combined update: acc *= c, c the back-projected factor of the spectrum of (r - 1) * K (+ 1)
 mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st,
                             const float* inv_s = nullptr);
@@ -169,10 +171,17 @@ mvd_status autocorr_kernel(const float* P, const int kd[3], float* Q, cudaStream
 mvd_status direct_conv_add(const int dims[3], const float* in, const float* k, const int kd[3], float* out,
                            cudaStream_t st);
 mvd_status one_update(mvd_ctx* c, int v);
-// zero boundary (boundary.cu)
+// zero / mirror boundary (boundary.cu)
 mvd_status pad_volume(const mvd_ctx* c, const float* user, float* padded, cudaStream_t st);
 mvd_status crop_volume(const mvd_ctx* c, const float* padded, float* user, cudaStream_t st);
 mvd_status clear_padding(const mvd_ctx* c, float* padded, cudaStream_t st);
+// mirror: the halo holds the reflection of the volume, the rest of the padding 0
+mvd_status mirror_fill(const mvd_ctx* c, float* padded, cudaStream_t st);
+// mirror: psi = max(psi . fold(cp + off) . inv_s, eps) inside, reflection refreshed;
+// cp is the back-projection on the padded grid (minus off)
+mvd_status mirror_update(const mvd_ctx* c, const float* cp, float off, const float* inv_s, cudaStream_t st);
+// the estimate's padding after it was written inside: zeroed or reflected
+mvd_status finish_padding(const mvd_ctx* c, float* padded, cudaStream_t st);
 mvd_status compute_inverse_sensitivity(mvd_ctx* c);
 // view v's pass from the current estimate: with prod == nullptr the
 // sequential update psi = max(psi . c_v, eps); else prod *= c_v
@@ -247,10 +256,12 @@ struct mvd_ctx {
     float weight_norm = 0.f;  // the normalisation target T of the weights
     float lambda = 0.f;       // Tikhonov regularisation of the sequential update (0 = none)
 
-    // zero boundary: the engines run on a padded grid (dims, M); the user's
-    // volume (udims, uM) sits in its low corner
+    // zero / mirror boundary: the engines run on a padded grid (dims, M); the
+    // user's volume (udims, uM) sits in its low corner; halo = largest PSF
+    // half-width per axis (the mirror boundary keeps psi's reflection there)
     int boundary = 0;                 // mvd_boundary
     int udims[3] = {0, 0, 0};
+    int halo[3] = {0, 0, 0};
     long uM = 0;
     float* d_invs = nullptr;  // 1 / sensitivity per view (nv padded volumes)
     float* d_stage = nullptr; // user-layout staging volume (uM)

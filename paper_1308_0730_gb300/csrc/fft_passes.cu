@@ -124,6 +124,15 @@ mvd_status fft_inverse_real_generic(const FftGeom& g, const float2* S, float* ds
     return launch(k_x_inverse<0>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x inverse", KC_SETUP);
 }
 
+mvd_status fft_x_inverse_dd(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st) {
+    if (dd_fast_x(g)) return dd_x_inverse_real(g, S2, dst, st);
+    GenX a = make_x(g);
+    a.S2in = S2;
+    a.psi = dst;
+    return launch(k_x_inverse<0>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x inverse (double-float)",
+                  KC_X_UPDATE);
+}
+
 mvd_status fft_y_generic(const FftGeom& g, float2* S, int inverse, cudaStream_t st) {
     GenY a = gen_y_args(g.Y, g.Xh, g.Z, g.py, S);
     return launch(inverse ? k_y<+1> : k_y<-1>, a, gen_y_tiles(g.Y, g.Xh, g.Z), gen_y_smem(g.Y), st, "fft y", KC_Y);

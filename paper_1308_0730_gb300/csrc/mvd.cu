@@ -409,15 +409,22 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
     const float* phi = c->d_views + (size_t)v * c->M;
     const int* kd = &c->kd[3 * v];
     const float* wt = c->d_w ? c->d_w + (size_t)v * c->M : nullptr;  // partial overlap (sequential update only)
-    const float* inv_s = c->d_invs ? c->d_invs + (size_t)v * c->M : nullptr;  // zero boundary
+    const float* inv_s = c->d_invs ? c->d_invs + (size_t)v * c->M : nullptr;  // zero / mirror boundary
     // the update leaves max(0 * c, eps) in a zero boundary's padding: clear it
     auto done = [&](mvd_status st) {
         return st == MVD_OK && !prod && c->boundary == MVD_BOUNDARY_ZERO ? clear_padding(c, c->d_psi, c->stream)
                                                                           : st;
     };
+    // mirror boundary: the back-projection goes to c->d_prod (FFT engines:
+    // minus 1, the transform of r - 1), then the fold and the update
+    const bool mirror = c->boundary == MVD_BOUNDARY_MIRROR;
     if (c->path == MVD_PATH_DIRECT) {
         MVD_TRY(direct_ratio(c->dims, c->d_psi, c->d_psf + c->koff[v], kd, phi, c->eps, c->d_r, c->stream,
                              c->direct_ty));
+        if (mirror) {
+            MVD_TRY(direct_conv(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_prod, c->stream));
+            return mirror_update(c, c->d_prod, 0.f, inv_s, c->stream);
+        }
         if (prod)
             return direct_accumulate(c->dims, c->d_r, c->d_comp + c->koff[v], kd, prod, c->stream, c->direct_ty,
                                      inv_s);
@@ -439,6 +446,10 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
         MVD_TRY(dd_y(g, S2, 0, c->stream));
         MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
         MVD_TRY(dd_y(g, S2, 1, c->stream));
+        if (mirror) {
+            MVD_TRY(fft_x_inverse_dd(g, S2, c->d_prod, c->stream));
+            return mirror_update(c, c->d_prod, 1.f, inv_s, c->stream);
+        }
         if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream, inv_s);
         return done(fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
     }
@@ -452,6 +463,10 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
     MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
     MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
     MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
+    if (mirror) {
+        MVD_TRY(fft_inverse_real(g, c->d_S, c->d_prod, c->stream));
+        return mirror_update(c, c->d_prod, 1.f, inv_s, c->stream);
+    }
     if (prod) return fft_x_accumulate(g, c->d_S, prod, c->stream, inv_s);
     return done(fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
 }
@@ -590,7 +605,7 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
         set_error("mvd_create: eps must be finite and >= 0");
         return MVD_ERR_ARG;
     }
-    if (opt.boundary != MVD_BOUNDARY_PERIODIC && opt.boundary != MVD_BOUNDARY_ZERO) {
+    if (opt.boundary < MVD_BOUNDARY_PERIODIC || opt.boundary > MVD_BOUNDARY_MIRROR) {
         set_error("mvd_create: unknown boundary %d", opt.boundary);
         return MVD_ERR_ARG;
     }
@@ -647,12 +662,14 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     for (int a = 0; a < 3; ++a) {
         c->udims[a] = dims[a];
         c->dims[a] = dims[a];
-        if (opt.boundary == MVD_BOUNDARY_ZERO) {
-            // pad by the largest half-width so no term of a periodic
-            // convolution wraps into the volume; round up to a smooth length
+        if (opt.boundary != MVD_BOUNDARY_PERIODIC) {
+            // pad by the largest half-width h so no term of a periodic
+            // convolution wraps into the volume (mirror: 2h, room for the
+            // reflections on both sides); round up to a smooth length
             int h = 0;
             for (int v = 0; v < n_views; ++v) h = std::max(h, psf_dims[3 * v + a] / 2);
-            int n = dims[a] + h;
+            c->halo[a] = h;
+            int n = dims[a] + (opt.boundary == MVD_BOUNDARY_MIRROR ? 2 * h : h);
             while (!smooth235(n)) ++n;
             c->dims[a] = n;
         }
@@ -681,11 +698,15 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     if ((st = dev_alloc(&c->d_red, 4, "reduction scratch")) != MVD_OK) return fail(st);
     if ((st = dev_alloc(&c->d_flag, 4, "flag")) != MVD_OK) return fail(st);
     const cudaMemcpyKind kind = opt.views_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (c->boundary == MVD_BOUNDARY_ZERO && (st = dev_alloc(&c->d_stage, (size_t)c->uM, "staging volume")) != MVD_OK)
-        return fail(st);
+    if (c->boundary != MVD_BOUNDARY_PERIODIC) {
+        if ((st = dev_alloc(&c->d_stage, (size_t)c->uM, "staging volume")) != MVD_OK) return fail(st);
+        // mirror: the back-projection on the padded grid, before the fold
+        if (c->boundary == MVD_BOUNDARY_MIRROR && (st = dev_alloc(&c->d_prod, (size_t)c->M, "back-projection")) != MVD_OK)
+            return fail(st);
+    }
     for (int v = 0; v < n_views; ++v) {
         float* dst = c->d_views + (size_t)v * c->M;
-        if (c->boundary == MVD_BOUNDARY_ZERO) {
+        if (c->boundary != MVD_BOUNDARY_PERIODIC) {
             const float* src = views[v];
             if (!opt.views_on_device) {
                 cudaError_t e = cudaMemcpyAsync(c->d_stage, views[v], c->uM * sizeof(float), kind, c->stream);
@@ -725,7 +746,7 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     }
     c->eps = opt.eps > 0.f ? opt.eps : (float)(1e-4 * (sum / ((double)c->uM * n_views)));
     if ((st = fill(c->d_psi, c->M, c->psi0, c->stream)) != MVD_OK) return fail(st);
-    if (c->boundary == MVD_BOUNDARY_ZERO && (st = clear_padding(c, c->d_psi, c->stream)) != MVD_OK) return fail(st);
+    if ((st = finish_padding(c, c->d_psi, c->stream)) != MVD_OK) return fail(st);
     c->state = 1;
     *out = c;
     return MVD_OK;
@@ -734,9 +755,9 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
 namespace {
 
 // Last step of mvd_precompute_kernels once the engine is set up: with a zero
-// boundary, the inverse sensitivity 1 / (1 * P_v^comp) of every view.
+// or mirror boundary, the inverse sensitivity of every view.
 mvd_status finish_precompute(mvd_ctx* c, int variant) {
-    if (c->boundary == MVD_BOUNDARY_ZERO) {
+    if (c->boundary != MVD_BOUNDARY_PERIODIC) {
         if (!c->d_invs) MVD_TRY(dev_alloc(&c->d_invs, (size_t)c->nv * c->M, "inverse sensitivities"));
         MVD_TRY(compute_inverse_sensitivity(c));
     }
@@ -840,12 +861,12 @@ mvd_status mvd_set_estimate(mvd_ctx* c, const float* psi, int on_device) {
         return MVD_ERR_STATE;
     }
     DeviceGuard dg(c->device);
-    const bool zero = c->boundary == MVD_BOUNDARY_ZERO;
+    const bool zero = c->boundary != MVD_BOUNDARY_PERIODIC;  // padded grid
     if (!psi) {
         MVD_TRY(fill(c->d_psi, c->M, c->psi0, c->stream));
-        return zero ? clear_padding(c, c->d_psi, c->stream) : MVD_OK;
+        return finish_padding(c, c->d_psi, c->stream);
     }
-    // with a zero boundary: stage the user-layout volume, check it, pad it
+    // on a padded grid: stage the user-layout volume, check it, pad it
     float* dst = zero ? c->d_stage : c->d_psi;
     const long n = zero ? c->uM : c->M;
     MVD_CUDA(cudaMemcpyAsync(dst, psi, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -857,10 +878,12 @@ mvd_status mvd_set_estimate(mvd_ctx* c, const float* psi, int on_device) {
     if (bad) {
         set_error("mvd_set_estimate: the estimate must be finite and > 0");
         fill(c->d_psi, c->M, c->psi0, c->stream);
-        if (zero) clear_padding(c, c->d_psi, c->stream);
+        finish_padding(c, c->d_psi, c->stream);
         return MVD_ERR_ARG;
     }
-    return zero ? pad_volume(c, c->d_stage, c->d_psi, c->stream) : MVD_OK;
+    if (!zero) return MVD_OK;
+    MVD_TRY(pad_volume(c, c->d_stage, c->d_psi, c->stream));
+    return finish_padding(c, c->d_psi, c->stream);
 }
 
 mvd_status mvd_iterate(mvd_ctx* c, int n_iter, const int* schedule, int schedule_len) {
@@ -1063,14 +1086,14 @@ mvd_status mvd_result(mvd_ctx* c, float* out, size_t n_elems) {
         set_error("mvd_result: context not created");
         return MVD_ERR_STATE;
     }
-    const long n = c->boundary == MVD_BOUNDARY_ZERO ? c->uM : c->M;
+    const long n = c->boundary != MVD_BOUNDARY_PERIODIC ? c->uM : c->M;
     if (n_elems < (size_t)n) {
         set_error("mvd_result: buffer holds %zu elements, need %ld", n_elems, n);
         return MVD_ERR_SHAPE;
     }
     DeviceGuard dg(c->device);
     const float* src = c->d_psi;
-    if (c->boundary == MVD_BOUNDARY_ZERO) {
+    if (c->boundary != MVD_BOUNDARY_PERIODIC) {
         MVD_TRY(crop_volume(c, c->d_psi, c->d_stage, c->stream));
         src = c->d_stage;
     }
@@ -1089,7 +1112,7 @@ mvd_status mvd_result_device(mvd_ctx* c, const float** dptr) {
         set_error("mvd_result_device: context not created");
         return MVD_ERR_STATE;
     }
-    if (c->boundary == MVD_BOUNDARY_ZERO) {
+    if (c->boundary != MVD_BOUNDARY_PERIODIC) {
         DeviceGuard dg(c->device);
         MVD_TRY(crop_volume(c, c->d_psi, c->d_stage, c->stream));
         *dptr = c->d_stage;

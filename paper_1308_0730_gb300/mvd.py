@@ -44,8 +44,8 @@ class MvdError(RuntimeError):
 
 MVD_PRECISE, MVD_FAST = 0, 1
 PRECISIONS = {"precise": MVD_PRECISE, "fast": MVD_FAST}
-MVD_BOUNDARY_PERIODIC, MVD_BOUNDARY_ZERO = 0, 1
-BOUNDARIES = {"periodic": MVD_BOUNDARY_PERIODIC, "zero": MVD_BOUNDARY_ZERO}
+MVD_BOUNDARY_PERIODIC, MVD_BOUNDARY_ZERO, MVD_BOUNDARY_MIRROR = 0, 1, 2
+BOUNDARIES = {"periodic": MVD_BOUNDARY_PERIODIC, "zero": MVD_BOUNDARY_ZERO, "mirror": MVD_BOUNDARY_MIRROR}
 
 
 class TuneResult(ctypes.Structure):
@@ -180,7 +180,7 @@ def mvd_create(views, psfs, dims=None, eps: float = 0.0, path="auto", stream=Non
     ``views``: list of float32 arrays ``[Z][Y][X]`` (numpy on the host, or CUDA
     tensors on the device, contiguous). ``psfs``: list of float32 host arrays
     ``[Kz][Ky][Kx]``. ``stream``: a ``torch.cuda.Stream`` or a raw handle.
-    ``boundary``: ``"periodic"`` or ``"zero"`` (see mvd_boundary).
+    ``boundary``: ``"periodic"``, ``"zero"`` or ``"mirror"`` (see mvd_boundary).
     """
     lib = load()
     on_dev = _is_device(views[0])

@@ -88,7 +88,7 @@ def test_create_rejects_invalid_arguments(lib, case, status):
     elif case == "bad_eps":
         kw["eps"] = float("nan")
     elif case == "bad_boundary":
-        kw["boundary"] = 2
+        kw["boundary"] = 3
     if case == "no_views":
         h = ctypes.c_void_p()
         opt = mvd.Options()
