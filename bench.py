@@ -683,56 +683,73 @@ def run_grad(args):
     return 0
 
 
+def _time_steps(args, d, stream, step):
+    """W untimed and K timed calls of ``step()`` (one whole deconvolution from the flat start)
+    on the context's stream: returns (ms per step, launches per step, clock summary)."""
+    import torch
+
+    from paper_1308_0730_gb300 import mvd
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        d.set_estimate(None)
+        step()
+    d.synchronize()
+    launches0 = mvd.mvd_launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            d.set_estimate(None)
+            step()
+        ev1.record(stream)
+        ev1.synchronize()
+    launches = (mvd.mvd_launch_count() - launches0) / args.steps
+    return ev0.elapsed_time(ev1) / args.steps, launches, clk.summary()
+
+
+def _variant_line(args, w, ms, launches, clocks, extra):
+    """The JSON line of a variant of the default workload (the same metric, device-resident)."""
+    X, Y, Z = w.dims
+    units = w.voxels * w.n_views * w.n_iter
+    cfg = {"workload": w.name, "volume": [X, Y, Z], "views": w.n_views, "iterations": w.n_iter}
+    cfg.update(extra)
+    cfg.update({"variant": "efficient", "engine": "fft", "precision": "precise", "l2": "inputs larger than L2"})
+    print(json.dumps({
+        "metric": METRIC, "value": units / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": cfg, "gpu_launches": launches, "clocks": clocks}), flush=True)
+    return 0
+
+
+def _resident_views(w):
+    import torch
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dviews = [torch.from_numpy(v).cuda() for v in w.views]
+    stream.synchronize()
+    return stream, dviews
+
+
 def run_combined(args):
     """The combined (simultaneous) update of Eq. 50 / Eq. 220 with the |V|-th root on the
     256x256x128 four-view workload, 20 iterations, device-resident, precise mode."""
-    import torch
-
     import __graft_entry__
 
     __graft_entry__.build()
     from paper_1308_0730_gb300 import mvd
 
     w = _workload(0)
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        dviews = [torch.from_numpy(v).cuda() for v in w.views]
-    stream.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream, dviews = _resident_views(w)
     with mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft") as d:
-        for _ in range(args.warmup):
-            d.set_estimate(None)
-            d.iterate_combined(w.n_iter)
-        d.synchronize()
-        launches0 = mvd.mvd_launch_count()
-        with ClockSampler(torch.cuda.current_device()) as clk:
-            ev0.record(stream)
-            for _ in range(args.steps):
-                d.set_estimate(None)
-                d.iterate_combined(w.n_iter)
-            ev1.record(stream)
-            ev1.synchronize()
-        launches = (mvd.mvd_launch_count() - launches0) / args.steps
-    ms = ev0.elapsed_time(ev1) / args.steps
-    units = w.voxels * w.n_views * w.n_iter
-    X, Y, Z = w.dims
-    print(json.dumps({
-        "metric": METRIC, "value": units / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "volume": [X, Y, Z], "views": w.n_views, "iterations": w.n_iter,
-                   "update": "combined, geometric mean of the view factors", "variant": "efficient",
-                   "engine": "fft", "precision": "precise", "l2": "inputs larger than L2"},
-        "gpu_launches": launches, "clocks": clk.summary()}), flush=True)
-    return 0
+        ms, launches, clocks = _time_steps(args, d, stream, lambda: d.iterate_combined(w.n_iter))
+    return _variant_line(args, w, ms, launches, clocks, {"update": "combined, geometric mean of the view factors"})
 
 
 def run_weighted(args):
     """Partially overlapping views on the 256x256x128 four-view workload: each view covers 70 % of
     the volume along x or y with cosine edges, weights normalised to the minimal overlap, 20
     sequential iterations, device-resident, precise mode."""
-    import torch
-
     import __graft_entry__
     from synth.workloads import blend_weights
 
@@ -744,38 +761,32 @@ def run_weighted(args):
     boxes = [((0, 0, 0), (int(0.7 * X), Y, Z)), ((int(0.3 * X), 0, 0), (X, Y, Z)),
              ((0, 0, 0), (X, int(0.7 * Y), Z)), ((0, int(0.3 * Y), 0), (X, Y, Z))]
     weights = [blend_weights(w.dims, lo, hi, (8, 8, 8)) for lo, hi in boxes]
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        dviews = [torch.from_numpy(v).cuda() for v in w.views]
-    stream.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream, dviews = _resident_views(w)
     with mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft") as d:
         T = d.set_weights(weights, "min_overlap")
-        for _ in range(args.warmup):
-            d.set_estimate(None)
-            d.iterate(w.n_iter)
-        d.synchronize()
-        launches0 = mvd.mvd_launch_count()
-        with ClockSampler(torch.cuda.current_device()) as clk:
-            ev0.record(stream)
-            for _ in range(args.steps):
-                d.set_estimate(None)
-                d.iterate(w.n_iter)
-            ev1.record(stream)
-            ev1.synchronize()
-        launches = (mvd.mvd_launch_count() - launches0) / args.steps
-    ms = ev0.elapsed_time(ev1) / args.steps
-    units = w.voxels * w.n_views * w.n_iter
-    print(json.dumps({
-        "metric": METRIC, "value": units / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "volume": [X, Y, Z], "views": w.n_views, "iterations": w.n_iter,
-                   "update": "sequential with view weights (partial overlap)", "weight_norm": "min_overlap",
-                   "weight_target": T, "variant": "efficient", "engine": "fft", "precision": "precise",
-                   "l2": "inputs larger than L2"},
-        "gpu_launches": launches, "clocks": clk.summary()}), flush=True)
-    return 0
+        ms, launches, clocks = _time_steps(args, d, stream, lambda: d.iterate(w.n_iter))
+    return _variant_line(args, w, ms, launches, clocks,
+                         {"update": "sequential with view weights (partial overlap)", "weight_norm": "min_overlap",
+                          "weight_target": T})
+
+
+def run_boundary(args):
+    """The 256x256x128 four-view workload with a zero or mirror boundary: the engines run on
+    the grid padded by the PSF half-widths h = (20, 7, 20) (zero: by h, 288 x 270 x 150;
+    mirror: by 2h, 300 x 270 x 180; {2,3,5}-smooth lengths) with the
+    sensitivity-normalised update; the metric counts the user's voxels. 20 sequential
+    iterations, device-resident, precise mode."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1308_0730_gb300 import mvd
+
+    w = _workload(0)
+    stream, dviews = _resident_views(w)
+    with mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft", boundary=args.boundary) as d:
+        ms, launches, clocks = _time_steps(args, d, stream, lambda: d.iterate(w.n_iter))
+    return _variant_line(args, w, ms, launches, clocks,
+                         {"update": f"sequential, {args.boundary} boundary (padded grid, sensitivity-normalised)"})
 
 
 def main():
@@ -790,6 +801,8 @@ def main():
                     help="time the sequential update with partial-overlap view weights instead")
     ap.add_argument("--combined", action="store_true",
                     help="time the combined (simultaneous) update with the geometric mean instead")
+    ap.add_argument("--boundary", choices=["periodic", "zero", "mirror"], default="periodic",
+                    help="zero / mirror: time the sequential update with that boundary (padded grid) instead")
     ap.add_argument("--grad", action="store_true",
                     help="time the PSF-calibration step (8 unrolled iterations, forward + adjoint) instead")
     ap.add_argument("--large", action="store_true",
@@ -809,6 +822,8 @@ def main():
         return run_combined(args)
     if args.weighted:
         return run_weighted(args)
+    if args.boundary != "periodic":
+        return run_boundary(args)
     return run_gpu(args)
 
 
