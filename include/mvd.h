@@ -155,6 +155,23 @@ mvd_status mvd_precompute_kernels(mvd_ctx* ctx, int variant);
 mvd_status mvd_set_estimate(mvd_ctx* ctx, const float* psi, int on_device);
 
 /*
+ * Loads new observed views into the context: the next time point of a series
+ * recorded with the same PSFs. Keeps the compound kernels, the spectra, the
+ * engine choice, view weights and regularisation; recomputes psi0 (the mean
+ * of the new views) and, unless eps was given at create, eps = 1e-4 psi0
+ * (then the captured iteration graphs are rebuilt on the next iterate); resets
+ * psi to the flat psi0 (mvd_set_estimate afterwards warm-starts instead).
+ *   views     n_views pointers to X*Y*Z floats, host or (on_device) device
+ *             pointers; finite and >= 0, not all zero, else MVD_ERR_ARG.
+ * Synchronises the context's stream (it reads the views' sum back). After a
+ * rejected load the context holds invalid views: iterate, autotune, the
+ * unrolled form and batch creation return MVD_ERR_STATE until a load
+ * succeeds. A batch already built from the context keeps the eps it was
+ * built with.
+ */
+mvd_status mvd_set_views(mvd_ctx* ctx, const float* const* views, int on_device);
+
+/*
  * Runs n_iter iterations of the sequential update. One iteration applies the
  * update of every view in `schedule` once, in order (schedule_len entries in
  * [0, n_views)); schedule == NULL or schedule_len == 0 means 0..n_views-1.

@@ -692,6 +692,10 @@ mvd_status mvd_unrolled_forward(mvd_ctx* c, int n_iter) {
         set_error("mvd_unrolled_forward: kernels not precomputed");
         return MVD_ERR_STATE;
     }
+    if (!c->views_ok) {
+        set_error("mvd_unrolled_forward: the last mvd_set_views failed; load valid views first");
+        return MVD_ERR_STATE;
+    }
     if (n_iter < 0) {
         set_error("mvd_unrolled_forward: n_iter < 0");
         return MVD_ERR_ARG;

@@ -513,8 +513,8 @@ mvd_status mvd_batch_create_mode(mvd_ctx* const* ctxs, int n, int n_iter, int mo
             set_error("mvd_batch_create: context %d is NULL", i);
             return MVD_ERR_ARG;
         }
-        if (c->state < 2) {
-            set_error("mvd_batch_create: context %d is not precomputed", i);
+        if (c->state < 2 || !c->views_ok) {
+            set_error("mvd_batch_create: context %d is not precomputed or holds rejected views", i);
             return MVD_ERR_STATE;
         }
         if (c->device != ctxs[0]->device || c->stream != ctxs[0]->stream) {

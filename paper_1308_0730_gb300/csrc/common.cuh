@@ -267,4 +267,6 @@ struct mvd_ctx {
     float* d_stage = nullptr; // user-layout staging volume (uM)
     int path = MVD_PATH_AUTO;
     float psi0 = 0.f, eps = 0.f;
+    bool eps_user = false;  // eps given at create (else 1e-4 psi0 of the current views)
+    bool views_ok = true;   // false after mvd_set_views rejected its input
 };

@@ -574,6 +574,60 @@ int mvd_profile_read(const char** names, unsigned long long* launches, double* m
     return n;
 }
 
+namespace {
+
+// Copies the views into the context (zero-padded on a padded grid), checks
+// them, sets psi0 = their mean over the user's voxels and (unless given at
+// create) eps = 1e-4 psi0, and resets psi to the flat psi0.
+mvd_status load_views(mvd_ctx* c, const float* const* views, int on_device, const char* who) {
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    c->views_ok = false;
+    for (int v = 0; v < c->nv; ++v) {
+        if (!views[v]) {
+            set_error("%s: view %d is NULL", who, v);
+            return MVD_ERR_ARG;
+        }
+        float* dst = c->d_views + (size_t)v * c->M;
+        if (c->boundary != MVD_BOUNDARY_PERIODIC) {
+            const float* src = views[v];
+            if (!on_device) {
+                MVD_CUDA(cudaMemcpyAsync(c->d_stage, views[v], c->uM * sizeof(float), kind, c->stream));
+                src = c->d_stage;
+            }
+            MVD_TRY(pad_volume(c, src, dst, c->stream));
+            continue;
+        }
+        MVD_CUDA(cudaMemcpyAsync(dst, views[v], c->M * sizeof(float), kind, c->stream));
+    }
+    MVD_CUDA(cudaMemsetAsync(c->d_red, 0, 4 * sizeof(double), c->stream));
+    MVD_CUDA(cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->stream));
+    MVD_TRY(view_stats(c->d_views, (long)c->nv * c->M, c->d_red, c->d_flag, c->stream));
+    double sum = 0.0;
+    int bad = 0;
+    MVD_CUDA(cudaMemcpyAsync(&sum, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MVD_CUDA(cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MVD_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad) {
+        set_error("%s: a view holds a negative or non-finite value", who);
+        return MVD_ERR_ARG;
+    }
+    const double mean = sum / ((double)c->uM * c->nv);
+    if (!((float)mean > 0.f)) {
+        set_error("%s: all views are zero", who);
+        return MVD_ERR_ARG;
+    }
+    c->psi0 = (float)mean;
+    const float eps = c->eps_user ? c->eps : (float)(1e-4 * mean);
+    if (eps != c->eps) drop_graphs(c);  // the captured passes carry eps
+    c->eps = eps;
+    MVD_TRY(fill(c->d_psi, c->M, c->psi0, c->stream));
+    MVD_TRY(finish_padding(c, c->d_psi, c->stream));
+    c->views_ok = true;
+    return MVD_OK;
+}
+
+}  // namespace
+
 mvd_status mvd_create(const float* const* views, int n_views, const float* const* psfs, const int* psf_dims,
                       const int dims[3], const mvd_options* opt_in, mvd_ctx** out) {
     clear_error();
@@ -697,56 +751,19 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     if ((st = dev_alloc(&c->d_psf, (size_t)ktotal, "PSFs")) != MVD_OK) return fail(st);
     if ((st = dev_alloc(&c->d_red, 4, "reduction scratch")) != MVD_OK) return fail(st);
     if ((st = dev_alloc(&c->d_flag, 4, "flag")) != MVD_OK) return fail(st);
-    const cudaMemcpyKind kind = opt.views_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (c->boundary != MVD_BOUNDARY_PERIODIC) {
         if ((st = dev_alloc(&c->d_stage, (size_t)c->uM, "staging volume")) != MVD_OK) return fail(st);
         // mirror: the back-projection on the padded grid, before the fold
         if (c->boundary == MVD_BOUNDARY_MIRROR && (st = dev_alloc(&c->d_prod, (size_t)c->M, "back-projection")) != MVD_OK)
             return fail(st);
     }
-    for (int v = 0; v < n_views; ++v) {
-        float* dst = c->d_views + (size_t)v * c->M;
-        if (c->boundary != MVD_BOUNDARY_PERIODIC) {
-            const float* src = views[v];
-            if (!opt.views_on_device) {
-                cudaError_t e = cudaMemcpyAsync(c->d_stage, views[v], c->uM * sizeof(float), kind, c->stream);
-                if (e != cudaSuccess) return fail(cuda_status(e, "copying a view"));
-                src = c->d_stage;
-            }
-            if ((st = pad_volume(c, src, dst, c->stream)) != MVD_OK) return fail(st);
-            continue;
-        }
-        cudaError_t e = cudaMemcpyAsync(dst, views[v], c->M * sizeof(float), kind, c->stream);
-        if (e != cudaSuccess) return fail(cuda_status(e, "copying a view"));
-    }
     {
         cudaError_t e = cudaMemcpyAsync(c->d_psf, psf_h.data(), ktotal * sizeof(float), cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) return fail(cuda_status(e, "copying PSFs"));
-        e = cudaMemsetAsync(c->d_red, 0, 4 * sizeof(double), c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->stream);
-        if (e != cudaSuccess) return fail(cuda_status(e, "clearing scratch"));
     }
-    if ((st = view_stats(c->d_views, (long)n_views * c->M, c->d_red, c->d_flag, c->stream)) != MVD_OK) return fail(st);
-    double sum = 0.0;
-    int bad = 0;
-    {
-        cudaError_t e = cudaMemcpyAsync(&sum, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return fail(cuda_status(e, "reading view statistics"));
-    }
-    if (bad) {
-        set_error("mvd_create: a view holds a negative or non-finite value");
-        return fail(MVD_ERR_ARG);
-    }
-    c->psi0 = (float)(sum / ((double)c->uM * n_views));
-    if (!(c->psi0 > 0.f)) {
-        set_error("mvd_create: all views are zero");
-        return fail(MVD_ERR_ARG);
-    }
-    c->eps = opt.eps > 0.f ? opt.eps : (float)(1e-4 * (sum / ((double)c->uM * n_views)));
-    if ((st = fill(c->d_psi, c->M, c->psi0, c->stream)) != MVD_OK) return fail(st);
-    if ((st = finish_padding(c, c->d_psi, c->stream)) != MVD_OK) return fail(st);
+    c->eps_user = opt.eps > 0.f;
+    c->eps = opt.eps;
+    if ((st = load_views(c, views, opt.views_on_device, "mvd_create")) != MVD_OK) return fail(st);
     c->state = 1;
     *out = c;
     return MVD_OK;
@@ -767,6 +784,20 @@ mvd_status finish_precompute(mvd_ctx* c, int variant) {
 }
 
 }  // namespace
+
+mvd_status mvd_set_views(mvd_ctx* c, const float* const* views, int on_device) {
+    clear_error();
+    if (!c || !views) {
+        set_error("mvd_set_views: NULL argument");
+        return MVD_ERR_ARG;
+    }
+    if (c->state < 1) {
+        set_error("mvd_set_views: context not created");
+        return MVD_ERR_STATE;
+    }
+    DeviceGuard dg(c->device);
+    return load_views(c, views, on_device, "mvd_set_views");
+}
 
 mvd_status mvd_precompute_kernels(mvd_ctx* c, int variant) {
     clear_error();
@@ -894,6 +925,10 @@ mvd_status mvd_iterate(mvd_ctx* c, int n_iter, const int* schedule, int schedule
     }
     if (c->state < 2) {
         set_error("mvd_iterate: kernels not precomputed");
+        return MVD_ERR_STATE;
+    }
+    if (!c->views_ok) {
+        set_error("mvd_iterate: the last mvd_set_views failed; load valid views first");
         return MVD_ERR_STATE;
     }
     if (n_iter < 0 || schedule_len < 0 || (schedule_len > 0 && !schedule)) {
@@ -1056,6 +1091,10 @@ mvd_status mvd_iterate_combined(mvd_ctx* c, int n_iter, int root) {
         set_error("mvd_iterate_combined: kernels not precomputed");
         return MVD_ERR_STATE;
     }
+    if (!c->views_ok) {
+        set_error("mvd_iterate_combined: the last mvd_set_views failed; load valid views first");
+        return MVD_ERR_STATE;
+    }
     if (n_iter < 0) {
         set_error("mvd_iterate_combined: n_iter < 0");
         return MVD_ERR_ARG;
@@ -1179,6 +1218,10 @@ mvd_status mvd_autotune(mvd_ctx* c, const char* cache_path, mvd_tune_result* out
     }
     if (c->state < 2) {
         set_error("mvd_autotune: kernels not precomputed");
+        return MVD_ERR_STATE;
+    }
+    if (!c->views_ok) {
+        set_error("mvd_autotune: the last mvd_set_views failed; load valid views first");
         return MVD_ERR_STATE;
     }
     DeviceGuard dg(c->device);

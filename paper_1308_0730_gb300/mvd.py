@@ -32,7 +32,7 @@ EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_s
            "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy", "mvd_unrolled_forward",
            "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp", "mvd_autotune",
            "mvd_batch_create_mode", "mvd_batch_mode", "mvd_iterate_combined",
-           "mvd_set_weights", "mvd_get_weights", "mvd_set_regularization"]
+           "mvd_set_weights", "mvd_get_weights", "mvd_set_regularization", "mvd_set_views"]
 
 
 class MvdError(RuntimeError):
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_iterate_combined.restype = ci
     lib.mvd_set_weights.argtypes = [vp, ctypes.POINTER(vp), ci, ci, ctypes.c_float, _FP]
     lib.mvd_set_weights.restype = ci
+    lib.mvd_set_views.argtypes = [vp, ctypes.POINTER(vp), ci]
+    lib.mvd_set_views.restype = ci
     lib.mvd_get_weights.argtypes = [vp, ci, _FP, sz]
     lib.mvd_set_regularization.argtypes = [vp, ctypes.c_float]
     lib.mvd_set_regularization.restype = ci
@@ -229,6 +231,16 @@ def mvd_set_estimate(ctx, psi=None):
     else:
         h = _host_f32(psi)
         _check(lib.mvd_set_estimate(ctx, ctypes.c_void_p(h.ctypes.data), 0))
+
+
+def mvd_set_views(ctx, views):
+    """Loads the next time point's views (numpy arrays or CUDA tensors, the context's shape)."""
+    lib = load()
+    on_dev = _is_device(views[0])
+    keep = [v if on_dev else _host_f32(v) for v in views]
+    ptrs = (ctypes.c_void_p * len(keep))(*[ctypes.c_void_p(int(v.data_ptr()) if on_dev else v.ctypes.data)
+                                            for v in keep])
+    _check(lib.mvd_set_views(ctx, ptrs, 1 if on_dev else 0))
 
 
 def mvd_iterate(ctx, n_iter: int, schedule=None):
@@ -447,6 +459,9 @@ class Deconvolver:
 
     def set_estimate(self, psi=None):
         mvd_set_estimate(self.ctx, psi)
+
+    def set_views(self, views):
+        mvd_set_views(self.ctx, views)
 
     def result(self, out=None) -> np.ndarray:
         if out is None:

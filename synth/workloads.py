@@ -305,6 +305,17 @@ def _observe(rng, truth, psfs):
     return views
 
 
+def time_series(w: "Workload", n_points: int, seed: int) -> list:
+    """Views of ``n_points`` later time points of workload ``w``: the object drifts by one voxel
+    along x per time point, recorded with the same PSFs and fresh Poisson noise."""
+    psfs = [p.astype(np.float64) for p in w.psfs]
+    out = []
+    for t in range(n_points):
+        rng = np.random.default_rng(seed + t)
+        out.append(_observe(rng, np.roll(w.truth.astype(np.float64), t, axis=2), psfs))
+    return out
+
+
 def _finish(name, dims, truth, psfs64, views, n_iter, variant="efficient", **meta):
     return Workload(name=name, dims=tuple(dims), views=views,
                     psfs=[p.astype(np.float32) for p in psfs64],

@@ -112,4 +112,5 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.mvd_autotune(None, None, None) == mvd.MVD_ERR_ARG
     assert lib.mvd_unrolled_forward(None, 1) == mvd.MVD_ERR_ARG
     assert lib.mvd_unrolled_backward(None, None, None, None) == mvd.MVD_ERR_ARG
+    assert lib.mvd_set_views(None, None, 0) == mvd.MVD_ERR_ARG
     assert "NULL" in mvd.mvd_last_error()
