@@ -76,7 +76,8 @@ struct FftPlan {
 };
 
 // Radix plan for a {2,3,5}-smooth length; false if L has another prime factor.
-bool make_radix_plan(int L, FftPlan* p);
+// dd: the plan also drives double-float passes (no radix 10 there).
+bool make_radix_plan(int L, FftPlan* p, bool dd);
 
 // ---------------------------------------------------------------------------
 // kernel launchers (defined in the .cu files)

@@ -199,6 +199,26 @@ struct DftDD<5, S> {
     }
 };
 
+template <int S>
+struct Root9<cdd, S> {
+    __device__ __forceinline__ static cdd get(int m) {
+        // cos, sin of 2 pi m / 9 for m = 1, 2, 4, as double-float
+        const double c = m == 1 ? 0.76604444311897803520 : m == 2 ? 0.17364817766693034885 : -0.93969262078590838405;
+        const double s = m == 1 ? 0.64278760968653932632 : m == 2 ? 0.98480775301220805936 : 0.34202014332566873304;
+        return cdd{MVD_DD(c), MVD_DD(S * s)};
+    }
+};
+
+template <int S>
+struct DftDD<6, S> {
+    __device__ __forceinline__ static void run(cdd* v) { dft6<mvd::DftDD, S>(v); }
+};
+
+template <int S>
+struct DftDD<9, S> {
+    __device__ __forceinline__ static void run(cdd* v) { dft9<mvd::DftDD, S>(v); }
+};
+
 // one Stockham butterfly and the multi-line driver, as in fft.cuh
 template <int R, int S>
 __device__ __forceinline__ void stockham_bfly_dd(const cdd* __restrict__ A, cdd* __restrict__ B, int j,
@@ -292,6 +312,8 @@ __device__ __forceinline__ void stage_dd_io(int R, const cdd* A, cdd* B, const c
         case 4: stockham_stage_dd_io<4, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
         case 2: stockham_stage_dd_io<2, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
         case 3: stockham_stage_dd_io<3, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
+        case 6: stockham_stage_dd_io<6, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
+        case 9: stockham_stage_dd_io<9, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
         default: stockham_stage_dd_io<5, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
     }
 }
@@ -339,6 +361,8 @@ __device__ cdd* fft_lines_dd(cdd* A, cdd* B, int nlines, int ls, const FftPlan& 
             case 4: stockham_stage_dd<4, S>(A, B, nlines, ls, p.L, Ns, tw); break;
             case 2: stockham_stage_dd<2, S>(A, B, nlines, ls, p.L, Ns, tw); break;
             case 3: stockham_stage_dd<3, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 6: stockham_stage_dd<6, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 9: stockham_stage_dd<9, S>(A, B, nlines, ls, p.L, Ns, tw); break;
             default: stockham_stage_dd<5, S>(A, B, nlines, ls, p.L, Ns, tw); break;
         }
         __syncthreads();

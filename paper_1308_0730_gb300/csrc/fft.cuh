@@ -140,6 +140,91 @@ struct Dft<5, S> {
 };
 
 // ---------------------------------------------------------------------------
+// composite small DFTs, generic in the element type T (float2 here, complex
+// double-float in dd.cuh) and in the family D of prime-length DFTs
+// ---------------------------------------------------------------------------
+
+// Prime-factor (Good-Thomas) DFTs of lengths 6 = 2 x 3 and 10 = 2 x 5: input
+// n = (N2 n1 + 2 n2) mod N with N1 = 2, output k with k = k1 (mod 2) and
+// k = k2 (mod N2); the exponent n k then splits into a 2-point and an
+// N2-point part, so there are no twiddles between the two. The 2-point DFTs
+// over n1 are the sums (k1 = 0) and differences (k1 = 1) of the pairs below.
+template <template <int, int> class D, int S, typename T>
+__device__ __forceinline__ void dft6(T* v) {
+    T a[3] = {cadd(v[0], v[3]), cadd(v[2], v[5]), cadd(v[4], v[1])};
+    T b[3] = {csub(v[0], v[3]), csub(v[2], v[5]), csub(v[4], v[1])};
+    D<3, S>::run(a);
+    D<3, S>::run(b);
+    v[0] = a[0], v[4] = a[1], v[2] = a[2];
+    v[3] = b[0], v[1] = b[1], v[5] = b[2];
+}
+
+template <template <int, int> class D, int S, typename T>
+__device__ __forceinline__ void dft10(T* v) {
+    T a[5] = {cadd(v[0], v[5]), cadd(v[2], v[7]), cadd(v[4], v[9]), cadd(v[6], v[1]), cadd(v[8], v[3])};
+    T b[5] = {csub(v[0], v[5]), csub(v[2], v[7]), csub(v[4], v[9]), csub(v[6], v[1]), csub(v[8], v[3])};
+    D<5, S>::run(a);
+    D<5, S>::run(b);
+    v[0] = a[0], v[6] = a[1], v[2] = a[2], v[8] = a[3], v[4] = a[4];
+    v[5] = b[0], v[1] = b[1], v[7] = b[2], v[3] = b[3], v[9] = b[4];
+}
+
+// exp(s 2 pi i m / 9) as an element of type T (specialised per type)
+template <typename T, int S>
+struct Root9;
+
+template <int S>
+struct Root9<float2, S> {
+    __device__ __forceinline__ static float2 get(int m) {
+        // cos, sin of 2 pi m / 9 for m = 1, 2, 4
+        const float c = m == 1 ? 0.76604444311897803520f : m == 2 ? 0.17364817766693034885f : -0.93969262078590838405f;
+        const float s = m == 1 ? 0.64278760968653932632f : m == 2 ? 0.98480775301220805936f : 0.34202014332566873304f;
+        return make_float2(c, S * s);
+    }
+};
+
+// Length-9 DFT as 3 x 3 (Cooley-Tukey): 3-point DFTs over n1 of x[3 n1 + n2]
+// (c_n2), twiddles exp(s 2 pi i n2 k1 / 9), 3-point DFTs over n2, output at
+// k1 + 3 k2.
+template <template <int, int> class D, int S, typename T>
+__device__ __forceinline__ void dft9(T* v) {
+    T c0[3] = {v[0], v[3], v[6]};
+    T c1[3] = {v[1], v[4], v[7]};
+    T c2[3] = {v[2], v[5], v[8]};
+    D<3, S>::run(c0);
+    D<3, S>::run(c1);
+    D<3, S>::run(c2);
+    c1[1] = cmul(c1[1], Root9<T, S>::get(1));
+    c2[1] = cmul(c2[1], Root9<T, S>::get(2));
+    c1[2] = cmul(c1[2], Root9<T, S>::get(2));
+    c2[2] = cmul(c2[2], Root9<T, S>::get(4));
+    T r0[3] = {c0[0], c1[0], c2[0]};
+    T r1[3] = {c0[1], c1[1], c2[1]};
+    T r2[3] = {c0[2], c1[2], c2[2]};
+    D<3, S>::run(r0);
+    D<3, S>::run(r1);
+    D<3, S>::run(r2);
+    v[0] = r0[0], v[3] = r0[1], v[6] = r0[2];
+    v[1] = r1[0], v[4] = r1[1], v[7] = r1[2];
+    v[2] = r2[0], v[5] = r2[1], v[8] = r2[2];
+}
+
+template <int S>
+struct Dft<6, S> {
+    __device__ __forceinline__ static void run(float2* v) { dft6<mvd::Dft, S>(v); }
+};
+
+template <int S>
+struct Dft<10, S> {
+    __device__ __forceinline__ static void run(float2* v) { dft10<mvd::Dft, S>(v); }
+};
+
+template <int S>
+struct Dft<9, S> {
+    __device__ __forceinline__ static void run(float2* v) { dft9<mvd::Dft, S>(v); }
+};
+
+// ---------------------------------------------------------------------------
 // one Stockham butterfly (see the file header)
 // ---------------------------------------------------------------------------
 
@@ -205,6 +290,9 @@ __device__ float2* fft_lines(float2* A, float2* B, int nlines, int ls, const Fft
             case 4: stockham_stage<4, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
             case 2: stockham_stage<2, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
             case 3: stockham_stage<3, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
+            case 6: stockham_stage<6, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
+            case 9: stockham_stage<9, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
+            case 10: stockham_stage<10, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
             default: stockham_stage<5, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
         }
         __syncthreads();

@@ -9,24 +9,29 @@ namespace mvd {
 
 namespace {
 
-__global__ void __launch_bounds__(kGenThreads) k_dd_x_forward(DdX a) {
+// generic double-float passes: three blocks per SM (their tiles' shared
+// memory allows three; the registers of the radix-9/10 butterflies would
+// otherwise leave room for two)
+constexpr int kDdGenBlocks = 3;
+
+__global__ void __launch_bounds__(kGenThreads, kDdGenBlocks) k_dd_x_forward(DdX a) {
     extern __shared__ cdd smd[];
     dd_x_forward_tile<false>(a, blockIdx.x, smd);
 }
 
-__global__ void __launch_bounds__(kGenThreads) k_dd_x_ratio(DdX a) {
+__global__ void __launch_bounds__(kGenThreads, kDdGenBlocks) k_dd_x_ratio(DdX a) {
     extern __shared__ cdd smd[];
     dd_x_ratio_tile<false>(a, blockIdx.x, smd);
 }
 
 template <int S>
-__global__ void __launch_bounds__(kGenThreads) k_dd_y(DdY a) {
+__global__ void __launch_bounds__(kGenThreads, kDdGenBlocks) k_dd_y(DdY a) {
     extern __shared__ cdd smd[];
     dd_y_tile<false, S>(a, blockIdx.x, smd);
 }
 
 template <bool MUL>
-__global__ void __launch_bounds__(kGenThreads) k_dd_z(DdZ a) {
+__global__ void __launch_bounds__(kGenThreads, kDdGenBlocks) k_dd_z(DdZ a) {
     extern __shared__ cdd smd[];
     dd_z_tile<false, MUL>(a, blockIdx.x, smd);
 }

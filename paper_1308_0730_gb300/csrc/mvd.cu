@@ -90,35 +90,87 @@ void prof_end(int cls, cudaStream_t st) {
     g_prof.push_back({cls, t_open_ev, e});
 }
 
-bool make_radix_plan(int L, FftPlan* p) {
+namespace {
+
+// Rough cost per point of one Stockham stage of radix R in double-float
+// operations: the small DFT, the twiddle products of (R-1)/R of the points
+// (none in the first stage) and the shared-memory round trip.
+double stage_cost(int R, bool first) {
+    double dft;
+    switch (R) {
+        case 2: dft = 16; break;
+        case 3: dft = 41; break;
+        case 4: dft = 32; break;
+        case 5: dft = 74; break;
+        case 6: dft = 57; break;
+        case 8: dft = 52; break;
+        case 9: dft = 99; break;
+        default: dft = 90; break;  // 10
+    }
+    return dft + (first ? 0.0 : 38.0 * (R - 1) / R) + 40.0;
+}
+
+// cheapest factorisation of n into the allowed radices <= max_r (bit R of
+// `allowed`), in non-increasing order
+void best_plan(int n, int max_r, unsigned allowed, std::vector<int>& cur, double cost, std::vector<int>& best,
+               double& best_cost) {
+    if (n == 1) {
+        if (cost < best_cost) best_cost = cost, best = cur;
+        return;
+    }
+    static const int kRadices[] = {10, 9, 8, 6, 5, 4, 3, 2};
+    for (int R : kRadices) {
+        if (R > max_r || !(allowed >> R & 1u) || n % R != 0 || (int)cur.size() >= kMaxStages) continue;
+        const double c = cost + stage_cost(R, cur.empty());
+        if (c >= best_cost) continue;
+        cur.push_back(R);
+        best_plan(n / R, R, allowed, cur, c, best, best_cost);
+        cur.pop_back();
+    }
+}
+
+}  // namespace
+
+bool make_radix_plan(int L, FftPlan* p, bool dd) {
     p->L = L;
     p->nst = 0;
-    int n = L, a = 0, n3 = 0, n5 = 0;
+    int n = L, a = 0;
     while (n % 2 == 0) n /= 2, ++a;
-    while (n % 3 == 0) n /= 3, ++n3;
-    while (n % 5 == 0) n /= 5, ++n5;
-    if (n != 1) return false;
+    while (n % 3 == 0) n /= 3;
+    while (n % 5 == 0) n /= 5;
+    if (n != 1 || L < 1) return false;
     auto push = [&](int r) {
         if (p->nst < kMaxStages) p->radix[p->nst++] = r;
     };
-    const int q = a / 3, rem = a % 3;
-    if (rem == 0) {
-        for (int i = 0; i < q; ++i) push(8);
-    } else if (rem == 1) {
-        if (q >= 1) {
-            for (int i = 0; i < q - 1; ++i) push(8);
-            push(4);
-            push(4);
+    if (L == (1 << a)) {  // powers of two: radix 8, then 4 4 or 4 or 2 for the rest
+        const int q = a / 3, rem = a % 3;
+        if (rem == 0) {
+            for (int i = 0; i < q; ++i) push(8);
+        } else if (rem == 1) {
+            if (q >= 1) {
+                for (int i = 0; i < q - 1; ++i) push(8);
+                push(4);
+                push(4);
+            } else {
+                push(2);
+            }
         } else {
-            push(2);
+            for (int i = 0; i < q; ++i) push(8);
+            push(4);
         }
-    } else {
-        for (int i = 0; i < q; ++i) push(8);
-        push(4);
+        return true;
     }
-    for (int i = 0; i < n3; ++i) push(3);
-    for (int i = 0; i < n5; ++i) push(5);
-    return p->nst < kMaxStages;
+    // mixed lengths: the cheapest product of radices 2..10 (composite 6, 9, 10
+    // cut the number of stages), the largest radix first (it has no twiddles);
+    // without 10 where double-float passes run (their registers)
+    std::vector<int> cur, best;
+    double best_cost = 1e300;
+    const unsigned allowed = (1u << 2) | (1u << 3) | (1u << 4) | (1u << 5) | (1u << 6) | (1u << 8) | (1u << 9) |
+                             (dd ? 0u : (1u << 10));
+    best_plan(L, 10, allowed, cur, 0.0, best, best_cost);
+    if (best.empty()) return false;
+    for (int r : best) push(r);
+    return true;
 }
 
 }  // namespace mvd
@@ -227,7 +279,8 @@ mvd_status setup_fft(mvd_ctx* c) {
     // MVD_FFT_GENERIC=1 forces the generic kernels (used to test both engines)
     const char* gen = std::getenv("MVD_FFT_GENERIC");
     g.fast = !(gen && gen[0] == '1');
-    if (!make_radix_plan(g.X, &g.px) || !make_radix_plan(g.Y, &g.py) || !make_radix_plan(g.Z, &g.pz)) {
+    if (!make_radix_plan(g.X, &g.px, c->precise) || !make_radix_plan(g.Y, &g.py, c->precise) ||
+        !make_radix_plan(g.Z, &g.pz, c->precise)) {
         set_error("FFT engine needs {2,3,5}-smooth dims, got %d x %d x %d", g.X, g.Y, g.Z);
         return MVD_ERR_UNSUPPORTED;
     }
@@ -892,14 +945,14 @@ mvd_status mvd_set_estimate(mvd_ctx* c, const float* psi, int on_device) {
         return MVD_ERR_STATE;
     }
     DeviceGuard dg(c->device);
-    const bool zero = c->boundary != MVD_BOUNDARY_PERIODIC;  // padded grid
+    const bool padded = c->boundary != MVD_BOUNDARY_PERIODIC;
     if (!psi) {
         MVD_TRY(fill(c->d_psi, c->M, c->psi0, c->stream));
         return finish_padding(c, c->d_psi, c->stream);
     }
     // on a padded grid: stage the user-layout volume, check it, pad it
-    float* dst = zero ? c->d_stage : c->d_psi;
-    const long n = zero ? c->uM : c->M;
+    float* dst = padded ? c->d_stage : c->d_psi;
+    const long n = padded ? c->uM : c->M;
     MVD_CUDA(cudaMemcpyAsync(dst, psi, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              c->stream));
     MVD_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
@@ -912,7 +965,7 @@ mvd_status mvd_set_estimate(mvd_ctx* c, const float* psi, int on_device) {
         finish_padding(c, c->d_psi, c->stream);
         return MVD_ERR_ARG;
     }
-    if (!zero) return MVD_OK;
+    if (!padded) return MVD_OK;
     MVD_TRY(pad_volume(c, c->d_stage, c->d_psi, c->stream));
     return finish_padding(c, c->d_psi, c->stream);
 }

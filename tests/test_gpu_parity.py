@@ -279,6 +279,25 @@ def test_fft_lengths(mvd, monkeypatch, dims, engine):
     assert rel_err(got, want) < PARITY_TOL, err_report(got, want)
 
 
+# Mixed lengths whose plans take every radix of the generic passes: 2, 3, 4,
+# 5, 8 and the composite 6 and 9 (both precisions) and 10 (FP32 only), on
+# every axis, in both precisions.
+MIXED_CASES = [(6, 9, 10), (12, 18, 20), (27, 30, 36), (45, 50, 54), (60, 81, 20), (100, 40, 15), (270, 8, 6),
+               (8, 150, 12), (10, 12, 180)]
+
+
+@pytest.mark.parametrize("precision", ["precise", "fast"])
+@pytest.mark.parametrize("dims", MIXED_CASES)
+def test_mixed_radix_lengths(mvd, dims, precision):
+    w = synth.small_case(300 + sum(dims), dims=dims, n_views=2, boxes=[(3, 5, 3), (5, 3, 5)], n_iter=2,
+                         asymmetric=True)
+    want, _ = oracle.deconvolve(w.views, w.psfs, 2, "efficient")
+    with mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", precision=precision) as d:
+        d.iterate(2)
+        got = d.result()
+    assert rel_err(got, want) < PARITY_TOL, err_report(got, want)
+
+
 def test_graph_replay_matches_plain_launches(mvd, monkeypatch):
     """On a non-default stream one iteration is captured as a CUDA graph and replayed; the
     result must equal the one-by-one launches bit for bit, and match the oracle."""
