@@ -44,13 +44,15 @@ L2_BYTES = 129 * 2 ** 20
 def _kernel_bytes(X, Y, Z, precise=True):
     M = X * Y * Z
     spec = 8 * (X // 2 + 1) * Y * Z  # FP32 half spectrum; double-float is 2 * spec
-    if precise:  # the update reads the double-float spectrum
+    if precise:  # double-float forward blur, FP32 back-projection
         return {
             "dd_x_forward": 4 * M + 2 * spec,       # read psi, write S2
             "dd_y": 4 * spec,                       # read S2, write S2
             "dd_z_mul": 6 * spec,                   # read S2 and a double-float kernel spectrum, write S2
-            "dd_x_ratio": 4 * spec + 4 * M,         # read S2 and phi, write S2
-            "x_update": 2 * spec + 8 * M,           # read S2, read and write psi
+            "dd_x_ratio": 3 * spec + 4 * M,         # read S2 and phi, write the FP32 spectrum S
+            "y": 2 * spec,                          # read S, write S
+            "z_mul": 3 * spec,                      # read S and the FP32 kernel spectrum, write S
+            "x_update": spec + 8 * M,               # read S, read and write psi
         }
     return {
         "x_forward": 4 * M + spec,          # read psi, write S
@@ -73,6 +75,7 @@ def _kernel_bytes(X, Y, Z, precise=True):
 DD_FFT_OPS = 38.0
 FP32_FFT_OPS = 5.0
 DD_CMUL_OPS = 38.0
+FP32_CMUL_OPS = 6.0
 
 
 def _kernel_alu_ops(X, Y, Z):
@@ -86,6 +89,8 @@ def _kernel_alu_ops(X, Y, Z):
         "dd_y": Xh * Z * dd(Y),
         "dd_z_mul": Xh * Y * (2 * dd(Z) + DD_CMUL_OPS * Z),  # forward, times the spectrum, inverse
         "dd_x_ratio": (Y * Z / 2) * (dd(X) + f32(X)),         # inverse in double-float, r - 1 forward in FP32
+        "y": Xh * Z * f32(Y),
+        "z_mul": Xh * Y * (2 * f32(Z) + FP32_CMUL_OPS * Z),
         "x_update": (Y * Z / 2) * f32(X),
     }
 
@@ -450,7 +455,7 @@ def run_gpu(args):
             "update_effective_hbm_frac": (12.0 * units_per_step * args.steps / (ms * 1e-3) / 1e9) / peak,
             "kernels": per_kernel,
             "profiled_ms_per_step": ms_profiled / args.steps,
-            "precision": "double-float (pairs of FP32) for the forward blur and the back-projection's y and z passes; FP32 x passes of the back-projection",
+            "precision": "double-float (pairs of FP32) for the forward blur b = psi * P_v; FP32 back-projection of r - 1",
             "fast_fp32": {"value": ws * units_per_step * args.steps / (ms_fast * 1e-3) / 1e9, "unit": UNIT,
                           "ms_per_step": ms_fast / args.steps,
                           "kernels": fast_kernels, "roofline": fast_roof,

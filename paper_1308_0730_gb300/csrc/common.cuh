@@ -121,7 +121,9 @@ mvd_status dd_forward_real(const FftGeom& g, const float* src, cdd* S2, cudaStre
 mvd_status dd_y(const FftGeom& g, cdd* S2, int inverse, cudaStream_t st);
 mvd_status dd_z_mul(const FftGeom& g, cdd* S2, const cdd* K2, cudaStream_t st);
 mvd_status dd_z_forward_scaled(const FftGeom& g, cdd* S2, double scale, cudaStream_t st);
-mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cudaStream_t st);
+// the inverse x of b (double-float) -> r - 1 -> FP32 forward x, written to the
+// FP32 spectrum S when given, else exactly into S2
+mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cudaStream_t st, float2* S = nullptr);
 // double-float spectrum -> real volume (x inverse, rounded to FP32); X of 32..1024, a power of two
 mvd_status dd_x_inverse_real(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st);
 bool dd_fast_x(const FftGeom& g);
@@ -228,7 +230,8 @@ struct mvd_ctx {
     float2* d_tw = nullptr;  // twiddle tables (x, y, z)
     float2* d_S = nullptr;   // work spectrum Xh*Y*Z
     // kernel spectra, each Xh*Y*Z, slot 2v = P_v and 2v+1 = P_v^comp: FP32
-    // in fast mode (d_K), double-float in precise mode (d_KP2)
+    // in fast mode (d_K), double-float in precise mode (d_KP2); precise mode
+    // also keeps P_v^comp in FP32 for the back-projection, slot v of d_K
     float2* d_K = nullptr;
     mvd::cdd* d_tw2 = nullptr;  // double-float twiddle tables (x, y, z)
     mvd::cdd* d_S2 = nullptr;   // double-float work spectrum (precise mode)

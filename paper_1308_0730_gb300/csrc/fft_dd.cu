@@ -152,11 +152,12 @@ mvd_status dd_x_inverse_real(const FftGeom& g, const cdd* S2, float* dst, cudaSt
     return rc;
 }
 
-mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cudaStream_t st) {
+mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cudaStream_t st, float2* S) {
     if (g.fast && dd_fast_length(g.X)) {
         mvd_status rc = MVD_ERR_UNSUPPORTED;
         DdXFast a = ddf_args(g);
         a.S2 = S2;
+        a.S = S;
         a.phi = phi;
         a.eps = eps;
         with_dd_len(g.X, [&](auto Lc) {
@@ -168,6 +169,7 @@ mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cu
     }
     DdX a = dd_x_args(g.X, g.YZ, g.px, g.tw2x);
     a.S2 = S2;
+    a.S = S;
     a.phi = phi;
     a.eps = eps;
     return launch(k_dd_x_ratio, a, dd_x_tiles(g.X, g.YZ), dd_x_smem(g.X), st, "dd x ratio", KC_DD_X_RATIO);

@@ -47,6 +47,7 @@ struct DdX {
     cdd* S2;                // double-float spectrum
     const float* phi;       // observed view
     float eps;
+    float2* S;              // ratio: the FP32 spectrum of r - 1 goes here when set, else into S2
 };
 
 __host__ __device__ inline DdX dd_x_args(int X, long YZ, const FftPlan& plan, const cdd* tw2) {
@@ -155,7 +156,10 @@ __device__ void dd_x_ratio_tile(const DdX& a, long tile, cdd* sm) {
             const float2 d = csub(zk, zm);
             val = make_float2(0.5f * d.y, -0.5f * d.x);
         }
-        cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, cdd{dd_from(val.x), dd_from(val.y)});
+        if (a.S)
+            a.S[(long)k * a.YZ + rho0 + row] = val;
+        else
+            cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, cdd{dd_from(val.x), dd_from(val.y)});
     }
 }
 

@@ -235,6 +235,7 @@ struct DdXFast {
     const cdd* tw2;
     FftPlan plan;      // FP32 plan of X (radices + FP32 twiddles) for the r - 1 transform
     float* dst;        // real rows written by the plain inverse
+    float2* S;         // ratio: the FP32 spectrum of r - 1 goes here when set, else into S2
 };
 
 // unpack the packed forward double-float spectra (natural order in registers
@@ -380,7 +381,10 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
             const float2 d = csub(zk, zm);
             val = make_float2(0.5f * d.y, -0.5f * d.x);
         }
-        cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, cdd{dd_from(val.x), dd_from(val.y)});
+        if (a.S)
+            a.S[(long)k * a.YZ + rho0 + row] = val;
+        else
+            cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, cdd{dd_from(val.x), dd_from(val.y)});
     }
 }
 

@@ -301,7 +301,7 @@ mvd_status setup_fft(mvd_ctx* c) {
     g.pz.tw = c->d_tw + g.X + g.Y;
     const size_t ns = (size_t)g.Xh * g.YZ;
     MVD_TRY(dev_alloc(&c->d_S, ns, "work spectrum"));
-    if (!c->precise) MVD_TRY(dev_alloc(&c->d_K, ns * 2 * c->nv, "kernel spectra"));
+    MVD_TRY(dev_alloc(&c->d_K, ns * (c->precise ? 1 : 2) * c->nv, "kernel spectra"));
     const float inv_m = (float)(1.0 / (double)c->M);
     if (c->precise) {
         // double-float twiddles: hi = fl32(w), lo = fl32(w - hi), w in FP64
@@ -326,7 +326,7 @@ mvd_status setup_fft(mvd_ctx* c) {
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_KP2), ns * 2 * c->nv, "double-float kernel spectra"));
     }
     // kernel spectra, scaled by 1/M: slot 2v = P_v, 2v+1 = P_v^comp (FP32 in
-    // fast mode, double-float in precise mode)
+    // fast mode, double-float in precise mode, plus P_v^comp in FP32)
     for (int v = 0; v < c->nv; ++v) {
         for (int which = 0; which < 2; ++which) {
             const float* k = (which == 0 ? c->d_psf : c->d_comp) + c->koff[v];
@@ -336,9 +336,9 @@ mvd_status setup_fft(mvd_ctx* c) {
                 MVD_TRY(dd_forward_real(g, c->d_r, dst, c->stream));
                 MVD_TRY(dd_y(g, dst, 0, c->stream));
                 MVD_TRY(dd_z_forward_scaled(g, dst, 1.0 / (double)c->M, c->stream));
-                continue;
+                if (which == 0) continue;
             }
-            float2* dst = c->d_K + ns * (2 * v + which);
+            float2* dst = c->d_K + ns * (c->precise ? v : 2 * v + which);
             MVD_TRY(fft_forward_real(g, c->d_r, dst, c->stream));
             MVD_TRY(fft_y(g, dst, 0, c->stream));
             MVD_TRY(fft_z_forward_scaled(g, dst, inv_m, c->stream));
@@ -490,29 +490,23 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
         cdd* S2 = c->d_S2;
         const float4* K4 = reinterpret_cast<const float4*>(c->d_KP2);
         const cdd* Kp2 = reinterpret_cast<const cdd*>(K4 + ns * (2 * v));
-        const cdd* Kc2 = reinterpret_cast<const cdd*>(K4 + ns * (2 * v + 1));
         MVD_TRY(dd_forward_real(g, c->d_psi, S2, c->stream));
         MVD_TRY(dd_y(g, S2, 0, c->stream));
         MVD_TRY(dd_z_mul(g, S2, Kp2, c->stream));
         MVD_TRY(dd_y(g, S2, 1, c->stream));
-        MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream));
-        MVD_TRY(dd_y(g, S2, 0, c->stream));
-        MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
-        MVD_TRY(dd_y(g, S2, 1, c->stream));
-        if (mirror) {
-            MVD_TRY(fft_x_inverse_dd(g, S2, c->d_prod, c->stream));
-            return mirror_update(c, c->d_prod, 1.f, inv_s, c->stream);
-        }
-        if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream, inv_s);
-        return done(fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
+        // the ratio pass hands r - 1 over as an FP32 spectrum: the
+        // back-projection c = 1 + (r - 1) * P_v^comp runs in FP32 (its error
+        // is relative to c ~ 1, not to the volume's norm)
+        MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream, c->d_S));
+    } else {
+        const float2* Kp = c->d_K + ns * (2 * v);
+        MVD_TRY(fft_forward_real(g, c->d_psi, c->d_S, c->stream));
+        MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
+        MVD_TRY(fft_z_mul(g, c->d_S, Kp, c->stream));
+        MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
+        MVD_TRY(fft_x_ratio(g, c->d_S, phi, c->eps, c->stream));
     }
-    const float2* Kp = c->d_K + ns * (2 * v);
-    const float2* Kc = c->d_K + ns * (2 * v + 1);
-    MVD_TRY(fft_forward_real(g, c->d_psi, c->d_S, c->stream));
-    MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
-    MVD_TRY(fft_z_mul(g, c->d_S, Kp, c->stream));
-    MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
-    MVD_TRY(fft_x_ratio(g, c->d_S, phi, c->eps, c->stream));
+    const float2* Kc = c->d_K + ns * (c->precise ? v : 2 * v + 1);
     MVD_TRY(fft_y(g, c->d_S, 0, c->stream));
     MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
     MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
