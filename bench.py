@@ -44,15 +44,13 @@ L2_BYTES = 129 * 2 ** 20
 def _kernel_bytes(X, Y, Z, precise=True):
     M = X * Y * Z
     spec = 8 * (X // 2 + 1) * Y * Z  # FP32 half spectrum; double-float is 2 * spec
-    if precise:  # double-float forward blur, FP32 back-projection
+    if precise:  # the update reads the double-float spectrum
         return {
             "dd_x_forward": 4 * M + 2 * spec,       # read psi, write S2
             "dd_y": 4 * spec,                       # read S2, write S2
             "dd_z_mul": 6 * spec,                   # read S2 and a double-float kernel spectrum, write S2
-            "dd_x_ratio": 3 * spec + 4 * M,         # read S2 and phi, write the FP32 spectrum S
-            "y": 2 * spec,                          # read S, write S
-            "z_mul": 3 * spec,                      # read S and the FP32 kernel spectrum, write S
-            "x_update": spec + 8 * M,               # read S, read and write psi
+            "dd_x_ratio": 4 * spec + 4 * M,         # read S2 and phi, write S2
+            "x_update": 2 * spec + 8 * M,           # read S2, read and write psi
         }
     return {
         "x_forward": 4 * M + spec,          # read psi, write S
@@ -344,6 +342,26 @@ def run_gpu(args):
     mvd.mvd_profile_enable(False)
     fast.close()
 
+    # the same steps with the FP32 back-projection (MVD_MIXED), for comparison
+    mixed = mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft", device=local, precision="mixed")
+
+    def mixed_step():
+        mixed.set_estimate(None)
+        mixed.iterate(w.n_iter)
+
+    for _ in range(args.warmup):
+        mixed_step()
+    ev6 = torch.cuda.Event(enable_timing=True)
+    ev7 = torch.cuda.Event(enable_timing=True)
+    ev6.record(stream)
+    for _ in range(args.steps):
+        mixed_step()
+    ev7.record(stream)
+    ev7.synchronize()
+    ms_mixed = ev6.elapsed_time(ev7)
+    psi_mixed = mixed.result()
+    mixed.close()
+
     # --- end to end through the public API from pinned host buffers ---
     # A time series with fixed PSFs: one context; every step loads the time
     # point's views from pinned host memory (mvd_set_views: H2D, view mean,
@@ -455,13 +473,19 @@ def run_gpu(args):
             "update_effective_hbm_frac": (12.0 * units_per_step * args.steps / (ms * 1e-3) / 1e9) / peak,
             "kernels": per_kernel,
             "profiled_ms_per_step": ms_profiled / args.steps,
-            "precision": "double-float (pairs of FP32) for the forward blur b = psi * P_v; FP32 back-projection of r - 1",
+            "precision": "double-float (pairs of FP32) for the forward blur and the back-projection's y and z passes; FP32 x passes of the back-projection",
             "fast_fp32": {"value": ws * units_per_step * args.steps / (ms_fast * 1e-3) / 1e9, "unit": UNIT,
                           "ms_per_step": ms_fast / args.steps,
                           "kernels": fast_kernels, "roofline": fast_roof,
                           "max_rel_diff_vs_precise": float(np.max(np.abs(psi_fast.astype(np.float64) - psi_dev)
                                                                   / np.maximum(np.abs(psi_dev.astype(np.float64)),
                                                                                1e-3 * np.abs(psi_dev).max())))},
+            "mixed": {"value": ws * units_per_step * args.steps / (ms_mixed * 1e-3) / 1e9, "unit": UNIT,
+                      "ms_per_step": ms_mixed / args.steps,
+                      "precision": "double-float forward blur, FP32 back-projection (not held to 1e-4)",
+                      "max_rel_diff_vs_precise": float(np.max(np.abs(psi_mixed.astype(np.float64) - psi_dev)
+                                                              / np.maximum(np.abs(psi_dev.astype(np.float64)),
+                                                                           1e-3 * np.abs(psi_dev).max())))},
             "clocks": clk.summary(),
             "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{len(cpu_times)} view updates (view 0) of the {X}x{Y}x{Z} workload, "

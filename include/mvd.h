@@ -71,17 +71,21 @@ typedef enum { MVD_PATH_AUTO = 0, MVD_PATH_DIRECT = 1, MVD_PATH_FFT = 2 } mvd_pa
 
 /* Arithmetic of the FFT engine.
  *   MVD_PRECISE: double-float (pairs of FP32, about 48 significant bits) for
- *     the whole forward blur b = psi * P_v. FP32 FFT rounding is absolute (it
+ *     the whole forward blur b = psi * P_v and for the back-projection's y, z
+ *     and inverse x passes; the back-projection's forward x pass transforms
+ *     r - 1 in FP32 (c = (r - 1) * K + 1 holds because K sums to 1, and r - 1
+ *     is small where the estimate fits). FP32 FFT rounding is absolute (it
  *     scales with the whole volume's norm), so in FP32 the dim voxels of b
  *     carry large relative errors that the ratio phi / b and the iteration
- *     amplify; double-float removes them. The back-projection runs in FP32 on
- *     r - 1 (c = (r - 1) * K + 1 holds because K sums to 1): its rounding is
- *     absolute against r - 1, small where the estimate fits, and enters the
- *     update as a relative error of the factor c ~ 1 at every voxel, dim or
- *     bright.
+ *     amplify; double-float removes them.
+ *   MVD_MIXED: the forward blur as in MVD_PRECISE, the back-projection in FP32
+ *     (1.3x faster). Its rounding is absolute against r - 1: within 1e-4 of
+ *     an exact computation where r - 1 stays moderate, but a count where b is
+ *     near eps (low-count data, no background) makes |r - 1| large and its
+ *     rounding spreads over the volume (4e-4 seen after 15 iterations).
  *   MVD_FAST: everything in FP32 (faster; after tens of iterations dim voxels
  *     differ from an exact computation by about 1e-3 relative). */
-typedef enum { MVD_PRECISE = 0, MVD_FAST = 1 } mvd_precision;
+typedef enum { MVD_PRECISE = 0, MVD_FAST = 1, MVD_MIXED = 2 } mvd_precision;
 
 /* How the image convolutions continue the volume past its faces.
  *   MVD_BOUNDARY_PERIODIC: periodic (circular) convolution on the X*Y*Z grid.

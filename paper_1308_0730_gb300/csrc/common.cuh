@@ -226,12 +226,13 @@ struct mvd_ctx {
 
     // FFT engine
     mvd::FftGeom geom{};
-    int precise = 1;         // forward blur in double-float (MVD_PRECISE)
+    int precise = 1;         // 1 MVD_PRECISE, 2 MVD_MIXED (double-float forward blur), 0 MVD_FAST
     float2* d_tw = nullptr;  // twiddle tables (x, y, z)
     float2* d_S = nullptr;   // work spectrum Xh*Y*Z
     // kernel spectra, each Xh*Y*Z, slot 2v = P_v and 2v+1 = P_v^comp: FP32
-    // in fast mode (d_K), double-float in precise mode (d_KP2); precise mode
-    // also keeps P_v^comp in FP32 for the back-projection, slot v of d_K
+    // in fast mode (d_K), double-float in precise and mixed mode (d_KP2);
+    // mixed mode also keeps P_v^comp in FP32 for its back-projection, slot v
+    // of d_K
     float2* d_K = nullptr;
     mvd::cdd* d_tw2 = nullptr;  // double-float twiddle tables (x, y, z)
     mvd::cdd* d_S2 = nullptr;   // double-float work spectrum (precise mode)

@@ -301,7 +301,7 @@ mvd_status setup_fft(mvd_ctx* c) {
     g.pz.tw = c->d_tw + g.X + g.Y;
     const size_t ns = (size_t)g.Xh * g.YZ;
     MVD_TRY(dev_alloc(&c->d_S, ns, "work spectrum"));
-    MVD_TRY(dev_alloc(&c->d_K, ns * (c->precise ? 1 : 2) * c->nv, "kernel spectra"));
+    if (c->precise != 1) MVD_TRY(dev_alloc(&c->d_K, ns * (c->precise ? 1 : 2) * c->nv, "kernel spectra"));
     const float inv_m = (float)(1.0 / (double)c->M);
     if (c->precise) {
         // double-float twiddles: hi = fl32(w), lo = fl32(w - hi), w in FP64
@@ -326,7 +326,8 @@ mvd_status setup_fft(mvd_ctx* c) {
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_KP2), ns * 2 * c->nv, "double-float kernel spectra"));
     }
     // kernel spectra, scaled by 1/M: slot 2v = P_v, 2v+1 = P_v^comp (FP32 in
-    // fast mode, double-float in precise mode, plus P_v^comp in FP32)
+    // fast mode, double-float in precise and mixed mode, plus P_v^comp in FP32
+    // in mixed mode)
     for (int v = 0; v < c->nv; ++v) {
         for (int which = 0; which < 2; ++which) {
             const float* k = (which == 0 ? c->d_psf : c->d_comp) + c->koff[v];
@@ -336,7 +337,7 @@ mvd_status setup_fft(mvd_ctx* c) {
                 MVD_TRY(dd_forward_real(g, c->d_r, dst, c->stream));
                 MVD_TRY(dd_y(g, dst, 0, c->stream));
                 MVD_TRY(dd_z_forward_scaled(g, dst, 1.0 / (double)c->M, c->stream));
-                if (which == 0) continue;
+                if (which == 0 || c->precise == 1) continue;
             }
             float2* dst = c->d_K + ns * (c->precise ? v : 2 * v + which);
             MVD_TRY(fft_forward_real(g, c->d_r, dst, c->stream));
@@ -364,7 +365,7 @@ struct TuneChoice {
 
 std::string tune_key(const mvd_ctx* c) {
     std::string k = "mvd-tune-v1 dims " + std::to_string(c->dims[0]) + " " + std::to_string(c->dims[1]) + " " +
-                    std::to_string(c->dims[2]) + " precision " + std::to_string(c->precise ? 0 : 1) + " boxes";
+                    std::to_string(c->dims[2]) + " precision " + std::to_string(c->precise == 1 ? MVD_PRECISE : c->precise == 2 ? MVD_MIXED : MVD_FAST) + " boxes";
     for (int v = 0; v < c->nv; ++v)
         for (int a = 0; a < 3; ++a) k += " " + std::to_string(c->kd[3 * v + a]);
     int dev = 0;
@@ -494,10 +495,27 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
         MVD_TRY(dd_y(g, S2, 0, c->stream));
         MVD_TRY(dd_z_mul(g, S2, Kp2, c->stream));
         MVD_TRY(dd_y(g, S2, 1, c->stream));
-        // the ratio pass hands r - 1 over as an FP32 spectrum: the
-        // back-projection c = 1 + (r - 1) * P_v^comp runs in FP32 (its error
-        // is relative to c ~ 1, not to the volume's norm)
-        MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream, c->d_S));
+        if (c->precise == 2) {
+            // MVD_MIXED: the ratio pass hands r - 1 over as an FP32 spectrum
+            // and the back-projection runs in FP32
+            MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream, c->d_S));
+        } else {
+            // MVD_PRECISE: the FP32 spectrum of r - 1 is stored exactly as
+            // double-float and the back-projection's y and z passes run in
+            // double-float, so no rounding of a large |r - 1| (a count where b
+            // is near eps) spreads over the volume
+            const cdd* Kc2 = reinterpret_cast<const cdd*>(K4 + ns * (2 * v + 1));
+            MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream));
+            MVD_TRY(dd_y(g, S2, 0, c->stream));
+            MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
+            MVD_TRY(dd_y(g, S2, 1, c->stream));
+            if (mirror) {
+                MVD_TRY(fft_x_inverse_dd(g, S2, c->d_prod, c->stream));
+                return mirror_update(c, c->d_prod, 1.f, inv_s, c->stream);
+            }
+            if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream, inv_s);
+            return done(fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
+        }
     } else {
         const float2* Kp = c->d_K + ns * (2 * v);
         MVD_TRY(fft_forward_real(g, c->d_psi, c->d_S, c->stream));
@@ -694,7 +712,7 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
         set_error("mvd_create: dims must be >= 1");
         return MVD_ERR_SHAPE;
     }
-    if (opt.precision != MVD_PRECISE && opt.precision != MVD_FAST) {
+    if (opt.precision != MVD_PRECISE && opt.precision != MVD_FAST && opt.precision != MVD_MIXED) {
         set_error("mvd_create: unknown precision %d", opt.precision);
         return MVD_ERR_ARG;
     }
@@ -783,7 +801,7 @@ mvd_status mvd_create(const float* const* views, int n_views, const float* const
     c->ktotal = ktotal;
     c->psf_sum = psf_sum;
     c->path_opt = opt.path;
-    c->precise = opt.precision == MVD_PRECISE ? 1 : 0;
+    c->precise = opt.precision == MVD_PRECISE ? 1 : opt.precision == MVD_MIXED ? 2 : 0;
 
     auto fail = [&](mvd_status st) {
         cudaStreamSynchronize(c->stream);

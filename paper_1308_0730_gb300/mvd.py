@@ -42,8 +42,8 @@ class MvdError(RuntimeError):
         self.status = status
 
 
-MVD_PRECISE, MVD_FAST = 0, 1
-PRECISIONS = {"precise": MVD_PRECISE, "fast": MVD_FAST}
+MVD_PRECISE, MVD_FAST, MVD_MIXED = 0, 1, 2
+PRECISIONS = {"precise": MVD_PRECISE, "fast": MVD_FAST, "mixed": MVD_MIXED}
 MVD_BOUNDARY_PERIODIC, MVD_BOUNDARY_ZERO, MVD_BOUNDARY_MIRROR = 0, 1, 2
 BOUNDARIES = {"periodic": MVD_BOUNDARY_PERIODIC, "zero": MVD_BOUNDARY_ZERO, "mirror": MVD_BOUNDARY_MIRROR}
 
