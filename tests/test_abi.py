@@ -63,6 +63,7 @@ def _good():
     ("bad_path", mvd.MVD_ERR_ARG),
     ("bad_eps", mvd.MVD_ERR_ARG),
     ("bad_boundary", mvd.MVD_ERR_ARG),
+    ("bad_precision", mvd.MVD_ERR_ARG),
 ])
 def test_create_rejects_invalid_arguments(lib, case, status):
     views, psfs = _good()
@@ -89,6 +90,8 @@ def test_create_rejects_invalid_arguments(lib, case, status):
         kw["eps"] = float("nan")
     elif case == "bad_boundary":
         kw["boundary"] = 3
+    elif case == "bad_precision":
+        kw["precision"] = 3
     if case == "no_views":
         h = ctypes.c_void_p()
         opt = mvd.Options()
