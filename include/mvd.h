@@ -161,7 +161,9 @@ mvd_status mvd_set_estimate(mvd_ctx* ctx, const float* psi, int on_device);
 
 /*
  * Loads new observed views into the context: the next time point of a series
- * recorded with the same PSFs. Keeps the compound kernels, the spectra, the
+ * recorded with the same PSFs (the paper's time-lapse recordings of hundreds
+ * of time points, processed in parallel per time point; main text and the
+ * table of experiments). Keeps the compound kernels, the spectra, the
  * engine choice, view weights and regularisation; recomputes psi0 (the mean
  * of the new views) and, unless eps was given at create, eps = 1e-4 psi0
  * (then the captured iteration graphs are rebuilt on the next iterate); resets
