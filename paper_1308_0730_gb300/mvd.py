@@ -153,6 +153,19 @@ def _host_f32(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float32)
 
 
+def _check_volumes(vols, shape, what, count=None):
+    """The library reads X*Y*Z floats behind every volume pointer, so each volume must have
+    exactly ``shape`` ([Z][Y][X]); device tensors are read as they are and must also be
+    contiguous float32. Raises ValueError otherwise."""
+    if count is not None and len(vols) != count:
+        raise ValueError(f"expected {count} {what}s, got {len(vols)}")
+    for i, v in enumerate(vols):
+        if tuple(v.shape) != tuple(shape):
+            raise ValueError(f"{what} {i} has shape {tuple(v.shape)}, expected {tuple(shape)}")
+        if _is_device(v) and (str(v.dtype) != "torch.float32" or not v.is_contiguous()):
+            raise ValueError(f"{what} {i}: a device tensor must be contiguous float32")
+
+
 def mvd_last_error() -> str:
     return (load().mvd_last_error() or b"").decode()
 
@@ -186,6 +199,8 @@ def mvd_create(views, psfs, dims=None, eps: float = 0.0, path="auto", stream=Non
     """
     lib = load()
     on_dev = _is_device(views[0])
+    expect = tuple(views[0].shape) if dims is None else (int(dims[2]), int(dims[1]), int(dims[0]))
+    _check_volumes(views, expect, "view")
     keep = []
     if on_dev:
         ptrs = [ctypes.c_void_p(int(v.data_ptr())) for v in views]
@@ -433,6 +448,7 @@ class Deconvolver:
     def __init__(self, views, psfs, variant="efficient", eps=0.0, path="auto", stream=None, device=-1,
                  precision="precise", boundary="periodic"):
         self.shape = tuple(views[0].shape)
+        self.n_views = len(views)
         self.psf_shapes = [tuple(p.shape) for p in psfs]
         self.ctx = mvd_create(views, psfs, eps=eps, path=path, stream=stream, device=device, precision=precision,
                               boundary=boundary)
@@ -446,6 +462,8 @@ class Deconvolver:
         mvd_iterate(self.ctx, n_iter, schedule)
 
     def set_weights(self, weights, norm="sum1", value=0.0) -> float:
+        if weights is not None:
+            _check_volumes(weights, self.shape, "weight image", self.n_views)
         return mvd_set_weights(self.ctx, weights, norm, value)
 
     def set_regularization(self, lam):
@@ -458,9 +476,12 @@ class Deconvolver:
         mvd_iterate_combined(self.ctx, n_iter, root)
 
     def set_estimate(self, psi=None):
+        if psi is not None:
+            _check_volumes([psi], self.shape, "estimate")
         mvd_set_estimate(self.ctx, psi)
 
     def set_views(self, views):
+        _check_volumes(views, self.shape, "view", self.n_views)
         mvd_set_views(self.ctx, views)
 
     def result(self, out=None) -> np.ndarray:

@@ -117,3 +117,38 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.mvd_unrolled_backward(None, None, None, None) == mvd.MVD_ERR_ARG
     assert lib.mvd_set_views(None, None, 0) == mvd.MVD_ERR_ARG
     assert "NULL" in mvd.mvd_last_error()
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor: only what the binding's checks read."""
+
+    def __init__(self, shape, dtype="torch.float32", contiguous=True):
+        self.shape = shape
+        self.dtype = dtype
+        self.is_cuda = True
+        self._contiguous = contiguous
+
+    def data_ptr(self):
+        return 0
+
+    def is_contiguous(self):
+        return self._contiguous
+
+
+def test_volume_checks_of_the_binding():
+    """Pointers cross the C ABI without sizes: the binding refuses volumes of the wrong shape
+    or layout before the library reads X*Y*Z floats behind them."""
+    good = [np.ones((4, 5, 6), np.float32)] * 2
+    mvd._check_volumes(good, (4, 5, 6), "view", 2)
+    with pytest.raises(ValueError):
+        mvd._check_volumes(good, (4, 5, 7), "view")
+    with pytest.raises(ValueError):
+        mvd._check_volumes(good, (4, 5, 6), "view", 3)
+    with pytest.raises(ValueError):
+        mvd._check_volumes([good[0], np.ones((4, 5, 5), np.float32)], (4, 5, 6), "view")
+    mvd._check_volumes([_FakeDeviceTensor((4, 5, 6))], (4, 5, 6), "view")
+    for bad in (_FakeDeviceTensor((4, 5, 6), dtype="torch.float64"), _FakeDeviceTensor((4, 5, 6), contiguous=False)):
+        with pytest.raises(ValueError):
+            mvd._check_volumes([bad], (4, 5, 6), "view")
+    with pytest.raises(ValueError):  # mixed view shapes at create, before any device work
+        mvd.mvd_create([good[0], np.ones((4, 5, 5), np.float32)], [np.ones((3, 3, 3), np.float32)] * 2)
