@@ -15,7 +15,8 @@
  *
  * with P_v^comp the compound kernel of Eq. 222 (or of Eq. 230, Eq. 240, or
  * the plain mirrored PSF of Eq. 51). "*" is periodic (circular) convolution
- * on the volume grid, (f * k)(x) = sum_d k(d) f((x - d) mod dims).
+ * on the volume grid, (f * k)(x) = sum_d k(d) f((x - d) mod dims), unless the
+ * context has a zero or mirror boundary (mvd_boundary).
  *
  * Conventions shared by every entry point
  *   Layout   FP32 volumes, x fastest: voxel (x,y,z) at index x + X*(y + Y*z).
