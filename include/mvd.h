@@ -279,6 +279,19 @@ mvd_status mvd_get_compound_kernel(mvd_ctx* ctx, int v, float* out, size_t n_ele
 unsigned long long mvd_launch_count(void);
 
 /*
+ * The radix plan the FFT engine's shared-memory (Stockham) passes use for an
+ * axis of length L under `precision` (mvd_precision): the stage radices, in
+ * order, into radices[0..n-1]. Host only; needs no GPU.
+ * Returns n >= 1, 0 if L is not {2,3,5}-smooth (or L < 2), or -1 if
+ * max_stages < n or radices is NULL or precision is unknown. Powers of two
+ * take radix 8 stages with one 4 or 2 (4 4 when that avoids a 2); other
+ * lengths the cheapest product of radices 2, 3, 4, 5, 6, 8, 9 and 10 (no 10
+ * for MVD_PRECISE and MVD_MIXED, whose double-float passes would spill with
+ * it), largest radix first.
+ */
+int mvd_fft_plan(int L, int precision, int* radices, int max_stages);
+
+/*
  * Per-kernel timing for measurement. While enabled, every launch of the
  * update's kernels is bracketed by two CUDA events recorded on the launching
  * stream. mvd_profile_read synchronises on the recorded events and returns,

@@ -612,6 +612,16 @@ const char* mvd_last_error(void) { return t_err.c_str(); }
 
 unsigned long long mvd_launch_count(void) { return g_launches.load(); }
 
+int mvd_fft_plan(int L, int precision, int* radices, int max_stages) {
+    if (!radices || (precision != MVD_PRECISE && precision != MVD_FAST && precision != MVD_MIXED)) return -1;
+    if (L < 2) return 0;
+    mvd::FftPlan p{};
+    if (!mvd::make_radix_plan(L, &p, precision != MVD_FAST)) return 0;
+    if (p.nst > max_stages) return -1;
+    for (int s = 0; s < p.nst; ++s) radices[s] = p.radix[s];
+    return p.nst;
+}
+
 void mvd_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(mvd::g_prof_mu);
     mvd::g_prof.clear();

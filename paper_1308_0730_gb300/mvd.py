@@ -32,7 +32,7 @@ EXPORTS = ["mvd_default_options", "mvd_create", "mvd_precompute_kernels", "mvd_s
            "mvd_batch_run", "mvd_batch_wait", "mvd_batch_tasks", "mvd_batch_destroy", "mvd_unrolled_forward",
            "mvd_unrolled_backward", "mvd_gaussian_psf", "mvd_gaussian_psf_vjp", "mvd_autotune",
            "mvd_batch_create_mode", "mvd_batch_mode", "mvd_iterate_combined",
-           "mvd_set_weights", "mvd_get_weights", "mvd_set_regularization", "mvd_set_views"]
+           "mvd_set_weights", "mvd_get_weights", "mvd_set_regularization", "mvd_set_views", "mvd_fft_plan"]
 
 
 class MvdError(RuntimeError):
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mvd_set_weights.restype = ci
     lib.mvd_set_views.argtypes = [vp, ctypes.POINTER(vp), ci]
     lib.mvd_set_views.restype = ci
+    lib.mvd_fft_plan.argtypes = [ci, ci, ctypes.POINTER(ci), ci]
+    lib.mvd_fft_plan.restype = ci
     lib.mvd_get_weights.argtypes = [vp, ci, _FP, sz]
     lib.mvd_set_regularization.argtypes = [vp, ctypes.c_float]
     lib.mvd_set_regularization.restype = ci
@@ -256,6 +258,15 @@ def mvd_set_views(ctx, views):
     ptrs = (ctypes.c_void_p * len(keep))(*[ctypes.c_void_p(int(v.data_ptr()) if on_dev else v.ctypes.data)
                                             for v in keep])
     _check(lib.mvd_set_views(ctx, ptrs, 1 if on_dev else 0))
+
+
+def mvd_fft_plan(L: int, precision="precise") -> list:
+    """Stage radices of the Stockham passes for an axis of length L ([] if L is not {2,3,5}-smooth)."""
+    buf = (ctypes.c_int * 64)()
+    n = load().mvd_fft_plan(int(L), PRECISIONS[precision] if isinstance(precision, str) else int(precision), buf, 64)
+    if n < 0:
+        raise ValueError("mvd_fft_plan: bad precision")
+    return list(buf[:n])
 
 
 def mvd_iterate(ctx, n_iter: int, schedule=None):
