@@ -471,9 +471,13 @@ void mvdo_conv_zero(const double* in, const int dims[3], const double* k, const 
  * which divides the back-projection by the sensitivity s_v = 1 * P_v^comp
  * (the back-projection of a field of ones, 1 in the periodic case):
  *   psi <- max(psi (r * P_v^comp) / s_v, eps).
+ * With view weights w_v (NULL: none) and Tikhonov lambda the factor
+ * f = ((r * P_v^comp) / s_v) / (1 + lambda psi) enters as in
+ * mvdo_deconvolve_weighted: psi <- max(psi + w (psi f - psi), eps).
  * Otherwise as mvdo_deconvolve. Returns eps, or -1. */
 double mvdo_deconvolve_zero(int n_views, const double* const* views, const double* const* psfs, const int* pdims,
-                            const int dims[3], int variant, int n_iter, double eps, int init, double* psi) {
+                            const int dims[3], int variant, int n_iter, const double* const* weights, double lambda,
+                            double eps, int init, double* psi) {
     const long M = (long)dims[0] * dims[1] * dims[2];
     double psi0 = mvdo_mean_views(n_views, views, dims);
     if (eps <= 0.0) eps = 1e-4 * psi0;
@@ -511,8 +515,17 @@ double mvdo_deconvolve_zero(int n_views, const double* const* views, const doubl
 #pragma omp parallel for schedule(static)
             for (long i = 0; i < M; ++i) r[i] = views[v][i] / fmax(b[i], eps);
             mvdo_conv_zero(r, dims, comp[v], pd, c);
+            if (!weights && lambda == 0.0) {
 #pragma omp parallel for schedule(static)
-            for (long i = 0; i < M; ++i) psi[i] = fmax(psi[i] * c[i] / sens[v][i], eps);
+                for (long i = 0; i < M; ++i) psi[i] = fmax(psi[i] * c[i] / sens[v][i], eps);
+            } else {
+#pragma omp parallel for schedule(static)
+                for (long i = 0; i < M; ++i) {
+                    const double f = c[i] / sens[v][i] / (1.0 + lambda * psi[i]);
+                    const double w = weights ? weights[v][i] : 1.0;
+                    psi[i] = fmax(psi[i] + w * (psi[i] * f - psi[i]), eps);
+                }
+            }
         }
     }
     for (int v = 0; v < n_views; ++v) {
@@ -594,9 +607,11 @@ void mvdo_backproject_mirror(const double* r, const int dims[3], const double* k
  * back-projection of a field of ones; 1 wherever P_v^comp is symmetric under
  * the reflection of each face it reaches):
  *   psi <- max(psi c / s_v, eps),  c = backproject_mirror(r, P_v^comp).
+ * View weights and Tikhonov lambda enter as in mvdo_deconvolve_zero.
  * Otherwise as mvdo_deconvolve. Returns eps, or -1. */
 double mvdo_deconvolve_mirror(int n_views, const double* const* views, const double* const* psfs, const int* pdims,
-                              const int dims[3], int variant, int n_iter, double eps, int init, double* psi) {
+                              const int dims[3], int variant, int n_iter, const double* const* weights,
+                              double lambda, double eps, int init, double* psi) {
     const long M = (long)dims[0] * dims[1] * dims[2];
     double psi0 = mvdo_mean_views(n_views, views, dims);
     if (eps <= 0.0) eps = 1e-4 * psi0;
@@ -631,8 +646,17 @@ double mvdo_deconvolve_mirror(int n_views, const double* const* views, const dou
 #pragma omp parallel for schedule(static)
             for (long i = 0; i < M; ++i) r[i] = views[v][i] / fmax(b[i], eps);
             mvdo_backproject_mirror(r, dims, comp[v], pd, c);
+            if (!weights && lambda == 0.0) {
 #pragma omp parallel for schedule(static)
-            for (long i = 0; i < M; ++i) psi[i] = fmax(psi[i] * c[i] / sens[v][i], eps);
+                for (long i = 0; i < M; ++i) psi[i] = fmax(psi[i] * c[i] / sens[v][i], eps);
+            } else {
+#pragma omp parallel for schedule(static)
+                for (long i = 0; i < M; ++i) {
+                    const double f = c[i] / sens[v][i] / (1.0 + lambda * psi[i]);
+                    const double w = weights ? weights[v][i] : 1.0;
+                    psi[i] = fmax(psi[i] + w * (psi[i] * f - psi[i]), eps);
+                }
+            }
         }
     }
     for (int v = 0; v < n_views; ++v) {

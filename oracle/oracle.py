@@ -70,12 +70,14 @@ def _load():
             lib.mvdo_deconvolve_weighted.restype = ctypes.c_double
             lib.mvdo_conv_zero.argtypes = [_D, _I, _D, _I, _D]
             lib.mvdo_deconvolve_zero.argtypes = [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D), _I, _I,
-                                                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
+                                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_int, _D]
             lib.mvdo_deconvolve_zero.restype = ctypes.c_double
             lib.mvdo_conv_mirror.argtypes = [_D, _I, _D, _I, _D]
             lib.mvdo_backproject_mirror.argtypes = [_D, _I, _D, _I, _D]
             lib.mvdo_deconvolve_mirror.argtypes = [ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D), _I, _I,
-                                                   ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _D]
+                                                   ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.c_double,
+                                                   ctypes.c_double, ctypes.c_int, _D]
             lib.mvdo_deconvolve_mirror.restype = ctypes.c_double
             lib.mvdo_update_at.argtypes = [_D, _D, _D, _I, _D, _I, _I, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_long), ctypes.c_int, _D]
@@ -294,38 +296,39 @@ def deconvolve_weighted(views, psfs, n_iter, weights=None, variant="efficient", 
     return psi, used
 
 
-def deconvolve_zero(views, psfs, n_iter, variant="efficient", eps=0.0, psi_init=None):
-    """Sequential deconvolution whose image convolutions use a zero boundary. Returns ``(psi, eps)``."""
+def _deconvolve_bounded(fn, views, psfs, n_iter, variant, eps, psi_init, weights, lam):
     var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     vs = [_f64(v) for v in views]
     ps, parr, pd = _psf_arrays(psfs)
     varr = (_D * len(vs))(*[_dptr(v) for v in vs])
+    if weights is None:
+        ws, warr = [], None
+    else:
+        ws = [_f64(w) for w in weights]
+        warr = (_D * len(ws))(*[_dptr(w) for w in ws])
     if psi_init is None:
         psi, init = np.empty_like(vs[0]), 0
     else:
         psi, init = _f64(psi_init).copy(), 1
-    used = _load().mvdo_deconvolve_zero(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), float(eps),
-                                        init, _dptr(psi))
+    used = fn(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), warr, float(lam), float(eps), init,
+              _dptr(psi))
     if used < 0:
         raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
     return psi, used
 
 
-def deconvolve_mirror(views, psfs, n_iter, variant="efficient", eps=0.0, psi_init=None):
-    """Sequential deconvolution whose image convolutions use a mirror boundary. Returns ``(psi, eps)``."""
-    var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-    vs = [_f64(v) for v in views]
-    ps, parr, pd = _psf_arrays(psfs)
-    varr = (_D * len(vs))(*[_dptr(v) for v in vs])
-    if psi_init is None:
-        psi, init = np.empty_like(vs[0]), 0
-    else:
-        psi, init = _f64(psi_init).copy(), 1
-    used = _load().mvdo_deconvolve_mirror(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter), float(eps),
-                                          init, _dptr(psi))
-    if used < 0:
-        raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
-    return psi, used
+def deconvolve_zero(views, psfs, n_iter, variant="efficient", eps=0.0, psi_init=None, weights=None, lam=0.0):
+    """Sequential deconvolution whose image convolutions use a zero boundary, optionally with
+    view weights and Tikhonov ``lam`` (as in deconvolve_weighted). Returns ``(psi, eps)``."""
+    return _deconvolve_bounded(_load().mvdo_deconvolve_zero, views, psfs, n_iter, variant, eps, psi_init, weights,
+                               lam)
+
+
+def deconvolve_mirror(views, psfs, n_iter, variant="efficient", eps=0.0, psi_init=None, weights=None, lam=0.0):
+    """Sequential deconvolution whose image convolutions use a mirror boundary, optionally with
+    view weights and Tikhonov ``lam``. Returns ``(psi, eps)``."""
+    return _deconvolve_bounded(_load().mvdo_deconvolve_mirror, views, psfs, n_iter, variant, eps, psi_init, weights,
+                               lam)
 
 
 def unrolled_grad(views, psfs, n_iter, truth, variant="efficient"):

@@ -158,3 +158,65 @@ def test_the_three_boundaries_differ():
     c, _ = oracle.deconvolve(views, psfs, 2, "efficient")
     assert np.abs(a - b).max() > 1e-3 * np.abs(b).max()
     assert np.abs(a - c).max() > 1e-3 * np.abs(c).max()
+
+
+# ---------------------------------------------------------------------------
+# view weights and Tikhonov regularisation with the zero and mirror boundaries
+# ---------------------------------------------------------------------------
+
+BOUNDED = {"zero": (oracle.deconvolve_zero, oracle.conv_zero), "mirror": (oracle.deconvolve_mirror, oracle.conv_mirror)}
+
+
+def _weights(shape, n, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.uniform(0.2, 1.0, size=shape) for _ in range(n)]
+
+
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+def test_unit_weights_and_no_regularisation_reduce_to_the_plain_update(boundary):
+    deconv, blur = BOUNDED[boundary]
+    views, psfs, _ = _noise_free() if boundary == "zero" else _mirror_noise_free()
+    a, _ = deconv(views, psfs, 2, "efficient")
+    b, _ = deconv(views, psfs, 2, "efficient", weights=[np.ones_like(v) for v in views], lam=0.0)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+def test_a_zero_weight_view_drops_out(boundary):
+    """Plain kernels (P_v^comp = P_v^*, no dependence on the other views): weight 0 for view 1
+    equals running views 0 and 2 alone from the same start and floor."""
+    deconv, _ = BOUNDED[boundary]
+    views, psfs, truth = _noise_free() if boundary == "zero" else _mirror_noise_free()
+    start = np.full_like(truth, truth.mean())
+    w = [np.ones_like(v) for v in views]
+    w[1] = np.zeros_like(views[1])
+    a, _ = deconv(views, psfs, 2, "plain", eps=1e-9, psi_init=start, weights=w)
+    b, _ = deconv([views[0], views[2]], [psfs[0], psfs[2]], 2, "plain", eps=1e-9, psi_init=start)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+def test_weighted_noise_free_truth_is_a_fixed_point(boundary):
+    deconv, _ = BOUNDED[boundary]
+    views, psfs, truth = _noise_free() if boundary == "zero" else _mirror_noise_free()
+    psi, _ = deconv(views, psfs, 2, "efficient", psi_init=truth, weights=_weights(truth.shape, 3, 7))
+    assert np.abs(psi - truth).max() <= 1e-10 * truth.max()
+
+
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+def test_one_weighted_regularised_update_matches_the_periodic_one_away_from_the_faces(boundary):
+    """From a flat start the first update at voxels farther than twice the kernel reach from
+    every face sees no boundary: it equals the periodic weighted, regularised update there."""
+    deconv, _ = BOUNDED[boundary]
+    rng = np.random.default_rng(8)
+    shape = (20, 22, 24)
+    views = [rng.uniform(1.0, 3.0, size=shape)]
+    psfs = [_separable_symmetric((5, 3, 7))]
+    w = _weights(shape, 1, 9)
+    start = np.full(shape, 2.0)
+    a, _ = deconv(views, psfs, 1, "efficient", eps=1e-9, psi_init=start, weights=w, lam=0.05)
+    b, _ = oracle.deconvolve_weighted(views, psfs, 1, w, "efficient", eps=1e-9, psi_init=start, lam=0.05)
+    hz, hy, hx = 2 * 2, 2 * 1, 2 * 3  # twice the half-widths of the 5 x 3 x 7 ([z][y][x]) box
+    inner = (slice(hz, shape[0] - hz), slice(hy, shape[1] - hy), slice(hx, shape[2] - hx))
+    assert np.abs(a[inner] - b[inner]).max() <= 1e-12 * np.abs(b[inner]).max()
+    assert np.abs(a - b).max() > 1e-6  # the faces do differ
