@@ -673,6 +673,86 @@ double mvdo_deconvolve_mirror(int n_views, const double* const* views, const dou
     return bad ? -1.0 : eps;
 }
 
+/* The combined update (as mvdo_deconvolve_combined) with a zero (boundary 1)
+ * or mirror (boundary 2) boundary: every view's factor is its back-projected
+ * ratio divided by its sensitivity, c_v / s_v (the blur and back-projection of
+ * mvdo_deconvolve_zero or mvdo_deconvolve_mirror), and psi <- max(psi .
+ * prod_v (c_v / s_v)^e, eps) with e = 1 / |V| when root != 0, else 1.
+ * Returns eps, or -1 (also for an unknown boundary). */
+double mvdo_deconvolve_combined_bounded(int n_views, const double* const* views, const double* const* psfs,
+                                        const int* pdims, const int dims[3], int variant, int n_iter, int root,
+                                        int boundary, double eps, int init, double* psi) {
+    if (boundary != 1 && boundary != 2) return -1.0;
+    const long M = (long)dims[0] * dims[1] * dims[2];
+    double psi0 = mvdo_mean_views(n_views, views, dims);
+    if (eps <= 0.0) eps = 1e-4 * psi0;
+    if (!init)
+        for (long i = 0; i < M; ++i) psi[i] = psi0;
+    double** pn = (double**)malloc(sizeof(double*) * n_views);
+    double** comp = (double**)malloc(sizeof(double*) * n_views);
+    double** sens = (double**)malloc(sizeof(double*) * n_views);
+    int bad = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        double s = 0.0;
+        for (long i = 0; i < T; ++i) s += psfs[v][i];
+        pn[v] = (double*)malloc(sizeof(double) * T);
+        for (long i = 0; i < T; ++i) pn[v][i] = psfs[v][i] / s;
+    }
+    double* b = (double*)malloc(sizeof(double) * M);
+    double* r = (double*)malloc(sizeof(double) * M);
+    double* c = (double*)malloc(sizeof(double) * M);
+    double* prod = (double*)malloc(sizeof(double) * M);
+    for (long i = 0; i < M; ++i) r[i] = 1.0;
+    for (int v = 0; v < n_views; ++v) {
+        const long T = (long)pdims[3 * v] * pdims[3 * v + 1] * pdims[3 * v + 2];
+        comp[v] = (double*)malloc(sizeof(double) * T);
+        sens[v] = (double*)malloc(sizeof(double) * M);
+        if (mvdo_compound(n_views, (const double* const*)pn, pdims, v, variant, comp[v]) != 0) bad = 1;
+        if (bad) continue;
+        if (boundary == 1)
+            mvdo_conv_zero(r, dims, comp[v], pdims + 3 * v, sens[v]);
+        else
+            mvdo_backproject_mirror(r, dims, comp[v], pdims + 3 * v, sens[v]);
+    }
+    for (int it = 0; it < n_iter && !bad; ++it) {
+        for (long i = 0; i < M; ++i) prod[i] = 1.0;
+        for (int v = 0; v < n_views; ++v) {
+            const int* pd = pdims + 3 * v;
+            if (boundary == 1)
+                mvdo_conv_zero(psi, dims, pn[v], pd, b);
+            else
+                mvdo_conv_mirror(psi, dims, pn[v], pd, b);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) r[i] = views[v][i] / fmax(b[i], eps);
+            if (boundary == 1)
+                mvdo_conv_zero(r, dims, comp[v], pd, c);
+            else
+                mvdo_backproject_mirror(r, dims, comp[v], pd, c);
+#pragma omp parallel for schedule(static)
+            for (long i = 0; i < M; ++i) prod[i] *= c[i] / sens[v][i];
+        }
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < M; ++i) {
+            const double f = root ? pow(prod[i], 1.0 / n_views) : prod[i];
+            psi[i] = fmax(psi[i] * f, eps);
+        }
+    }
+    for (int v = 0; v < n_views; ++v) {
+        free(comp[v]);
+        free(pn[v]);
+        free(sens[v]);
+    }
+    free(comp);
+    free(pn);
+    free(sens);
+    free(b);
+    free(r);
+    free(c);
+    free(prod);
+    return bad ? -1.0 : eps;
+}
+
 /* One view update evaluated only at the listed voxels (flat indices):
  *   out[i] = max(psi(x_i) * c(x_i), eps), with c, r, b computed from the
  * definitions above on the neighbourhood each sample needs. */

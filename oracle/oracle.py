@@ -61,6 +61,11 @@ def _load():
                                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                      ctypes.c_int, _D]
             lib.mvdo_deconvolve_combined.restype = ctypes.c_double
+            lib.mvdo_deconvolve_combined_bounded.argtypes = [ctypes.c_int, ctypes.POINTER(_D),
+                                                             ctypes.POINTER(_D), _I, _I, ctypes.c_int,
+                                                             ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                             ctypes.c_double, ctypes.c_int, _D]
+            lib.mvdo_deconvolve_combined_bounded.restype = ctypes.c_double
             lib.mvdo_normalize_weights.argtypes = [ctypes.c_int, ctypes.POINTER(_D), _I, ctypes.c_int,
                                                    ctypes.c_double, ctypes.POINTER(_D)]
             lib.mvdo_normalize_weights.restype = ctypes.c_double
@@ -234,9 +239,12 @@ def deconvolve(views, psfs, n_iter, variant="efficient", schedule=None, eps=0.0,
     return psi, used
 
 
-def deconvolve_combined(views, psfs, n_iter, variant="efficient", root=True, eps=0.0, psi_init=None):
+def deconvolve_combined(views, psfs, n_iter, variant="efficient", root=True, eps=0.0, psi_init=None,
+                        boundary="periodic"):
     """Combined (simultaneous) update, Eq. 50 / Eq. 220: every view's factor from the same psi,
     their product (or with ``root`` its |V|-th root, the geometric mean) applied at once.
+    ``boundary``: "periodic", or "zero" / "mirror" (factors c_v / s_v, as in deconvolve_zero
+    and deconvolve_mirror).
 
     Returns ``(psi, eps_used)``; ``eps <= 0`` selects ``1e-4 * psi0``.
     """
@@ -248,8 +256,14 @@ def deconvolve_combined(views, psfs, n_iter, variant="efficient", root=True, eps
         psi, init = np.empty_like(vs[0]), 0
     else:
         psi, init = _f64(psi_init).copy(), 1
-    used = _load().mvdo_deconvolve_combined(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter),
-                                            1 if root else 0, float(eps), init, _dptr(psi))
+    if boundary == "periodic":
+        used = _load().mvdo_deconvolve_combined(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var, int(n_iter),
+                                                1 if root else 0, float(eps), init, _dptr(psi))
+    else:
+        used = _load().mvdo_deconvolve_combined_bounded(len(vs), varr, parr, pd, _dims_xyz(vs[0]), var,
+                                                        int(n_iter), 1 if root else 0,
+                                                        {"zero": 1, "mirror": 2}[boundary], float(eps), init,
+                                                        _dptr(psi))
     if used < 0:
         raise ValueError("oracle deconvolution failed (compound kernel sums to zero)")
     return psi, used

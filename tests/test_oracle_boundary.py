@@ -220,3 +220,51 @@ def test_one_weighted_regularised_update_matches_the_periodic_one_away_from_the_
     inner = (slice(hz, shape[0] - hz), slice(hy, shape[1] - hy), slice(hx, shape[2] - hx))
     assert np.abs(a[inner] - b[inner]).max() <= 1e-12 * np.abs(b[inner]).max()
     assert np.abs(a - b).max() > 1e-6  # the faces do differ
+
+
+# ---------------------------------------------------------------------------
+# the combined (simultaneous) update with the zero and mirror boundaries
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+@pytest.mark.parametrize("root", [True, False])
+def test_combined_with_one_view_is_the_sequential_update(boundary, root):
+    deconv, _ = BOUNDED[boundary]
+    views, psfs, _ = _noise_free() if boundary == "zero" else _mirror_noise_free()
+    a, _ = oracle.deconvolve_combined(views[:1], psfs[:1], 3, "efficient", root=root, boundary=boundary)
+    b, _ = deconv(views[:1], psfs[:1], 3, "efficient")
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+def test_combined_noise_free_truth_is_a_fixed_point(boundary):
+    views, psfs, truth = _noise_free() if boundary == "zero" else _mirror_noise_free()
+    for root in (True, False):
+        psi, _ = oracle.deconvolve_combined(views, psfs, 2, "efficient", root=root, psi_init=truth,
+                                            boundary=boundary)
+        assert np.abs(psi - truth).max() <= 1e-10 * truth.max()
+
+
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+def test_combined_root_of_identical_views_is_one_view(boundary):
+    """Plain kernels: N copies of one view give N identical factors, whose geometric mean is
+    the single view's factor."""
+    views, psfs, _ = _noise_free() if boundary == "zero" else _mirror_noise_free()
+    a, _ = oracle.deconvolve_combined([views[0]] * 3, [psfs[0]] * 3, 2, "plain", root=True, boundary=boundary)
+    b, _ = oracle.deconvolve_combined(views[:1], psfs[:1], 2, "plain", root=True, boundary=boundary)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("boundary", ["zero", "mirror"])
+def test_one_combined_update_matches_the_periodic_one_away_from_the_faces(boundary):
+    rng = np.random.default_rng(10)
+    shape = (20, 22, 24)
+    views = [rng.uniform(1.0, 3.0, size=shape) for _ in range(2)]
+    psfs = [_separable_symmetric((5, 3, 7)), _separable_symmetric((3, 5, 5))]
+    start = np.full(shape, 2.0)
+    a, _ = oracle.deconvolve_combined(views, psfs, 1, "efficient", eps=1e-9, psi_init=start, boundary=boundary)
+    b, _ = oracle.deconvolve_combined(views, psfs, 1, "efficient", eps=1e-9, psi_init=start)
+    # compound kernels live on each PSF's box: reach (2, 2, 3) in (z, y, x); twice that
+    inner = (slice(4, shape[0] - 4), slice(4, shape[1] - 4), slice(6, shape[2] - 6))
+    assert np.abs(a[inner] - b[inner]).max() <= 1e-12 * np.abs(b[inner]).max()
+    assert np.abs(a - b).max() > 1e-6
