@@ -820,6 +820,24 @@ def run_weighted(args):
                           "weight_target": T})
 
 
+def run_regularized(args):
+    """Tikhonov regularisation (Green's one-step-late form, lambda = 0.006, inside the paper's
+    0.0006-0.06) on the 256x256x128 four-view workload, 20 sequential iterations,
+    device-resident, precise mode."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1308_0730_gb300 import mvd
+
+    w = _workload(0)
+    stream, dviews = _resident_views(w)
+    with mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft") as d:
+        d.set_regularization(0.006)
+        ms, launches, clocks = _time_steps(args, d, stream, lambda: d.iterate(w.n_iter))
+    return _variant_line(args, w, ms, launches, clocks,
+                         {"update": "sequential with Tikhonov regularisation (one-step-late)", "lambda": 0.006})
+
+
 def run_boundary(args):
     """The 256x256x128 four-view workload with a zero or mirror boundary: the engines run on
     the grid padded by the PSF half-widths h = (20, 7, 20) (zero: by h, 288 x 270 x 150;
@@ -851,6 +869,8 @@ def main():
                     help="time the sequential update with partial-overlap view weights instead")
     ap.add_argument("--combined", action="store_true",
                     help="time the combined (simultaneous) update with the geometric mean instead")
+    ap.add_argument("--regularized", action="store_true",
+                    help="time the sequential update with Tikhonov regularisation (lambda 0.006) instead")
     ap.add_argument("--boundary", choices=["periodic", "zero", "mirror"], default="periodic",
                     help="zero / mirror: time the sequential update with that boundary (padded grid) instead")
     ap.add_argument("--grad", action="store_true",
@@ -872,6 +892,8 @@ def main():
         return run_combined(args)
     if args.weighted:
         return run_weighted(args)
+    if args.regularized:
+        return run_regularized(args)
     if args.boundary != "periodic":
         return run_boundary(args)
     return run_gpu(args)
