@@ -454,7 +454,13 @@ def mvd_gaussian_psf_vjp(sigma_xy: float, sigma_ax: float, box_xyz, grad_psf, an
 
 
 class Deconvolver:
-    """Owns one context: ``with Deconvolver(views, psfs) as d: d.iterate(10); psi = d.result()``."""
+    """Owns one context: ``with Deconvolver(views, psfs) as d: d.iterate(10); psi = d.result()``.
+
+    ``variant``: "plain", "efficient", "opt1", "opt2" (mvd_variant). ``path``: "auto", "direct",
+    "fft". ``precision``: "precise", "mixed", "fast" (mvd_precision). ``boundary``: "periodic",
+    "zero", "mirror" (mvd_boundary). Volumes are ``[Z][Y][X]`` float32 (numpy, or contiguous
+    CUDA tensors); the setters check their shapes against the context's.
+    """
 
     def __init__(self, views, psfs, variant="efficient", eps=0.0, path="auto", stream=None, device=-1,
                  precision="precise", boundary="periodic"):
