@@ -419,7 +419,9 @@ mvd_status mvd_gaussian_psf_vjp(double sigma_xy, double sigma_ax, double angle_d
  * acquisition loops that allocate at start-up only. It runs one view update
  * with the direct engine and allocates nothing:
  *   psi = max(psi . ((phi / max(psi * psf, eps)) * comp), eps)
- * All pointers are device pointers the caller owns: psi (X*Y*Z floats,
+ * All pointers are device pointers the caller owns, on the current device
+ * (host, pinned or another device's memory returns MVD_ERR_ARG, checked with
+ * cudaPointerGetAttributes): psi (X*Y*Z floats,
  * updated in place), phi (X*Y*Z floats), psf and comp (Kx*Ky*Kz floats each,
  * PSF layout; used as given, so pass a normalised PSF and its compound
  * kernel, e.g. from mvd_get_compound_kernel). dims = {X,Y,Z}, kdims =

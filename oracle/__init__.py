@@ -21,6 +21,9 @@ from .oracle import (  # noqa: F401
     update,
     update_at,
     deconvolve,
+    deconvolve_fft,
+    conv_fft,
+    grid_spectrum,
     deconvolve_combined,
     deconvolve_zero,
     deconvolve_mirror,

@@ -79,6 +79,29 @@ extern "C" mvd_status mvd_update_direct_noalloc(float* psi, const float* phi, co
                        kdims[1], kdims[2]);
         return MVD_ERR_UNSUPPORTED;
     }
+    // every buffer must be device (or managed) memory of the current device:
+    // the scratch below is this device's, and the kernels read X*Y*Z and
+    // Kx*Ky*Kz floats behind the pointers
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return mvd::cuda_status(e, "mvd_update_direct_noalloc: current device");
+    const void* bufs[4] = {psi, phi, psf, comp};
+    const char* names[4] = {"psi", "phi", "psf", "comp"};
+    for (int i = 0; i < 4; ++i) {
+        cudaPointerAttributes at{};
+        e = cudaPointerGetAttributes(&at, bufs[i]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            mvd::set_error("mvd_update_direct_noalloc: %s is not a CUDA pointer", names[i]);
+            return MVD_ERR_ARG;
+        }
+        const bool ok = (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+        if (!ok) {
+            mvd::set_error("mvd_update_direct_noalloc: %s is not device memory of the current device %d", names[i],
+                           dev);
+            return MVD_ERR_ARG;
+        }
+    }
     float* r = nullptr;
     MVD_TRY(ratio_scratch(&r));
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -358,14 +358,27 @@ def mvd_update_direct_noalloc(psi, phi, psf, comp, eps: float, stream=None):
     """One view update without any device allocation (see include/mvd.h).
 
     ``psi`` (updated in place), ``phi``, ``psf`` and ``comp`` are contiguous
-    float32 CUDA tensors; ``psi``/``phi`` shaped ``[Z][Y][X]``, ``psf``/``comp``
-    shaped ``[Kz][Ky][Kx]``.
+    float32 CUDA tensors on one device; ``psi``/``phi`` shaped ``[Z][Y][X]``,
+    ``psf``/``comp`` shaped ``[Kz][Ky][Kx]``. Anything else raises ValueError
+    before the library sees a pointer (it reads X*Y*Z and Kx*Ky*Kz floats behind
+    them). The call runs with psi's device current.
     """
+    for name, t in (("psi", psi), ("phi", phi), ("psf", psf), ("comp", comp)):
+        if not _is_device(t) or str(t.dtype) != "torch.float32" or not t.is_contiguous() or t.dim() != 3:
+            raise ValueError(f"{name} must be a contiguous 3D float32 CUDA tensor")
+    if len({t.device for t in (psi, phi, psf, comp)}) != 1:
+        raise ValueError("psi, phi, psf and comp must live on one device")
+    _check_volumes([phi], psi.shape, "view")
+    _check_volumes([comp], psf.shape, "kernel")
     dims = (ctypes.c_int * 3)(int(psi.shape[2]), int(psi.shape[1]), int(psi.shape[0]))
     kd = (ctypes.c_int * 3)(int(psf.shape[2]), int(psf.shape[1]), int(psf.shape[0]))
     st = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     ptr = lambda t: ctypes.c_void_p(int(t.data_ptr()))  # noqa: E731
-    _check(load().mvd_update_direct_noalloc(ptr(psi), ptr(phi), ptr(psf), ptr(comp), dims, kd, float(eps), st))
+    import torch
+
+    with torch.cuda.device(psi.device):  # the C entry point works on the current device
+            _check(load().mvd_update_direct_noalloc(ptr(psi), ptr(phi), ptr(psf), ptr(comp), dims, kd, float(eps),
+                                                st))
 
 
 BATCH_MODES = {"auto": 0, "persistent": 1, "branches": 2}

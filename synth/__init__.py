@@ -18,3 +18,4 @@ from .workloads import (  # noqa: F401
     config5_crop,
     small_case,
 )
+from .device import DeviceWorkload, config3_device  # noqa: F401

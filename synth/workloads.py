@@ -192,6 +192,17 @@ def _ellipsoid_counts(args):
     return out
 
 
+def ellipsoid_params(rng, dims, n, radii_range, intensity_range):
+    """Random centres (x, y, z), per-axis radii, intensities and orientations of n ellipsoids,
+    drawn in this order from ``rng``."""
+    X, Y, Z = dims
+    centres = rng.uniform(0, 1, size=(n, 3)) * np.array([X, Y, Z])
+    radii = rng.uniform(*radii_range, size=(n, 3))
+    inten = rng.uniform(*intensity_range, size=n)
+    rots = [_random_rotation(rng) for _ in range(n)]
+    return centres, radii, inten, rots
+
+
 def ellipsoids_truth(rng, dims, n, radii_range, intensity_range, workers: int = 1) -> np.ndarray:
     """Solid ellipsoids (random radii, orientation, intensity), additive, periodic.
 
@@ -205,10 +216,7 @@ def ellipsoids_truth(rng, dims, n, radii_range, intensity_range, workers: int = 
     h = int(math.ceil(radii_range[1])) + 1
     nb = 2 * h + 1
     vol = np.zeros((Z, Y, X))
-    centres = rng.uniform(0, 1, size=(n, 3)) * np.array([X, Y, Z])
-    radii = rng.uniform(*radii_range, size=(n, 3))
-    inten = rng.uniform(*intensity_range, size=n)
-    rots = [_random_rotation(rng) for _ in range(n)]
+    centres, radii, inten, rots = ellipsoid_params(rng, dims, n, radii_range, intensity_range)
     base = np.arange(nb) - h
     ci_all = np.floor(centres).astype(int)
     frac_all = centres - ci_all  # centre offset within its voxel
@@ -403,28 +411,43 @@ def config4_layout(seed: int = 1004, n_volumes: int = 48):
     return out
 
 
-def config4(seed: int = 1004, n_volumes: int = 48, only=None):
+def _batch_volume(args):
+    seed, b, dims, n_views, peak = args
+    rng = np.random.default_rng([seed, b])
+    X, Y, Z = dims
+    # object density as in the 256x256x128 case (3000 per 8.4e6 voxels)
+    n_obj = max(8, int(round(3000 * X * Y * Z / (256 * 256 * 128))))
+    truth = ellipsoids_truth(rng, dims, n_obj, (3.0, 6.0), (0.5, 1.0))
+    psfs, angles = _spim_psfs(n_views, 1.2, 4.0, (15, 15, 41))
+    truth = _scale_to_peak(truth, psfs, peak)
+    views = _observe(rng, truth, psfs)
+    return _finish(f"batch{b:02d}-{X}x{Y}x{Z}-{n_views}views", dims, truth, psfs,
+                   views, 15, angles=angles, peak=peak)
+
+
+def config4(seed: int = 1004, n_volumes: int = 48, only=None, workers: int = 1):
     """48 independent volumes: log-uniform sizes, 2-6 views, peak 50-300 photons.
 
     ``only``: indices of the volumes to generate (default all); volume b's
     objects and noise use ``default_rng([seed, b])`` so any subset is
-    reproducible on its own.
+    reproducible on its own. ``workers > 1`` generates the volumes in a
+    spawned process pool (the calling program's main module must be
+    import-safe); the result is identical.
     """
-    out = []
-    for b, (dims, n_views, peak) in enumerate(config4_layout(seed, n_volumes)):
-        if only is not None and b not in only:
-            continue
-        rng = np.random.default_rng([seed, b])
-        X, Y, Z = dims
-        # object density as in the 256x256x128 case (3000 per 8.4e6 voxels)
-        n_obj = max(8, int(round(3000 * X * Y * Z / (256 * 256 * 128))))
-        truth = ellipsoids_truth(rng, dims, n_obj, (3.0, 6.0), (0.5, 1.0))
-        psfs, angles = _spim_psfs(n_views, 1.2, 4.0, (15, 15, 41))
-        truth = _scale_to_peak(truth, psfs, peak)
-        views = _observe(rng, truth, psfs)
-        out.append(_finish(f"batch{b:02d}-{X}x{Y}x{Z}-{n_views}views", dims, truth, psfs,
-                           views, 15, angles=angles, peak=peak))
-    return out
+    jobs = [(seed, b, dims, n_views, peak) for b, (dims, n_views, peak) in enumerate(config4_layout(seed, n_volumes))
+            if only is None or b in only]
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+
+        # largest volumes first, so the pool's tail is short
+        order = sorted(range(len(jobs)), key=lambda i: -int(np.prod(jobs[i][2])))
+        with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
+            done = pool.map(_batch_volume, [jobs[i] for i in order], chunksize=1)
+        out = [None] * len(jobs)
+        for i, w in zip(order, done):
+            out[i] = w
+        return out
+    return [_batch_volume(j) for j in jobs]
 
 
 SIGMA_TRUE = (1.2, 4.0)

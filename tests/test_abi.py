@@ -152,3 +152,58 @@ def test_volume_checks_of_the_binding():
             mvd._check_volumes([bad], (4, 5, 6), "view")
     with pytest.raises(ValueError):  # mixed view shapes at create, before any device work
         mvd.mvd_create([good[0], np.ones((4, 5, 5), np.float32)], [np.ones((3, 3, 3), np.float32)] * 2)
+
+
+@pytest.mark.parametrize("case,status", [
+    ("null_psi", mvd.MVD_ERR_ARG),
+    ("null_dims", mvd.MVD_ERR_ARG),
+    ("eps_zero", mvd.MVD_ERR_ARG),
+    ("eps_negative", mvd.MVD_ERR_ARG),
+    ("eps_nan", mvd.MVD_ERR_ARG),
+    ("even_box", mvd.MVD_ERR_SHAPE),
+    ("box_larger_than_volume", mvd.MVD_ERR_SHAPE),
+    ("zero_dim", mvd.MVD_ERR_SHAPE),
+    ("beyond_scratch", mvd.MVD_ERR_SHAPE),
+    ("box_beyond_shared_memory", mvd.MVD_ERR_UNSUPPORTED),
+])
+def test_noalloc_rejects_invalid_arguments(lib, case, status):
+    """Host-side checks of the allocation-free update, made before any device call: the
+    pointers below are never dereferenced."""
+    fake = ctypes.c_void_p(4096)
+    ptrs = {"psi": fake, "phi": fake, "psf": fake, "comp": fake}
+    dims, kd, eps = [32, 32, 32], [3, 5, 7], 1e-3
+    dims_p = True
+    if case == "null_psi":
+        ptrs["psi"] = None
+    elif case == "null_dims":
+        dims_p = False
+    elif case == "eps_zero":
+        eps = 0.0
+    elif case == "eps_negative":
+        eps = -1.0
+    elif case == "eps_nan":
+        eps = float("nan")
+    elif case == "even_box":
+        kd = [3, 4, 5]
+    elif case == "box_larger_than_volume":
+        kd = [33, 3, 3]
+    elif case == "zero_dim":
+        dims = [32, 0, 32]
+    elif case == "beyond_scratch":
+        dims = [256, 128, 128]
+    elif case == "box_beyond_shared_memory":
+        dims, kd = [128, 128, 128], [101, 101, 101]
+    d = (ctypes.c_int * 3)(*dims) if dims_p else None
+    k = (ctypes.c_int * 3)(*kd)
+    rc = lib.mvd_update_direct_noalloc(ptrs["psi"], ptrs["phi"], ptrs["psf"], ptrs["comp"], d, k, eps, None)
+    assert rc == status, (case, rc, mvd.mvd_last_error())
+
+
+def test_noalloc_binding_checks_its_tensors():
+    """The binding refuses what would make the kernels read or write outside the caller's
+    buffers, before it passes any pointer."""
+    torch = pytest.importorskip("torch")
+    a = torch.ones((8, 8, 8))
+    k = torch.ones((3, 3, 3))
+    with pytest.raises(ValueError):
+        mvd.mvd_update_direct_noalloc(a, a, k, k, 1e-3)  # host tensors

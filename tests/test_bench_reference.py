@@ -20,7 +20,7 @@ def test_reference_arm_prints_the_contract_line():
                 "scaling", "dtype", "data", "config"):
         assert key in d, key
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
-    assert d["config"]["workload"].startswith("ellipsoids-256x256x128")
+    assert d["config"]["workload"].startswith("ellipsoids-1024x1024x512")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e = d["e2e"]

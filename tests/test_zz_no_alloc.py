@@ -1,19 +1,22 @@
-"""The allocation-free view update (mvd_update_direct_noalloc) against the
-regular context path.
+"""The allocation-free view update (mvd_update_direct_noalloc) against the FP64
+oracle and the regular context path.
 
 Some callers cannot call cudaMalloc (their device memory belongs to a caching
 allocator, or they must not allocate once frames are streaming), so the
 library offers one view update that allocates nothing and keeps its ratio
 scratch in a file-scope device array. This test drives that entry point
 through the C ABI, twice in a row on the same estimate (the second call reuses
-the scratch the first one left behind), and checks each result against the
-update the regular entry points (create / precompute / iterate, direct
-engine) compute from the same start. The file name makes pytest collect it
-last, so a run that stops at the first failure has run every other test.
+the scratch the first one left behind). Each result is checked against the
+oracle's update (`oracle.update`, FP64) from the same start and against the
+update the regular entry points (create / precompute / iterate, direct engine)
+compute; the free device memory is the same before and after the second call.
+The file name makes pytest collect it last, so a run that stops at the first
+failure has run every other test.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from tests._util import PARITY_TOL, err_report, rel_err
 
@@ -53,12 +56,25 @@ def test_noalloc_update_matches_regular_path_twice(env):
     comps = [torch.from_numpy(c).to(dev) for c in comps]
     phis = [torch.from_numpy(v).to(dev) for v in w.views]
     psi = torch.full(w.truth.shape, psi0, dtype=torch.float32, device=dev)
+    pn = [p.astype(np.float64) / p.astype(np.float64).sum() for p in w.psfs]
     torch.cuda.synchronize()
-    for v, ref in zip(order, refs):
+    # the oracle's chain starts from its own flat estimate and floor
+    psi0_o = oracle.mean_views(w.views)
+    eps_o = 1e-4 * psi0_o
+    assert abs(psi0_o - psi0) <= 1e-6 * psi0_o
+    prev = np.full(w.truth.shape, psi0_o)
+    for i, (v, ref) in enumerate(zip(order, refs)):
+        free0, _ = torch.cuda.mem_get_info()
         mvd.mvd_update_direct_noalloc(psi, phis[v], psfs[v], comps[v], eps)
         torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        if i > 0:  # the first call on a device may look up the scratch address once
+            assert free1 == free0, f"free device memory changed by {free0 - free1} bytes"
         got = psi.cpu().numpy()
-        assert rel_err(got, ref) < PARITY_TOL, f"view {v}: {err_report(got, ref)}"
+        want = oracle.update(prev, w.views[v], pn[v], oracle.compound(pn, v, "efficient"), eps_o)
+        assert rel_err(got, want) < PARITY_TOL, f"view {v} vs oracle: {err_report(got, want)}"
+        assert rel_err(got, ref) < PARITY_TOL, f"view {v} vs context path: {err_report(got, ref)}"
+        prev = want
 
 
 def test_noalloc_rejects_volumes_beyond_its_scratch(env):
