@@ -1,21 +1,31 @@
 """Throughput benchmark: voxel-view updates per second of the efficient
 Bayesian multi-view update on GB300, through the library's C ABI.
 
-Default workload: 256x256x128 volume, 4 views at 0/90/180/270 deg about y,
-15x15x41 PSFs (sigma 1.2/4), 3000 ellipsoids, Poisson noise at peak 100
-photons, 20 sequential (OSEM-order) iterations of the efficient method.
+Headline workload: the 1024x1024x512 seven-view specimen (150k ellipsoids,
+PSFs sigma 1.5/5 with box 19x19x51 rotated by k*51.43 deg about y, peak 200
+photons plus a background of 5, Poisson noise), 10 sequential (OSEM-order)
+iterations of the efficient method in precise (double-float) mode. Its inputs
+are generated on the device (synth.config3_device); the views are 15 GiB.
 
 One step = one deconvolution of that volume: psi reset to the flat estimate,
-then 20 iterations x 4 view updates (views and kernel spectra resident in
-HBM; the PSFs of a time series are fixed, so kernels are precomputed once).
-value = voxels * views * iterations / step time, in Gvoxel-view/s.
-e2e = the same metric through the public API from pinned host buffers, for
-a time series with fixed PSFs: load the views (H2D) into the context,
-iterate, copy the result back (D2H); e2e.cold_value also builds and tears
-down the context (create + precompute + destroy) in every step.
+then 10 iterations x 7 view updates (views and kernel spectra resident in
+HBM). value = voxels * views * iterations / step time, in Gvoxel-view/s.
+e2e = the same metric through the public API from pinned host buffers, for a
+time series with fixed PSFs: every step loads the seven views (H2D) into the
+context (mvd_set_views), iterates and copies the result back (D2H).
+
+The same JSON line also carries
+  "mid":      the 256x256x128 four-view workload (20 iterations), with the
+              all-FP32 and mixed-precision pipelines beside it;
+  "batched":  48 volumes of uneven size and view count (15 iterations each):
+              one graph launch over all volumes, one persistent kernel, and the
+              48 volumes one after another ("plain"); ratio = plain / batched;
+  "roofline", "kernels": per-kernel CUDA-event times of one step and the
+              dominant kernel against the measured HBM peak;
+  "cpu_baseline": the FP64 oracle on the host cores on a bounded sample.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun each rank deconvolves its own independent volume (another
+Under torchrun each rank deconvolves its own independent specimen (another
 time point of the same acquisition): weak scaling, no collective on the data
 path; barrier + max over ranks around the timed region.
 """
@@ -38,9 +48,15 @@ if ROOT not in sys.path:
 METRIC = "Gvoxel-view updates/s"
 UNIT = "Gvoxel-view/s"
 L2_BYTES = 129 * 2 ** 20
+SPECIMEN_DIMS = (1024, 1024, 512)
+SPECIMEN_OBJECTS = 150_000
+# bounded CPU sample of the specimen (oracle timing): its recipe on a block whose
+# axes hold every rotated PSF box (up to 53 x 19 x 53)
+CPU_BLOCK = (128, 64, 64)
 
-# algorithmic bytes per voxel for each update kernel: every input and output
-# array it must touch, once (half spectrum = 8 * (X/2+1) * Y * Z bytes)
+
+# algorithmic bytes per launch of each update kernel: every input and output
+# array it must touch, once (FP32 half spectrum = 8 * (X/2+1) * Y * Z bytes)
 def _kernel_bytes(X, Y, Z, precise=True):
     M = X * Y * Z
     spec = 8 * (X // 2 + 1) * Y * Z  # FP32 half spectrum; double-float is 2 * spec
@@ -51,6 +67,7 @@ def _kernel_bytes(X, Y, Z, precise=True):
             "dd_z_mul": 6 * spec,                   # read S2 and a double-float kernel spectrum, write S2
             "dd_x_ratio": 4 * spec + 4 * M,         # read S2 and phi, write S2
             "x_update": 2 * spec + 8 * M,           # read S2, read and write psi
+            "dd_x_update_forward": 4 * spec + 8 * M,  # read S2 and psi, write psi and S2
         }
     return {
         "x_forward": 4 * M + spec,          # read psi, write S
@@ -60,36 +77,6 @@ def _kernel_bytes(X, Y, Z, precise=True):
         "x_update": spec + 8 * M,           # read S and psi, write psi
         "direct_ratio": 12 * M,             # read psi and phi, write r
         "direct_update": 12 * M,            # read r and psi, write psi
-    }
-
-
-# FP32-ALU work model of the double-float kernels (ALU-bound): one op = one FP32
-# add, multiply or FMA instruction. A double-float add costs 8 ops (TwoSum and two
-# adds), a double-float multiply 7 (product, three FMAs, FastTwoSum), a complex
-# double-float multiply 38 (two fused dot products of 19); a complex FFT of
-# length N is counted as the radix-2 algorithm's 3 N log2 N real adds and
-# 2 N log2 N real multiplies, i.e. 38 N log2 N ops in double-float and 5 N log2 N
-# in FP32.
-DD_FFT_OPS = 38.0
-FP32_FFT_OPS = 5.0
-DD_CMUL_OPS = 38.0
-FP32_CMUL_OPS = 6.0
-
-
-def _kernel_alu_ops(X, Y, Z):
-    import math
-
-    Xh = X // 2 + 1
-    dd = lambda n: DD_FFT_OPS * n * math.log2(n)  # noqa: E731
-    f32 = lambda n: FP32_FFT_OPS * n * math.log2(n)  # noqa: E731
-    return {
-        "dd_x_forward": (Y * Z / 2) * dd(X),                  # two real rows per complex line
-        "dd_y": Xh * Z * dd(Y),
-        "dd_z_mul": Xh * Y * (2 * dd(Z) + DD_CMUL_OPS * Z),  # forward, times the spectrum, inverse
-        "dd_x_ratio": (Y * Z / 2) * (dd(X) + f32(X)),         # inverse in double-float, r - 1 forward in FP32
-        "y": Xh * Z * f32(Y),
-        "z_mul": Xh * Y * (2 * f32(Z) + FP32_CMUL_OPS * Z),
-        "x_update": (Y * Z / 2) * f32(X),
     }
 
 
@@ -162,19 +149,41 @@ def _peaks():
     if os.path.exists(p):
         with open(p) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
     return 6800.0, "fallback"
 
 
 def _workload_seed(rank: int) -> int:
-    """Each rank deconvolves its own independent volume (weak scaling, no data-path collective)."""
-    return 1002 + 1000 * rank
+    """Each rank deconvolves its own independent specimen (weak scaling, no data-path collective)."""
+    return 1003 + 1000 * rank
+
+
+WORKLOADS = {
+    "specimen": SPECIMEN_DIMS,
+    "specimen-half": (512, 512, 256),   # the specimen's recipe at 1/8 of the voxels (profiler captures)
+    "specimen-quarter": (256, 256, 128),
+    # thin grids with one of the specimen's transform lengths (profiler captures of one pass)
+    "specimen-x1024": (1024, 64, 64),
+    "specimen-y1024": (64, 1024, 64),
+    "specimen-z512": (64, 64, 512),
+}
+
+
+def _specimen(rank: int, device: int, name: str = "specimen"):
+    """The specimen (or its recipe on a smaller grid), generated on the device."""
+    import synth
+
+    dims = WORKLOADS[name]
+    n_obj = max(1, round(SPECIMEN_OBJECTS * dims[0] * dims[1] * dims[2] / (SPECIMEN_DIMS[0] * SPECIMEN_DIMS[1]
+                                                                              * SPECIMEN_DIMS[2])))
+    return synth.config3_device(seed=_workload_seed(rank), dims=dims, n_objects=n_obj, device=f"cuda:{device}")
 
 
 def _workload(rank: int):
+    """The 256x256x128 four-view workload (20 iterations) of the variant benchmarks."""
     import synth
 
-    return synth.config2(seed=_workload_seed(rank))
+    return synth.config2(seed=1002 + 1000 * rank)
 
 
 def _max_over_ranks(x: float, dist, device) -> float:
@@ -193,45 +202,263 @@ def _job_value(world: int, units_per_rank: float, seconds: float) -> float:
     return world * units_per_rank / seconds / 1e9
 
 
-def _cpu_baseline(w, eps, steps=1):
-    """FP64 oracle on the host cores: one view update of the workload per step."""
-    import oracle
+# ---------------------------------------------------------------------------
+# FP64 oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
 
-    psfs64 = [p.astype(np.float64) / p.astype(np.float64).sum() for p in w.psfs]
-    K = oracle.compound(psfs64, 0, "efficient")
-    psi = np.full(w.truth.shape, float(np.mean([v.mean(dtype=np.float64) for v in w.views])))
-    phi = w.views[0].astype(np.float64)
-    times = []
-    for _ in range(steps):
+class OracleSample:
+    """The specimen's recipe (objects, seven rotated PSFs, photon level, background) on the
+    block CPU_BLOCK, with the oracle's compound kernels computed once (untimed). One step is
+    one iteration: the seven view updates of `oracle.update` (FP64 direct sums) in order.
+    The oracle's cost per voxel-view depends on the PSF boxes only, which the block keeps."""
+
+    def __init__(self):
+        import oracle
+        import synth
+
+        dims = CPU_BLOCK
+        n_obj = max(1, round(SPECIMEN_OBJECTS * dims[0] * dims[1] * dims[2] / (SPECIMEN_DIMS[0] * SPECIMEN_DIMS[1]
+                                                                                  * SPECIMEN_DIMS[2])))
+        self.w = synth.config3(dims=dims, n_objects=n_obj)
+        self.pn = [p.astype(np.float64) / p.astype(np.float64).sum() for p in self.w.psfs]
+        self.K = [oracle.compound(self.pn, v, "efficient") for v in range(len(self.pn))]
+        self.phi = [v.astype(np.float64) for v in self.w.views]
+        psi0 = oracle.mean_views(self.w.views)
+        self.eps = 1e-4 * psi0
+        self.psi = np.full(self.w.truth.shape, psi0)
+        self.units = self.w.voxels * len(self.pn)
+        self.cores = oracle.num_threads()
+
+    def step(self) -> float:
+        import oracle
+
         t0 = time.perf_counter()
-        oracle.update(psi, phi, psfs64[0], K, eps)
-        times.append(time.perf_counter() - t0)
-    return times, oracle.num_threads()
+        for v in range(len(self.pn)):
+            self.psi = oracle.update(self.psi, self.phi[v], self.pn[v], self.K[v], self.eps)
+        return time.perf_counter() - t0
+
+    def describe(self, steps: int, seconds: float) -> str:
+        X, Y, Z = CPU_BLOCK
+        return (f"{steps} iteration(s) (7 view updates each, FP64 direct sums, compound kernels of Eq. 222) of the "
+                f"1024x1024x512 specimen's recipe on a {X}x{Y}x{Z} block, {seconds:.1f} s")
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    w = _workload(0)
-    eps = 1e-4 * float(np.mean([v.mean(dtype=np.float64) for v in w.views]))
-    _cpu_baseline(w, eps, steps=args.warmup) if args.warmup > 0 else None
-    times, cores = _cpu_baseline(w, eps, steps=args.steps)
+    s = OracleSample()
+    for _ in range(args.warmup):
+        s.step()
+    times = [s.step() for _ in range(args.steps)]
     total = sum(times)
-    value = w.voxels * args.steps / total / 1e9
-    sample = (f"one view update (view 0) of the {w.dims[0]}x{w.dims[1]}x{w.dims[2]} 4-view workload per step, "
-              f"FP64 direct convolution")
+    value = s.units * args.steps / total / 1e9
+    X, Y, Z = SPECIMEN_DIMS
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "volume": list(w.dims), "views": w.n_views, "psf_box": [15, 15, 41],
-                   "iterations": w.n_iter, "variant": "efficient"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "config": {"workload": f"ellipsoids-{X}x{Y}x{Z}-7views", "volume": [X, Y, Z], "views": 7,
+                   "psf_box": [19, 19, 51], "iterations": 10, "variant": "efficient"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": s.cores, "kind": "oracle",
+                         "sample": "per step: " + s.describe(1, total / max(1, args.steps))},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------------------
+# roofline of the dominant kernel
+# ---------------------------------------------------------------------------
+
+def _profiled_counters(kernel: str, dims):
+    """DRAM bytes and FP32 thread instructions per launch of ``kernel`` on ``dims`` from the
+    committed ncu summary (profiles/traffic.json); entries captured on a smaller grid of the
+    same recipe carry the voxel ratio they were scaled by."""
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tf):
+        return None
+    with open(tf) as fh:
+        tr = json.load(fh)
+    rec = tr.get(f"{kernel}@{dims[0]}x{dims[1]}x{dims[2]}")
+    if rec is None:
+        return None
+    if isinstance(rec, (int, float)):
+        return {"dram_bytes": float(rec)}
+    return rec
+
+
+def _kernel_table(prof, kb, peak):
+    tot = sum(t for (_, t) in prof.values())
+    out = {}
+    for name, (n, ms) in prof.items():
+        if n and name in kb:
+            avg_s = ms / n * 1e-3
+            out[name] = {"launches": n, "avg_us": avg_s * 1e6, "share": ms / max(1e-12, tot),
+                         "GBps": kb[name] / avg_s / 1e9, "hbm_frac": kb[name] / avg_s / 1e9 / peak}
+    return out
+
+
+def _roofline(prof, kernels, dims, peak, peak_kind, alu_peak, units_per_step, ms_step):
+    dom = max(kernels, key=lambda k: prof[k][1])
+    rec = kernels[dom]
+    roof = {"bound": "hbm", "kernel": dom, "achieved": rec["GBps"], "peak": peak, "unit": "GB/s",
+            "frac": rec["GBps"] / peak, "traffic": None, "peak_source": peak_kind,
+            "achieved_basis": "algorithmic bytes per launch (every array the kernel must touch, once) / "
+                              "CUDA-event launch time"}
+    cnt = _profiled_counters(dom, dims)
+    if cnt:
+        avg_s = rec["avg_us"] * 1e-6
+        if "dram_bytes" in cnt:
+            roof["traffic"] = int(cnt["dram_bytes"])
+            roof["dram_frac"] = cnt["dram_bytes"] / avg_s / 1e9 / peak
+        if "fp32_inst" in cnt:
+            roof["alu_frac"] = cnt["fp32_inst"] / avg_s / 1e12 / alu_peak
+            roof["alu_peak_Tinst"] = alu_peak
+        if "source" in cnt:
+            roof["counters_source"] = cnt["source"]
+    # the whole update against the 12 B per voxel-view it must move (read psi and phi_v, write psi)
+    roof["update_effective_frac"] = 12.0 * units_per_step / (ms_step * 1e-3) / 1e9 / peak
+    return roof
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def _events_ms(stream, fn, n):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _profile_step(mvd, d, fn):
+    """Per-kernel CUDA-event times of one more step, its kernels launched one by one."""
+    mvd.mvd_profile_enable(True)
+    fn()
+    d.synchronize()
+    prof = mvd.mvd_profile_read()
+    mvd.mvd_profile_enable(False)
+    return prof
+
+
+def _mid_record(args, mvd, stream, peak):
+    """The 256x256x128 four-view workload, 20 iterations, device-resident: precise (the
+    parity-held pipeline), all-FP32 and mixed precision."""
+    import torch
+
+    w = _workload(0)
+    X, Y, Z = w.dims
+    units = w.voxels * w.n_views * w.n_iter
+    K = max(1, min(args.steps, 10))
+    with torch.cuda.stream(stream):
+        dviews = [torch.from_numpy(v).cuda() for v in w.views]
+    stream.synchronize()
+    rec = {"workload": w.name, "volume": [X, Y, Z], "views": w.n_views, "iterations": w.n_iter, "steps": K,
+           "warmup": 3}
+    results = {}
+    for precision in ("precise", "fast", "mixed"):
+        with mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft", precision=precision) as d:
+            def step():
+                d.set_estimate(None)
+                d.iterate(w.n_iter)
+
+            for _ in range(3):
+                step()
+            d.synchronize()
+            ms = _events_ms(stream, step, K) / K
+            prof = _profile_step(mvd, d, step)
+            results[precision] = d.result().astype(np.float64)
+        kt = _kernel_table(prof, _kernel_bytes(X, Y, Z, precise=precision != "fast") if precision != "mixed"
+                           else {**_kernel_bytes(X, Y, Z, True), **_kernel_bytes(X, Y, Z, False)}, peak)
+        entry = {"value": units / (ms * 1e-3) / 1e9, "ms_per_step": ms, "kernels": kt}
+        if precision == "precise":
+            rec.update(entry)
+        else:
+            ref = results["precise"]
+            tau = 1e-3 * np.abs(ref).max()
+            entry["max_rel_diff_vs_precise"] = float(np.max(np.abs(results[precision] - ref)
+                                                            / np.maximum(np.abs(ref), tau)))
+            entry["precision"] = {"fast": "all FP32 (not held to 1e-4)",
+                                  "mixed": "double-float forward blur, FP32 back-projection (not held to 1e-4)"}[
+                precision]
+            rec["fast_fp32" if precision == "fast" else "mixed"] = entry
+    return rec
+
+
+def _batched_record(args, mvd, stream):
+    """The 48-volume batch (sizes 48^3 to 320x320x192, 2-6 views, 15 iterations each): the
+    volumes one after another (each its own per-iteration graph), one graph launch with one
+    branch per volume, and one persistent kernel over all volumes' FFT tiles."""
+    import torch
+
+    import synth
+
+    t0 = time.perf_counter()
+    ws = synth.config4(workers=os.cpu_count() or 1)
+    gen_s = time.perf_counter() - t0
+    ds = []
+    for w in ws:
+        with torch.cuda.stream(stream):
+            dv = [torch.from_numpy(v).cuda() for v in w.views]
+        stream.synchronize()
+        ds.append(mvd.Deconvolver(dv, w.psfs, "efficient", path="fft", stream=stream))
+    n_iter = ws[0].n_iter
+    units = sum(w.voxels * w.n_views * n_iter for w in ws)
+    K = max(1, min(args.steps, 5))
+
+    def reset():
+        for d in ds:
+            d.set_estimate(None)
+
+    def plain():
+        reset()
+        for d in ds:
+            d.iterate(n_iter)
+
+    for _ in range(3):
+        plain()
+    stream.synchronize()
+    plain_ms = _events_ms(stream, plain, K) / K
+    plain_res = [d.result() for d in ds]
+    out = {}
+    for mode in ("branches", "persistent"):
+        b = mvd.mvd_batch_create(ds, n_iter, mode)
+
+        def batched():
+            reset()
+            mvd.mvd_batch_run(b)
+
+        for _ in range(3):
+            batched()
+        mvd.mvd_batch_wait(b)
+        l0 = mvd.mvd_launch_count()
+        ms = _events_ms(stream, batched, K) / K
+        mvd.mvd_batch_wait(b)
+        launches = (mvd.mvd_launch_count() - l0) / K
+        errs = []
+        for d, p in zip(ds, plain_res):
+            q, p64 = d.result().astype(np.float64), p.astype(np.float64)
+            errs.append(float(np.max(np.abs(q - p64) / np.maximum(np.abs(p64), 1e-3 * np.abs(p64).max()))))
+        out[mode] = {"ms": ms, "value": units / (ms * 1e-3) / 1e9, "ratio": plain_ms / ms,
+                     "launches_per_run": launches, "tasks": mvd.mvd_batch_tasks(b),
+                     "max_rel_diff_vs_plain": max(errs)}
+        mvd.mvd_batch_destroy(b)
+    for d in ds:
+        d.close()
+    best = max(out, key=lambda m: out[m]["ratio"])
+    return {"workload": f"batch of {len(ws)} volumes (48^3 to 320x320x192, 2-6 views, 15 iterations each)",
+            "voxels": int(sum(w.voxels for w in ws)), "voxel_view_updates": int(units), "steps": K, "warmup": 3,
+            "plain_ms": plain_ms, "plain_value": units / (plain_ms * 1e-3) / 1e9,
+            "batched_ms": out[best]["ms"], "value": out[best]["value"], "mode": best,
+            "ratio": out[best]["ratio"], "modes": out, "generation_s": gen_s}
 
 
 def run_gpu(args):
@@ -253,18 +480,18 @@ def run_gpu(args):
     __graft_entry__.build()
     from paper_1308_0730_gb300 import mvd
 
-    w = _workload(rank)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    w = _specimen(rank, local, args.workload)
+    gen_s = time.perf_counter() - t0
     X, Y, Z = w.dims
     M = w.voxels
-    stream = torch.cuda.Stream()
-    upd_per_step = w.n_views * w.n_iter
-    units_per_step = M * upd_per_step
-
-    # --- device-resident run (value) ---
-    with torch.cuda.stream(stream):
-        dviews = [torch.from_numpy(v).to(f"cuda:{local}", non_blocking=False) for v in w.views]
-    stream.synchronize()
-    d = mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft", device=local)
+    units_per_step = M * w.n_views * w.n_iter
+    view_bytes = 4 * M * w.n_views
+    d = mvd.Deconvolver(w.views, w.psfs, "efficient", stream=stream, path="fft", device=local)
+    hviews = None if args.quick else w.host_views(pinned=True)
+    w.views = None
+    torch.cuda.empty_cache()
 
     def step():
         d.set_estimate(None)
@@ -277,219 +504,86 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = mvd.mvd_launch_count()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-        ev1.record(stream)
-        ev1.synchronize()
+        ms = _events_ms(stream, step, args.steps)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
     launches = mvd.mvd_launch_count() - launches0
-    # per-kernel durations: the same K steps again with CUDA events around
-    # every launch on the launching stream (kernels launched one by one)
-    mvd.mvd_profile_enable(True)
-    ev2 = torch.cuda.Event(enable_timing=True)
-    ev3 = torch.cuda.Event(enable_timing=True)
-    ev2.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev3.record(stream)
-    ev3.synchronize()
-    prof = mvd.mvd_profile_read()
-    mvd.mvd_profile_enable(False)
-    ms_profiled = ev2.elapsed_time(ev3)
     t_max = _max_over_ranks(ms, dist, f"cuda:{local}")
-    psi_dev = d.result()
-    d.close()
-
-    if args.quick:  # device-resident timing only (used for profiler captures)
+    prof = _profile_step(mvd, d, step)
+    value = _job_value(ws, units_per_step * args.steps, t_max * 1e-3)
+    peak, peak_kind = _peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = _alu_peak_tops(sms)
+    kernels = _kernel_table(prof, _kernel_bytes(X, Y, Z), peak)
+    roofline = _roofline(prof, kernels, (X, Y, Z), peak, peak_kind, alu_peak, units_per_step, t_max / args.steps)
+    cfg = {"workload": w.name, "volume": [X, Y, Z], "views": w.n_views, "psf_box": [19, 19, 51],
+           "iterations": w.n_iter, "variant": "efficient", "engine": "fft", "precision": "precise (double-float)",
+           "l2": f"inputs larger than L2 (views {view_bytes / 2**30:.1f} GiB, kernel spectra "
+                 f"{32 * (X // 2 + 1) * Y * Z * w.n_views / 2**30:.1f} GiB > 129 MiB)",
+           "inputs": "generated on the device (synth.config3_device)", "parallelism": f"replicas x{ws}"}
+    if args.quick:
+        psi_dev = None
+        d.close()
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": _job_value(ws, units_per_step * args.steps, t_max * 1e-3),
-                              "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-                              "ms_per_step": t_max / args.steps, "quick": True,
-                              "config": {"workload": w.name}}), flush=True)
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": t_max / args.steps, "quick": True,
+                              "config": cfg, "kernels": kernels, "roofline": roofline, "generation_s": gen_s}),
+                  flush=True)
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
         return 0
 
-    # the same steps with every pass in FP32 (MVD_FAST), for comparison
-    fast = mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft", device=local, precision="fast")
-
-    def fast_step():
-        fast.set_estimate(None)
-        fast.iterate(w.n_iter)
-
-    for _ in range(args.warmup):
-        fast_step()
-    ev4 = torch.cuda.Event(enable_timing=True)
-    ev5 = torch.cuda.Event(enable_timing=True)
-    ev4.record(stream)
-    for _ in range(args.steps):
-        fast_step()
-    ev5.record(stream)
-    ev5.synchronize()
-    ms_fast = ev4.elapsed_time(ev5)
-    psi_fast = fast.result()
-    # per-kernel events of the FP32 passes (HBM-bound): one more step, launched one by one
-    mvd.mvd_profile_enable(True)
-    fast_step()
-    fast.synchronize()
-    prof_fast = mvd.mvd_profile_read()
-    mvd.mvd_profile_enable(False)
-    fast.close()
-
-    # the same steps with the FP32 back-projection (MVD_MIXED), for comparison
-    mixed = mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft", device=local, precision="mixed")
-
-    def mixed_step():
-        mixed.set_estimate(None)
-        mixed.iterate(w.n_iter)
-
-    for _ in range(args.warmup):
-        mixed_step()
-    ev6 = torch.cuda.Event(enable_timing=True)
-    ev7 = torch.cuda.Event(enable_timing=True)
-    ev6.record(stream)
-    for _ in range(args.steps):
-        mixed_step()
-    ev7.record(stream)
-    ev7.synchronize()
-    ms_mixed = ev6.elapsed_time(ev7)
-    psi_mixed = mixed.result()
-    mixed.close()
-
     # --- end to end through the public API from pinned host buffers ---
-    # A time series with fixed PSFs: one context; every step loads the time
-    # point's views from pinned host memory (mvd_set_views: H2D, view mean,
-    # flat estimate), runs the 20 iterations and copies the result back.
-    # "cold" builds and tears down a whole context per step instead.
-    pinned = [torch.from_numpy(v).pin_memory() for v in w.views]
-    hviews = [p.numpy() for p in pinned]
-    out = torch.empty(w.truth.shape, dtype=torch.float32).pin_memory().numpy()
-    series = mvd.Deconvolver(hviews, w.psfs, "efficient", stream=stream, path="fft", device=local)
+    psi_dev = d.result()
+    out = torch.empty(psi_dev.shape, dtype=torch.float32).pin_memory().numpy()
 
     def e2e_step():
-        series.set_views(hviews)
-        series.iterate(w.n_iter)
-        series.result(out)
+        d.set_views(hviews)
+        d.iterate(w.n_iter)
+        d.result(out)
 
-    def cold_step():
-        with mvd.Deconvolver(hviews, w.psfs, "efficient", stream=stream, path="fft", device=local) as e:
-            e.iterate(w.n_iter)
-            e.result(out)
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_step()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, f"cuda:{local}")
+    assert np.array_equal(out, psi_dev), "end-to-end result differs from the device-resident run"
+    d.close()
+    del hviews, psi_dev
 
-    def timed(step, n):
-        step()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(n):
-            step()
-        torch.cuda.synchronize()
-        return _max_over_ranks((time.perf_counter() - t0) / n, dist, f"cuda:{local}")
-
-    e2e_s = timed(e2e_step, max(1, args.steps))
-    assert np.allclose(out, psi_dev, rtol=1e-6, atol=0), "end-to-end result differs from the device run"
-    series.close()
-    cold_s = timed(cold_step, max(1, min(args.steps, 5)))
-    assert np.allclose(out, psi_dev, rtol=1e-6, atol=0), "end-to-end result differs from the device run"
-
+    mid = batched = cpu = None
+    if ws == 1:
+        mid = _mid_record(args, mvd, stream, peak)
+        batched = _batched_record(args, mvd, stream)
+        s = OracleSample()
+        times = [s.step() for _ in range(3)]
+        cpu = {"value": s.units * len(times) / sum(times) / 1e9, "unit": UNIT, "cores": s.cores, "kind": "oracle",
+               "sample": s.describe(len(times), sum(times))}
     if rank == 0:
-        peak, peak_kind = _peaks()
-        kb = _kernel_bytes(X, Y, Z)
-        per_kernel = {}
-        for name, (n, tot) in prof.items():
-            if n and name in kb:
-                per_kernel[name] = {"launches": n, "avg_us": 1e3 * tot / n, "share": tot / max(1e-9, sum(
-                    t for (_, t) in prof.values())), "GBps": kb[name] / (tot / n * 1e-3) / 1e9}
-        ops = _kernel_alu_ops(X, Y, Z)
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        alu_peak = _alu_peak_tops(sms)
-        for name, rec in per_kernel.items():
-            if name in ops:
-                rec["alu_Tops"] = ops[name] / (rec["avg_us"] * 1e-6) / 1e12
-                rec["alu_frac"] = rec["alu_Tops"] / alu_peak
-            rec["hbm_frac"] = rec["GBps"] / peak
-        dom = max(per_kernel, key=lambda k: prof[k][1])
-        traffic = None
-        tf = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tf):
-            with open(tf) as fh:
-                tr = json.load(fh)
-            key = f"{dom}@{X}x{Y}x{Z}"
-            traffic = tr.get(key)
-        if dom.startswith("dd_"):  # issue-bound on the FP32 pipes (see profiles/)
-            roofline = {"bound": "alu", "kernel": dom, "achieved": per_kernel[dom]["alu_Tops"], "peak": alu_peak,
-                        "unit": "T FP32 ops/s", "frac": per_kernel[dom]["alu_Tops"] / alu_peak,
-                        "traffic": traffic, "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2070 MHz",
-                        "hbm_frac_same_kernel": per_kernel[dom]["hbm_frac"]}
-        else:
-            roofline = {"bound": "hbm", "kernel": dom, "achieved": per_kernel[dom]["GBps"], "peak": peak,
-                        "unit": "GB/s", "frac": per_kernel[dom]["GBps"] / peak, "traffic": traffic,
-                        "peak_source": peak_kind}
-        kbf = _kernel_bytes(X, Y, Z, precise=False)
-        tot_fast = sum(t for (_, t) in prof_fast.values())
-        fast_kernels = {}
-        for name, (n, tot) in prof_fast.items():
-            if n and name in kbf:
-                gbps = kbf[name] / (tot / n * 1e-3) / 1e9
-                fast_kernels[name] = {"launches": n, "avg_us": 1e3 * tot / n, "share": tot / max(1e-9, tot_fast),
-                                      "GBps": gbps, "hbm_frac": gbps / peak}
-        fast_roof = None
-        if fast_kernels:
-            fd = max(fast_kernels, key=lambda k: prof_fast[k][1])
-            fast_roof = {"bound": "hbm", "kernel": fd, "achieved": fast_kernels[fd]["GBps"], "peak": peak,
-                         "unit": "GB/s", "frac": fast_kernels[fd]["hbm_frac"], "traffic": None,
-                         "peak_source": peak_kind}
-        value = _job_value(ws, units_per_step * args.steps, t_max * 1e-3)
-        # about 10 s of host work: view updates of the same workload, one after another
-        cpu_times, cores = _cpu_baseline(w, 1e-4 * float(np.mean([v.mean(dtype=np.float64) for v in w.views])),
-                                         steps=5)
-        cpu_value = M * len(cpu_times) / sum(cpu_times) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "volume": [X, Y, Z], "views": w.n_views,
-                       "psf_box": [15, 15, 41], "iterations": w.n_iter, "variant": "efficient",
-                       "engine": "fft", "l2": "inputs larger than L2 (views + kernel spectra "
-                       f"{(4 * M * w.n_views + 16 * (X // 2 + 1) * Y * Z * w.n_views) / 2**20:.0f} MiB > 129 MiB)",
-                       "parallelism": f"replicas x{ws}"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "e2e": {"value": _job_value(ws, units_per_step, e2e_s), "unit": UNIT,
-                    "h2d_bytes_per_step": int(sum(v.nbytes for v in w.views)),
-                    "d2h_bytes_per_step": int(out.nbytes),
-                    "per_step": "time series with fixed PSFs: load the views from pinned host memory "
-                                "(mvd_set_views), 20 iterations, result to pinned host memory; kernels "
-                                "precomputed once for the series",
-                    "cold_value": _job_value(ws, units_per_step, cold_s),
-                    "cold_per_step": "create (views H2D) + precompute + iterate + result (D2H) + destroy"},
+                    "h2d_bytes_per_step": int(view_bytes), "d2h_bytes_per_step": int(out.nbytes),
+                    "steps": e2e_steps,
+                    "per_step": "time series with fixed PSFs: load the 7 views from pinned host memory "
+                                "(mvd_set_views), 10 iterations, result to pinned host memory; kernels "
+                                "precomputed once for the series"},
             "gpu_launches": int(launches),
             "roofline": roofline,
-            "update_effective_hbm_frac": (12.0 * units_per_step * args.steps / (ms * 1e-3) / 1e9) / peak,
-            "kernels": per_kernel,
-            "profiled_ms_per_step": ms_profiled / args.steps,
-            "precision": "double-float (pairs of FP32) for the forward blur and the back-projection's y and z passes; FP32 x passes of the back-projection",
-            "fast_fp32": {"value": ws * units_per_step * args.steps / (ms_fast * 1e-3) / 1e9, "unit": UNIT,
-                          "ms_per_step": ms_fast / args.steps,
-                          "kernels": fast_kernels, "roofline": fast_roof,
-                          "max_rel_diff_vs_precise": float(np.max(np.abs(psi_fast.astype(np.float64) - psi_dev)
-                                                                  / np.maximum(np.abs(psi_dev.astype(np.float64)),
-                                                                               1e-3 * np.abs(psi_dev).max())))},
-            "mixed": {"value": ws * units_per_step * args.steps / (ms_mixed * 1e-3) / 1e9, "unit": UNIT,
-                      "ms_per_step": ms_mixed / args.steps,
-                      "precision": "double-float forward blur, FP32 back-projection (not held to 1e-4)",
-                      "max_rel_diff_vs_precise": float(np.max(np.abs(psi_mixed.astype(np.float64) - psi_dev)
-                                                              / np.maximum(np.abs(psi_dev.astype(np.float64)),
-                                                                           1e-3 * np.abs(psi_dev).max())))},
+            "kernels": kernels,
             "clocks": clk.summary(),
-            "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{len(cpu_times)} view updates (view 0) of the {X}x{Y}x{Z} workload, "
-                                       f"FP64 direct convolution, {sum(cpu_times):.1f} s"},
+            "cpu_baseline": cpu,
+            "mid": mid,
+            "batched": batched,
+            "generation_s": gen_s,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -499,151 +593,22 @@ def run_gpu(args):
 
 
 def run_batched(args):
-    """48 volumes of uneven size and view count (15 iterations each): one persistent
-    batched launch vs the same volumes deconvolved one after another."""
+    """The 48-volume batch alone (one JSON line)."""
     import torch
 
     import __graft_entry__
-    import synth
 
     __graft_entry__.build()
     from paper_1308_0730_gb300 import mvd
 
-    t0 = time.perf_counter()
-    ws = synth.config4()
-    gen_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
-    ds = []
-    for w in ws:
-        with torch.cuda.stream(stream):
-            dv = [torch.from_numpy(v).cuda() for v in w.views]
-        stream.synchronize()
-        ds.append(mvd.Deconvolver(dv, w.psfs, "efficient", path="fft", stream=stream))
-    n_iter = ws[0].n_iter
-    units = sum(w.voxels * w.n_views * n_iter for w in ws)
-
-    def reset():
-        for d in ds:
-            d.set_estimate(None)
-
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # plain: one volume after another (each replays its own per-iteration graph)
-    for _ in range(max(1, args.warmup)):
-        reset()
-        for d in ds:
-            d.iterate(n_iter)
-    plain_ms = []
-    for _ in range(args.steps):
-        reset()
-        ev0.record(stream)
-        for d in ds:
-            d.iterate(n_iter)
-        ev1.record(stream)
-        ev1.synchronize()
-        plain_ms.append(ev0.elapsed_time(ev1))
-    plain_res = [d.result() for d in ds]
-
-    def time_batch(mode):
-        b = mvd.mvd_batch_create(ds, n_iter, mode)
-        for _ in range(max(1, args.warmup)):
-            reset()
-            mvd.mvd_batch_run(b)
-            mvd.mvd_batch_wait(b)
-        ms = []
-        launches0 = mvd.mvd_launch_count()
-        with ClockSampler(torch.cuda.current_device()) as clk:
-            for _ in range(args.steps):
-                reset()
-                ev0.record(stream)
-                mvd.mvd_batch_run(b)
-                ev1.record(stream)
-                ev1.synchronize()
-                ms.append(ev0.elapsed_time(ev1))
-        mvd.mvd_batch_wait(b)
-        launches = (mvd.mvd_launch_count() - launches0) / args.steps
-        res = [d.result() for d in ds]
-        tasks = mvd.mvd_batch_tasks(b)
-        mvd.mvd_batch_destroy(b)
-        return statistics.median(ms), res, tasks, launches, clk.summary()
-
-    per_ms, per_res, per_tasks, _, _ = time_batch("persistent")
-    batch_ms_med, batch_res, tasks, launches, clocks = time_batch("branches")
-    for d in ds:
-        d.close()
-    errs = []
-    for p, q, r in zip(plain_res, batch_res, per_res):
-        p64 = p.astype(np.float64)
-        tau = 1e-3 * np.abs(p64).max()
-        errs.append(float(np.max(np.abs(q - p64) / np.maximum(np.abs(p64), tau))))
-        errs.append(float(np.max(np.abs(r - p64) / np.maximum(np.abs(p64), tau))))
-    pm, bm = statistics.median(plain_ms), batch_ms_med
-    line = {
-        "metric": METRIC, "value": units / (bm * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": bm, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batch of {len(ws)} volumes (48^3 to 320x320x192, 2-6 views, 15 iterations)",
-                   "voxels": int(sum(w.voxels for w in ws)), "voxel_view_updates": int(units),
-                   "engine": "fft", "batch_mode": "branches", "l2": "inputs larger than L2"},
-        "batched_vs_plain": {"batched_ms": bm, "plain_ms": pm, "speedup": pm / bm,
-                             "plain_value": units / (pm * 1e-3) / 1e9, "kernels_per_run": tasks,
-                             "persistent_ms": per_ms, "persistent_speedup": pm / per_ms,
-                             "persistent_tiles_per_run": per_tasks,
-                             "max_rel_err_batched_vs_plain": max(errs)},
-        "gpu_launches": launches,
-        "generation_s": gen_s,
-        "clocks": clocks,
-    }
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_large(args):
-    """The 1024x1024x512 seven-view specimen, 10 iterations, device-resident."""
-    import torch
-
-    import __graft_entry__
-    import synth
-
-    __graft_entry__.build()
-    from paper_1308_0730_gb300 import mvd
-
-    t0 = time.perf_counter()
-    w = synth.config3()
-    gen_s = time.perf_counter() - t0
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        dviews = [torch.from_numpy(v).cuda() for v in w.views]
-    stream.synchronize()
-    d = mvd.Deconvolver(dviews, w.psfs, "efficient", stream=stream, path="fft")
-    del dviews
-    torch.cuda.empty_cache()
-    free_b, total_b = torch.cuda.mem_get_info()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(max(1, args.warmup)):
-        d.set_estimate(None)
-        d.iterate(1)
-    d.synchronize()
-    ms = []
     with ClockSampler(torch.cuda.current_device()) as clk:
-        for _ in range(args.steps):
-            d.set_estimate(None)
-            ev0.record(stream)
-            d.iterate(w.n_iter)
-            ev1.record(stream)
-            ev1.synchronize()
-            ms.append(ev0.elapsed_time(ev1))
-    d.close()
-    units = w.voxels * w.n_views * w.n_iter
-    m = statistics.median(ms)
+        b = _batched_record(args, mvd, stream)
     print(json.dumps({
-        "metric": METRIC, "value": units / (m * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": m, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "volume": list(w.dims), "views": w.n_views, "psf_box": [19, 19, 51],
-                   "iterations": w.n_iter, "variant": "efficient", "engine": "fft", "precision": "precise",
-                   "l2": "inputs larger than L2"},
-        "device_used_gib": (total_b - free_b) / 2**30, "generation_s": gen_s, "clocks": clk.summary()}),
-        flush=True)
+        "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": b["steps"], "warmup": 3,
+        "ms_per_step": b["batched_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": {"workload": b["workload"]}, "batched": b,
+        "clocks": clk.summary()}), flush=True)
     return 0
 
 
@@ -864,7 +829,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mvd", choices=["mvd", "reference"])
     ap.add_argument("--quick", action="store_true",
-                    help="only the device-resident timing (no FP32 comparison, end-to-end or CPU legs)")
+                    help="only the device-resident timing and per-kernel events (no end-to-end, sub-records or CPU legs)")
     ap.add_argument("--weighted", action="store_true",
                     help="time the sequential update with partial-overlap view weights instead")
     ap.add_argument("--combined", action="store_true",
@@ -875,8 +840,8 @@ def main():
                     help="zero / mirror: time the sequential update with that boundary (padded grid) instead")
     ap.add_argument("--grad", action="store_true",
                     help="time the PSF-calibration step (8 unrolled iterations, forward + adjoint) instead")
-    ap.add_argument("--large", action="store_true",
-                    help="time the 1024x1024x512 seven-view specimen (10 iterations) instead")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="specimen",
+                    help="grid of the headline recipe (smaller ones for profiler captures)")
     ap.add_argument("--batched", action="store_true",
                     help="time the 48-volume batched workload against per-volume runs instead")
     args = ap.parse_args()
@@ -884,8 +849,6 @@ def main():
         return run_reference(args)
     if args.batched:
         return run_batched(args)
-    if args.large:
-        return run_large(args)
     if args.grad:
         return run_grad(args)
     if args.combined:

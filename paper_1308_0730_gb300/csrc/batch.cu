@@ -602,7 +602,7 @@ mvd_status mvd_batch_create_mode(mvd_ctx* const* ctxs, int n, int n_iter, int mo
         smem = std::max({smem, d.fx ? fast_x_smem(g.X) : gen_x_smem(g.X), d.fy ? fast_y_smem(g.Y) : gen_y_smem(g.Y),
                          d.fz ? fast_z_smem(g.Z) : gen_z_smem(g.Z, g.Y)});
         if (d.precise)
-            smem = std::max({smem, d.fx ? ddf_x_smem(g.X) : dd_x_smem(g.X), d.fy ? ddf_y_smem(g.Y) : dd_y_smem(g.Y),
+            smem = std::max({smem, d.fx ? ddf_ratio_smem(g.X) : dd_x_smem(g.X), d.fy ? ddf_y_smem(g.Y) : dd_y_smem(g.Y),
                              d.fz ? ddf_z_smem(g.Z) : dd_z_smem(g.Z, g.Y)});
     }
     // Entries (default schedule: views 0..nv-1 per iteration). Each volume's

@@ -119,6 +119,12 @@ mvd_status fft_x_accumulate_dd_fast(const FftGeom& g, const cdd* S2, float* acc,
 // double-float forward blur (fft_dd.cu): spectrum of complex double-float
 mvd_status dd_forward_real(const FftGeom& g, const float* src, cdd* S2, cudaStream_t st);
 mvd_status dd_y(const FftGeom& g, cdd* S2, int inverse, cudaStream_t st);
+// register-resident x and y lengths: the back-projection's y passes can take
+// and hand over FP32 spectra (forward y of the FP32 r - 1 spectrum into S2;
+// inverse y of S2 rounded into the FP32 spectrum for the FP32 x inverse)
+bool dd_fast_yx(const FftGeom& g);
+mvd_status dd_y_from_f32(const FftGeom& g, const float2* S1, cdd* S2, cudaStream_t st);
+mvd_status dd_y_inverse_to_f32(const FftGeom& g, cdd* S2, float2* S1, cudaStream_t st);
 mvd_status dd_z_mul(const FftGeom& g, cdd* S2, const cdd* K2, cudaStream_t st);
 mvd_status dd_z_forward_scaled(const FftGeom& g, cdd* S2, double scale, cudaStream_t st);
 // the inverse x of b (double-float) -> r - 1 -> FP32 forward x, written to the

@@ -37,10 +37,10 @@ __global__ void __launch_bounds__(kGenThreads, kDdGenBlocks) k_dd_z(DdZ a) {
 }
 
 // register-resident double-float passes (power-of-two lengths)
-template <int L, int S>
-__global__ void __launch_bounds__(kDdThreads) k_ddf_y(cdd* S2, long nlines, const cdd* tw2) {
+template <int L, int S, int IO = 0>
+__global__ void __launch_bounds__(kDdThreads) k_ddf_y(cdd* S2, long nlines, const cdd* tw2, float2* S1) {
     extern __shared__ cdd smd[];
-    ddf_y_tile<L, S, false>(S2, nlines, tw2, blockIdx.x, smd);
+    ddf_y_tile<L, S, false, IO>(S2, nlines, tw2, blockIdx.x, smd, S1);
 }
 
 template <int L, bool MUL>
@@ -162,7 +162,7 @@ mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cu
         a.eps = eps;
         with_dd_len(g.X, [&](auto Lc) {
             constexpr int L = decltype(Lc)::value;
-            rc = launch_raw(k_ddf_x_ratio<L>, gen_div_up(g.YZ, 2 * ddf_pairs(L)), kDdThreads, ddf_x_smem(L), st,
+            rc = launch_raw(k_ddf_x_ratio<L>, gen_div_up(g.YZ, 2 * ddf_pairs(L)), kDdThreads, ddf_ratio_smem(L), st,
                             "dd x ratio (fast)", KC_DD_X_RATIO, a);
         });
         return rc;
@@ -182,13 +182,45 @@ mvd_status dd_y(const FftGeom& g, cdd* S2, int inverse, cudaStream_t st) {
         with_dd_len(g.Y, [&](auto Lc) {
             constexpr int L = decltype(Lc)::value;
             rc = launch_raw(inverse ? k_ddf_y<L, +1> : k_ddf_y<L, -1>, gen_div_up(nl, ddf_y_lines(L)), kDdThreads,
-                            ddf_y_smem(L), st, "dd y (fast)", KC_DD_Y, S2, nl, g.tw2y);
+                            ddf_y_smem(L), st, "dd y (fast)", KC_DD_Y, S2, nl, g.tw2y, (float2*)nullptr);
         });
         return rc;
     }
     DdY a = dd_y_args(g.Y, g.Xh, g.Z, g.py, g.tw2y, S2);
     return launch(inverse ? k_dd_y<+1> : k_dd_y<-1>, a, dd_y_tiles(g.Y, g.Xh, g.Z), dd_y_smem(g.Y), st, "dd y",
                   KC_DD_Y);
+}
+
+bool dd_fast_yx(const FftGeom& g) { return g.fast && dd_fast_length(g.X) && dd_fast_length(g.Y); }
+
+mvd_status dd_y_from_f32(const FftGeom& g, const float2* S1, cdd* S2, cudaStream_t st) {
+    if (!dd_fast_yx(g)) {
+        set_error("dd y from FP32: needs register-resident x and y lengths, got %d x %d", g.X, g.Y);
+        return MVD_ERR_UNSUPPORTED;
+    }
+    mvd_status rc = MVD_ERR_UNSUPPORTED;
+    const long nl = (long)g.Xh * g.Z;
+    with_dd_len(g.Y, [&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        rc = launch_raw(k_ddf_y<L, -1, 1>, gen_div_up(nl, ddf_y_lines(L)), kDdThreads, ddf_y_smem(L), st,
+                        "dd y (FP32 in)", KC_DD_Y, S2, nl, g.tw2y, const_cast<float2*>(S1));
+    });
+    return rc;
+}
+
+mvd_status dd_y_inverse_to_f32(const FftGeom& g, cdd* S2, float2* S1, cudaStream_t st) {
+    if (!dd_fast_yx(g)) {
+        set_error("dd y to FP32: needs register-resident x and y lengths, got %d x %d", g.X, g.Y);
+        return MVD_ERR_UNSUPPORTED;
+    }
+    mvd_status rc = MVD_ERR_UNSUPPORTED;
+    const long nl = (long)g.Xh * g.Z;
+    with_dd_len(g.Y, [&](auto Lc) {
+        constexpr int L = decltype(Lc)::value;
+        rc = launch_raw(k_ddf_y<L, +1, 2>, gen_div_up(nl, ddf_y_lines(L)), kDdThreads, ddf_y_smem(L), st,
+                        "dd y (FP32 out)", KC_DD_Y, S2, nl, g.tw2y, S1);
+    });
+    return rc;
 }
 
 static mvd_status ddf_z(const FftGeom& g, cdd* S2, const cdd* K2, dd scale, bool mul, cudaStream_t st) {

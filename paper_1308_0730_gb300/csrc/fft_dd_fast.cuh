@@ -168,6 +168,18 @@ __host__ __device__ constexpr size_t ddf_x_smem(int L) {
 __host__ __device__ constexpr size_t ddf_y_smem(int L) { return (size_t)ddf_y_lines(L) * line_stride8(L) * sizeof(cdd); }
 __host__ __device__ constexpr size_t ddf_z_smem(int L) { return (size_t)ddf_z_cols(L) * line_stride8(L) * sizeof(cdd); }
 
+// 16-byte asynchronous global -> shared copy (L2 only); with !valid nothing is
+// read and the 16 bytes are zero-filled (src then only needs to be a valid
+// address)
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, bool valid) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <bool CO>
 __device__ __forceinline__ cdd ld_cdd(const cdd* p) {
     if constexpr (CO)
@@ -176,22 +188,43 @@ __device__ __forceinline__ cdd ld_cdd(const cdd* p) {
         return cdd_load(p);
 }
 
-template <int L, int S, bool CO>
+// IO selects where the lines come from and go to:
+//   0: the double-float spectrum S2, in place;
+//   1: read the FP32 spectrum S1 (each value widened exactly), write S2;
+//   2: read S2, write S1 with each value rounded to the nearest FP32 (hi + lo).
+// IO 1 takes the ratio pass's FP32 spectrum of r - 1 (exact FP32 values, so
+// nothing is lost against storing them as double-float); IO 2 hands the
+// inverse y transform to the FP32 x inverse of the update, which rounds its
+// input to FP32 in any case. Both halve the bytes of the side in FP32.
+template <int L, int S, bool CO, int IO = 0>
 __device__ __forceinline__ void ddf_y_tile(cdd* __restrict__ S2, long nlines, const cdd* __restrict__ tw2, long tile,
-                                           cdd* sm) {
+                                           cdd* sm, float2* __restrict__ S1 = nullptr) {
     using F = LineFFTDD<L, S, true>;
     constexpr int TPL = F::TPL, LPC = kDdThreads / TPL;
     const int li = threadIdx.x / TPL, t = threadIdx.x - li * TPL;
     const long line = tile * LPC + li;
     const bool ok = line < nlines;
     cdd* g = S2 + line * L;
+    float2* g1 = S1 + line * L;
     cdd v[kE8];
 #pragma unroll
-    for (int q = 0; q < kE8; ++q) v[q] = ok ? ld_cdd<CO>(g + t + TPL * q) : czero_dd();
+    for (int q = 0; q < kE8; ++q) {
+        if constexpr (IO == 1) {
+            const float2 f = ok ? (CO ? __ldcg(g1 + t + TPL * q) : g1[t + TPL * q]) : make_float2(0.f, 0.f);
+            v[q] = cdd{dd_from(f.x), dd_from(f.y)};
+        } else {
+            v[q] = ok ? ld_cdd<CO>(g + t + TPL * q) : czero_dd();
+        }
+    }
     F::run(v, sm + li * line_stride8(L), t, tw2);
     if (ok) {
 #pragma unroll
-        for (int q = 0; q < kE8; ++q) cdd_store(g + t + TPL * q, v[q]);
+        for (int q = 0; q < kE8; ++q) {
+            if constexpr (IO == 2)
+                g1[t + TPL * q] = make_float2(v[q].re.hi + v[q].re.lo, v[q].im.hi + v[q].im.lo);
+            else
+                cdd_store(g + t + TPL * q, v[q]);
+        }
     }
 }
 
@@ -284,19 +317,23 @@ __device__ __forceinline__ void ddf_x_forward_tile(const DdXFast& a, long tile, 
     ddf_store_halves<L>(a, v, sm, p, t, rho0, nrows);
 }
 
-// gather the half spectra of rows rho0 + p (A) and rho0 + P + p (B) of a
-// tile and form the full spectrum of the complex line A + iB in v
-template <int L, bool CO>
-__device__ __forceinline__ void ddf_gather_pair(const DdXFast& a, long rho0, int nrows, int p, int t, cdd* sm,
-                                                cdd (&v)[kE8]) {
-    constexpr int TPL = L / kE8, P = ddf_pairs(L), HS = half_stride8(L), XH = L / 2 + 1;
-    // rows < P -> row p (A), rows >= P -> row P + p (B), at stride HS
+// issue the asynchronous copies of the half spectra of rows rho0 + p (A) and
+// rho0 + P + p (B) of a tile into shared memory (rows < P -> row p, rows >= P
+// -> row P + p, at stride HS); every copy is in flight before any completes
+template <int L>
+__device__ __forceinline__ void ddf_gather_issue(const DdXFast& a, long rho0, int nrows, cdd* sm) {
+    constexpr int P = ddf_pairs(L), HS = half_stride8(L), XH = L / 2 + 1;
     for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
         const int k = idx / (2 * P), row = idx - k * 2 * P;
-        const cdd val = row < nrows ? ld_cdd<CO>(a.S2 + (long)k * a.YZ + rho0 + row) : czero_dd();
-        cdd_store(sm + row * HS + pad8(k), val);
+        const bool ok = row < nrows;
+        cp_async16(sm + row * HS + pad8(k), ok ? a.S2 + (long)k * a.YZ + rho0 + row : a.S2, ok);
     }
-    __syncthreads();
+}
+
+// the full spectrum of the complex line A + iB of pair p from the gathered halves
+template <int L>
+__device__ __forceinline__ void ddf_pair_line(const cdd* sm, int p, int t, cdd (&v)[kE8]) {
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), HS = half_stride8(L);
 #pragma unroll
     for (int q = 0; q < kE8; ++q) {
         const int k = t + TPL * q;
@@ -305,6 +342,17 @@ __device__ __forceinline__ void ddf_gather_pair(const DdXFast& a, long rho0, int
         v[q] = k <= L / 2 ? cdd{dd_sub(A.re, B.im), dd_add(A.im, B.re)}    // A + iB
                           : cdd{dd_add(A.re, B.im), dd_sub(B.re, A.im)};   // conj(A) + i conj(B)
     }
+}
+
+// gather the half spectra of rows rho0 + p (A) and rho0 + P + p (B) of a
+// tile and form the full spectrum of the complex line A + iB in v
+template <int L, bool CO>
+__device__ __forceinline__ void ddf_gather_pair(const DdXFast& a, long rho0, int nrows, int p, int t, cdd* sm,
+                                                cdd (&v)[kE8]) {
+    ddf_gather_issue<L>(a, rho0, nrows, sm);
+    cp_async_wait_all();
+    __syncthreads();
+    ddf_pair_line<L>(sm, p, t, v);
 }
 
 // double-float spectrum -> inverse x -> real rows (rounded to FP32) in dst
@@ -327,8 +375,16 @@ __device__ __forceinline__ void ddf_x_inverse_tile(const DdXFast& a, long tile, 
     }
 }
 
+// shared memory of the ratio pass: the x-pass buffer, then the 2P observed rows
+__host__ __device__ constexpr size_t ddf_ratio_smem(int L) {
+    return ddf_x_smem(L) + (size_t)2 * ddf_pairs(L) * L * sizeof(float);
+}
+
 // double-float spectrum -> inverse x -> b -> r - 1 = phi / max(b, eps) - 1
-// -> FP32 forward x -> back into S2 as double-float
+// -> FP32 forward x -> the FP32 spectrum of r - 1 into S (or, without S, into
+// S2 as double-float). The half spectra and the observed rows are staged in
+// shared memory by asynchronous copies that are all in flight at once, so no
+// register holds them across the inverse transform.
 template <int L, bool CO>
 __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cdd* sm) {
     constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L), XH = L / 2 + 1;
@@ -336,16 +392,20 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
     const long rho0 = tile * 2 * P;
     const int nrows = (int)min((long)2 * P, a.YZ - rho0);
     const bool oka = p < nrows, okb = P + p < nrows;
-    cdd v[kE8];
-    ddf_gather_pair<L, CO>(a, rho0, nrows, p, t, sm, v);
-    // the observed rows, fetched now to overlap the inverse transform
-    float2 w[kE8];
-    const long ra = (rho0 + p) * L, rb = (rho0 + P + p) * L;
-#pragma unroll
-    for (int q = 0; q < kE8; ++q) {
-        const int n = t + TPL * q;
-        w[q] = make_float2(oka ? __ldg(a.phi + ra + n) : 0.f, okb ? __ldg(a.phi + rb + n) : 0.f);
+    float* phs = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + ddf_x_smem(L));  // 2P rows of L
+    ddf_gather_issue<L>(a, rho0, nrows, sm);
+    {
+        // the observed rows rho0 .. rho0 + nrows - 1 are contiguous: 2P * L floats
+        const float* src = a.phi + rho0 * L;
+        for (int c = threadIdx.x; c < 2 * P * L / 4; c += kDdThreads) {
+            const bool ok = c * 4 < nrows * L;
+            cp_async16(phs + 4 * c, ok ? src + 4 * c : a.phi, ok);
+        }
     }
+    cp_async_wait_all();
+    __syncthreads();
+    cdd v[kE8];
+    ddf_pair_line<L>(sm, p, t, v);
     __syncthreads();
     LineFFTDD<L, +1, true>::run(v, sm + p * LS, t, a.tw2);
     // r - 1 of both rows as one complex FP32 line, forward x in registers (the
@@ -355,9 +415,10 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
     float2 f[kE8];
 #pragma unroll
     for (int q = 0; q < kE8; ++q) {
+        const int n = t + TPL * q;
         const float ba = v[q].re.hi + v[q].re.lo, bb = v[q].im.hi + v[q].im.lo;
-        const float xa = oka ? w[q].x / fmaxf(ba, a.eps) - 1.f : 0.f;
-        const float xb = okb ? w[q].y / fmaxf(bb, a.eps) - 1.f : 0.f;
+        const float xa = oka ? phs[p * L + n] / fmaxf(ba, a.eps) - 1.f : 0.f;
+        const float xb = okb ? phs[(P + p) * L + n] / fmaxf(bb, a.eps) - 1.f : 0.f;
         f[q] = make_float2(xa, xb);
     }
     // each FP32 line lives inside its own line's double-float region (the

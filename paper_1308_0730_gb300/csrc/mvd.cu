@@ -505,6 +505,19 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
             // double-float, so no rounding of a large |r - 1| (a count where b
             // is near eps) spreads over the volume
             const cdd* Kc2 = reinterpret_cast<const cdd*>(K4 + ns * (2 * v + 1));
+            if (dd_fast_yx(g) && !mirror) {
+                // the same arithmetic with the FP32 ends of the back-projection
+                // stored as FP32: the ratio pass's r - 1 spectrum (exact FP32
+                // values) and the inverse y output, which the FP32 x inverse of
+                // the update rounds to FP32 anyway (bit-identical results, half
+                // the bytes on those two hand-overs)
+                MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream, c->d_S));
+                MVD_TRY(dd_y_from_f32(g, c->d_S, S2, c->stream));
+                MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
+                MVD_TRY(dd_y_inverse_to_f32(g, S2, c->d_S, c->stream));
+                if (prod) return fft_x_accumulate(g, c->d_S, prod, c->stream, inv_s);
+                return done(fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
+            }
             MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream));
             MVD_TRY(dd_y(g, S2, 0, c->stream));
             MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));

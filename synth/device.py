@@ -39,7 +39,7 @@ class DeviceWorkload:
 
     @property
     def n_views(self) -> int:
-        return len(self.views)
+        return len(self.psfs)
 
     @property
     def voxels(self) -> int:
