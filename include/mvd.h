@@ -102,11 +102,13 @@ typedef enum { MVD_PRECISE = 0, MVD_FAST = 1, MVD_MIXED = 2 } mvd_precision;
  *     past a face back onto the reflected voxel, and the update divides by
  *     the folded sensitivity (1 wherever P_v^comp is symmetric under the
  *     face's reflection).
- *   Far from the faces both updates are the periodic one. Estimates and
- *   results keep the X*Y*Z layout. The sequential update only:
- *   mvd_iterate_combined, view weights, regularisation, the unrolled
- *   (differentiable) form and the persistent batch kernel return
- *   MVD_ERR_UNSUPPORTED on a context with a zero or mirror boundary. */
+ *   Far from the faces both updates are the periodic one. Estimates,
+ *   results and view weights keep the X*Y*Z layout. View weights and
+ *   regularisation compose with the sensitivity-normalised factor as in the
+ *   periodic update (factor (c_v / s_v) / (1 + lambda psi), fraction w_v of
+ *   the change), and mvd_iterate_combined multiplies the factors c_v / s_v.
+ *   The unrolled (differentiable) form and the persistent batch kernel
+ *   return MVD_ERR_UNSUPPORTED on a context with a zero or mirror boundary. */
 typedef enum { MVD_BOUNDARY_PERIODIC = 0, MVD_BOUNDARY_ZERO = 1, MVD_BOUNDARY_MIRROR = 2 } mvd_boundary;
 
 typedef struct {
@@ -205,9 +207,11 @@ mvd_status mvd_iterate(mvd_ctx* ctx, int n_iter, const int* schedule, int schedu
  * counting at each voxel covered by some view the views with w_v > 0.
  * From then on every view update of mvd_iterate applies the fraction w_v of
  * the change of the Richardson-Lucy step: psi = max(psi (1 + w_v (c_v - 1)), eps).
- * weights == NULL removes them. The combined update, the unrolled
- * differentiation and the persistent batch kernel return MVD_ERR_UNSUPPORTED
- * for a context with weights. Synchronises the stream.
+ * weights == NULL removes them. With a zero or mirror boundary the images
+ * are in the user's X*Y*Z layout and weigh the sensitivity-normalised
+ * factor (mvd_boundary). The combined update, the unrolled differentiation
+ * and the persistent batch kernel return MVD_ERR_UNSUPPORTED for a context
+ * with weights. Synchronises the stream.
  * mvd_get_weights copies view v's normalised weights (X*Y*Z floats) to host.
  */
 /*
@@ -241,7 +245,11 @@ mvd_status mvd_get_weights(mvd_ctx* ctx, int v, float* out, size_t n_elems);
  *   psi = max(psi . prod_v c_v, eps)               (root == 0, Eq. 50 as printed)
  *   psi = max(psi . (prod_v c_v)^(1/N), eps)       (root != 0, the geometric
  *        mean of the factors, as in the paper's convergence proof).
- * Needs one more volume on the device (the product, allocated on first use).
+ * With a zero or mirror boundary each factor is c_v / s_v (s_v the view's
+ * sensitivity, see mvd_boundary). View weights or lambda > 0 return
+ * MVD_ERR_UNSUPPORTED (they belong to the sequential update).
+ * Needs one more volume on the device (the product, allocated on first use;
+ * with the mirror boundary a second one for the back-projection).
  * Enqueues work only; graph capture as in mvd_iterate.
  */
 mvd_status mvd_iterate_combined(mvd_ctx* ctx, int n_iter, int root);

@@ -22,6 +22,7 @@
 // periodic case.
 #include "common.cuh"
 #include "dd.cuh"
+#include "fft.cuh"
 
 namespace mvd {
 
@@ -138,20 +139,35 @@ __device__ __forceinline__ float fold(const Geo& g, const Images& m, const float
     return s;
 }
 
-// psi = max(psi . fold(cp + off) . inv_s, eps) for every user voxel, written to
-// the voxel and to its reflections in the halo (each halo position has one
-// source voxel, so no two threads write the same address)
-__global__ void k_mirror_update(float* psi, const float* cp, float off, const float* inv_s, float eps, Geo g) {
+// psi = max(psi . F, eps) for every user voxel, F the folded back-projection
+// f = fold(cp + off) . inv_s composed with the view weight w and Tikhonov
+// lambda as in the periodic update (1 + w (f - 1 - lambda psi) / (1 + lambda
+// psi)), written to the voxel and to its reflections in the halo (each halo
+// position has one source voxel, so no two threads write the same address)
+__global__ void k_mirror_update(float* psi, const float* cp, float off, const float* inv_s, float eps, Geo g,
+                                const float* wt, float lam) {
     const long n = (long)g.X0 * g.Y0 * g.Z0;
     for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
         const int x = (int)(u % g.X0), y = (int)((u / g.X0) % g.Y0), z = (int)(u / ((long)g.X0 * g.Y0));
         const Images m = images_of(g, x, y, z);
         const long i = (long)x + (long)g.X * (y + (long)g.Y * z);
-        const float v = fmaxf(psi[i] * fold(g, m, cp, off) * __ldg(inv_s + i), eps);
+        const float p = psi[i];
+        const float f = update_factor(fold(g, m, cp, off) * __ldg(inv_s + i) - 1.f, p, wt, i, lam);
+        const float v = fmaxf(p * f, eps);
         for (int c = 0; c < m.nz; ++c)
             for (int b = 0; b < m.ny; ++b)
                 for (int a = 0; a < m.nx; ++a)
                     psi[(long)m.px[a] + (long)g.X * (m.py[b] + (long)g.Y * m.pz[c])] = v;
+    }
+}
+
+// combined update: prod *= fold(cp + off) . inv_s at every user voxel
+__global__ void k_mirror_accumulate(float* prod, const float* cp, float off, const float* inv_s, Geo g) {
+    const long n = (long)g.X0 * g.Y0 * g.Z0;
+    for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < n; u += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(u % g.X0), y = (int)((u / g.X0) % g.Y0), z = (int)(u / ((long)g.X0 * g.Y0));
+        const long i = (long)x + (long)g.X * (y + (long)g.Y * z);
+        prod[i] *= fold(g, images_of(g, x, y, z), cp, off) * __ldg(inv_s + i);
     }
 }
 
@@ -196,9 +212,16 @@ mvd_status mirror_fill(const mvd_ctx* c, float* padded, cudaStream_t st) {
     return launched("mirror fill");
 }
 
-mvd_status mirror_update(const mvd_ctx* c, const float* cp, float off, const float* inv_s, cudaStream_t st) {
-    k_mirror_update<<<grid_for(c->uM), kThreads, 0, st>>>(c->d_psi, cp, off, inv_s, c->eps, geo_of(c));
+mvd_status mirror_update(const mvd_ctx* c, const float* cp, float off, const float* inv_s, cudaStream_t st,
+                         const float* wt, float lam) {
+    k_mirror_update<<<grid_for(c->uM), kThreads, 0, st>>>(c->d_psi, cp, off, inv_s, c->eps, geo_of(c), wt, lam);
     return launched("mirror update");
+}
+
+mvd_status mirror_accumulate(const mvd_ctx* c, const float* cp, float off, const float* inv_s, float* prod,
+                             cudaStream_t st) {
+    k_mirror_accumulate<<<grid_for(c->uM), kThreads, 0, st>>>(prod, cp, off, inv_s, geo_of(c));
+    return launched("mirror accumulate");
 }
 
 mvd_status finish_padding(const mvd_ctx* c, float* padded, cudaStream_t st) {

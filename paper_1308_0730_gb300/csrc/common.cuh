@@ -188,7 +188,11 @@ mvd_status clear_padding(const mvd_ctx* c, float* padded, cudaStream_t st);
 mvd_status mirror_fill(const mvd_ctx* c, float* padded, cudaStream_t st);
 // mirror: psi = max(psi . fold(cp + off) . inv_s, eps) inside, reflection refreshed;
 // cp is the back-projection on the padded grid (minus off)
-mvd_status mirror_update(const mvd_ctx* c, const float* cp, float off, const float* inv_s, cudaStream_t st);
+mvd_status mirror_update(const mvd_ctx* c, const float* cp, float off, const float* inv_s, cudaStream_t st,
+                         const float* wt = nullptr, float lam = 0.f);
+// combined update with the mirror boundary: prod *= fold(cp + off) / s_v on the user's voxels
+mvd_status mirror_accumulate(const mvd_ctx* c, const float* cp, float off, const float* inv_s, float* prod,
+                             cudaStream_t st);
 // the estimate's padding after it was written inside: zeroed or reflected
 mvd_status finish_padding(const mvd_ctx* c, float* padded, cudaStream_t st);
 mvd_status compute_inverse_sensitivity(mvd_ctx* c);
@@ -276,6 +280,7 @@ struct mvd_ctx {
     long uM = 0;
     float* d_invs = nullptr;  // 1 / sensitivity per view (nv padded volumes)
     float* d_stage = nullptr; // user-layout staging volume (uM)
+    float* d_bp = nullptr;    // mirror boundary, combined update: the back-projection (d_prod holds the product)
     int path = MVD_PATH_AUTO;
     float psi0 = 0.f, eps = 0.f;
     bool eps_user = false;  // eps given at create (else 1e-4 psi0 of the current views)

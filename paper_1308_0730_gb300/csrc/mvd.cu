@@ -243,6 +243,7 @@ void free_all(mvd_ctx* c) {
     dev_free(c->d_flag);
     dev_free(c->d_invs);
     dev_free(c->d_stage);
+    dev_free(c->d_bp);
 }
 
 bool smooth235(int n) {
@@ -476,8 +477,10 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
         MVD_TRY(direct_ratio(c->dims, c->d_psi, c->d_psf + c->koff[v], kd, phi, c->eps, c->d_r, c->stream,
                              c->direct_ty));
         if (mirror) {
-            MVD_TRY(direct_conv(c->dims, c->d_r, c->d_comp + c->koff[v], kd, c->d_prod, c->stream));
-            return mirror_update(c, c->d_prod, 0.f, inv_s, c->stream);
+            float* bp = prod ? c->d_bp : c->d_prod;
+            MVD_TRY(direct_conv(c->dims, c->d_r, c->d_comp + c->koff[v], kd, bp, c->stream));
+            if (prod) return mirror_accumulate(c, bp, 0.f, inv_s, prod, c->stream);
+            return mirror_update(c, bp, 0.f, inv_s, c->stream, wt, c->lambda);
         }
         if (prod)
             return direct_accumulate(c->dims, c->d_r, c->d_comp + c->koff[v], kd, prod, c->stream, c->direct_ty,
@@ -523,8 +526,10 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
             MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
             MVD_TRY(dd_y(g, S2, 1, c->stream));
             if (mirror) {
-                MVD_TRY(fft_x_inverse_dd(g, S2, c->d_prod, c->stream));
-                return mirror_update(c, c->d_prod, 1.f, inv_s, c->stream);
+                float* bp = prod ? c->d_bp : c->d_prod;
+                MVD_TRY(fft_x_inverse_dd(g, S2, bp, c->stream));
+                if (prod) return mirror_accumulate(c, bp, 1.f, inv_s, prod, c->stream);
+                return mirror_update(c, bp, 1.f, inv_s, c->stream, wt, c->lambda);
             }
             if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream, inv_s);
             return done(fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
@@ -542,8 +547,10 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
     MVD_TRY(fft_z_mul(g, c->d_S, Kc, c->stream));
     MVD_TRY(fft_y(g, c->d_S, 1, c->stream));
     if (mirror) {
-        MVD_TRY(fft_inverse_real(g, c->d_S, c->d_prod, c->stream));
-        return mirror_update(c, c->d_prod, 1.f, inv_s, c->stream);
+        float* bp = prod ? c->d_bp : c->d_prod;
+        MVD_TRY(fft_inverse_real(g, c->d_S, bp, c->stream));
+        if (prod) return mirror_accumulate(c, bp, 1.f, inv_s, prod, c->stream);
+        return mirror_update(c, bp, 1.f, inv_s, c->stream, wt, c->lambda);
     }
     if (prod) return fft_x_accumulate(g, c->d_S, prod, c->stream, inv_s);
     return done(fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
@@ -1051,10 +1058,6 @@ mvd_status mvd_set_weights(mvd_ctx* c, const float* const* weights, int on_devic
         set_error("mvd_set_weights: context not created");
         return MVD_ERR_STATE;
     }
-    if (weights && c->boundary != MVD_BOUNDARY_PERIODIC) {
-        set_error("mvd_set_weights: view weights need the periodic boundary");
-        return MVD_ERR_UNSUPPORTED;
-    }
     DeviceGuard dg(c->device);
     drop_graphs(c);  // the captured update passes carry the weight pointers
     if (!weights) {
@@ -1078,11 +1081,29 @@ mvd_status mvd_set_weights(mvd_ctx* c, const float* const* weights, int on_devic
     mvd_status st = MVD_OK;
     unsigned long long* stats = nullptr;
     do {
+        const bool padded = c->boundary != MVD_BOUNDARY_PERIODIC;
         for (int v = 0; v < nv && st == MVD_OK; ++v) {
-            const cudaError_t e = cudaMemcpyAsync(w + (size_t)v * M, weights[v], sizeof(float) * M,
-                                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                                  c->stream);
-            if (e != cudaSuccess) st = cuda_status(e, "mvd_set_weights: copy");
+            if (!padded) {
+                const cudaError_t e = cudaMemcpyAsync(w + (size_t)v * M, weights[v], sizeof(float) * M,
+                                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                                      c->stream);
+                if (e != cudaSuccess) st = cuda_status(e, "mvd_set_weights: copy");
+                continue;
+            }
+            // zero / mirror boundary: the user-layout image onto the padded grid, 0 in the
+            // padding (no view covers it, so the overlap counts and the normalisation are
+            // those of the user's volume)
+            const float* src = weights[v];
+            if (!on_device) {
+                const cudaError_t e = cudaMemcpyAsync(c->d_stage, weights[v], sizeof(float) * c->uM,
+                                                      cudaMemcpyHostToDevice, c->stream);
+                if (e != cudaSuccess) {
+                    st = cuda_status(e, "mvd_set_weights: copy");
+                    break;
+                }
+                src = c->d_stage;
+            }
+            st = pad_volume(c, src, w + (size_t)v * M, c->stream);
         }
         if (st != MVD_OK) break;
         int bad = 0;
@@ -1138,10 +1159,6 @@ mvd_status mvd_set_regularization(mvd_ctx* c, float lambda) {
         set_error("mvd_set_regularization: lambda must be finite and >= 0");
         return MVD_ERR_ARG;
     }
-    if (lambda != 0.f && c->boundary != MVD_BOUNDARY_PERIODIC) {
-        set_error("mvd_set_regularization: regularisation needs the periodic boundary");
-        return MVD_ERR_UNSUPPORTED;
-    }
     DeviceGuard dg(c->device);
     drop_graphs(c);  // the captured update passes carry lambda
     c->lambda = lambda;
@@ -1158,13 +1175,19 @@ mvd_status mvd_get_weights(mvd_ctx* c, int v, float* out, size_t n_elems) {
         set_error("mvd_get_weights: no weights set");
         return MVD_ERR_STATE;
     }
-    if (v < 0 || v >= c->nv || n_elems < (size_t)c->M) {
+    const bool padded = c->boundary != MVD_BOUNDARY_PERIODIC;
+    const long n = padded ? c->uM : c->M;
+    if (v < 0 || v >= c->nv || n_elems < (size_t)n) {
         set_error("mvd_get_weights: bad view or buffer size");
         return MVD_ERR_ARG;
     }
     DeviceGuard dg(c->device);
-    MVD_CUDA(cudaMemcpyAsync(out, c->d_w + (size_t)v * c->M, sizeof(float) * c->M, cudaMemcpyDeviceToHost,
-                             c->stream));
+    const float* src = c->d_w + (size_t)v * c->M;
+    if (padded) {
+        MVD_TRY(crop_volume(c, src, c->d_stage, c->stream));
+        src = c->d_stage;
+    }
+    MVD_CUDA(cudaMemcpyAsync(out, src, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
     MVD_CUDA(cudaStreamSynchronize(c->stream));
     return MVD_OK;
 }
@@ -1187,19 +1210,24 @@ mvd_status mvd_iterate_combined(mvd_ctx* c, int n_iter, int root) {
         set_error("mvd_iterate_combined: n_iter < 0");
         return MVD_ERR_ARG;
     }
-    if (c->d_w || c->lambda != 0.f || c->boundary != MVD_BOUNDARY_PERIODIC) {
-        set_error("mvd_iterate_combined: view weights, regularisation and the zero boundary apply to the "
-                  "sequential update only");
+    if (c->d_w || c->lambda != 0.f) {
+        set_error("mvd_iterate_combined: view weights and regularisation apply to the sequential update only");
         return MVD_ERR_UNSUPPORTED;
     }
     DeviceGuard dg(c->device);
     if (!c->d_prod) MVD_TRY(dev_alloc(&c->d_prod, (size_t)c->M, "combined-update product"));
+    if (c->boundary == MVD_BOUNDARY_MIRROR && !c->d_bp)
+        MVD_TRY(dev_alloc(&c->d_bp, (size_t)c->M, "back-projection"));
     const float e = root ? (float)(1.0 / (double)c->nv) : 1.f;
-    // graph key: schedule entries are >= 0, so {-1} and {-2} name the two combined forms
+    // graph key: schedule entries are >= 0, so {-1} and {-2} name the two combined forms.
+    // Zero / mirror boundary: every factor is c_v / s_v (the accumulate passes divide
+    // by the sensitivity); afterwards the padding is cleared, or the halo refilled with
+    // the estimate's reflection for the next forward blurs.
     return run_iterations(c, {root ? -2 : -1}, n_iter, [&]() -> mvd_status {
         MVD_TRY(fill(c->d_prod, c->M, 1.f, c->stream));
         for (int v = 0; v < c->nv; ++v) MVD_TRY(view_pass(c, v, c->d_prod));
-        return apply_product(c->d_psi, c->d_prod, c->M, e, c->eps, c->stream);
+        MVD_TRY(apply_product(c->d_psi, c->d_prod, c->M, e, c->eps, c->stream));
+        return finish_padding(c, c->d_psi, c->stream);
     });
 }
 
