@@ -428,6 +428,20 @@ def _batched_record(args, mvd, stream):
     stream.synchronize()
     plain_ms = _events_ms(stream, plain, K) / K
     plain_res = [d.result() for d in ds]
+    # each volume alone (its own per-iteration graph): where the plain time goes
+    per_volume = []
+    for w, d in zip(ws, ds):
+        d.set_estimate(None)
+
+        def one(d=d):
+            d.iterate(n_iter)
+
+        ms1 = _events_ms(stream, one, 1)
+        per_volume.append({"volume": w.name, "voxels": w.voxels, "views": w.n_views, "ms": ms1,
+                           "value": w.voxels * w.n_views * n_iter / (ms1 * 1e-3) / 1e9})
+    small = [p for p in per_volume if p["voxels"] < 1_000_000]
+    small_ms = sum(p["ms"] for p in small)
+    tot_ms = sum(p["ms"] for p in per_volume)
     out = {}
     for mode in ("branches", "persistent"):
         b = mvd.mvd_batch_create(ds, n_iter, mode)
@@ -458,7 +472,10 @@ def _batched_record(args, mvd, stream):
             "voxels": int(sum(w.voxels for w in ws)), "voxel_view_updates": int(units), "steps": K, "warmup": 3,
             "plain_ms": plain_ms, "plain_value": units / (plain_ms * 1e-3) / 1e9,
             "batched_ms": out[best]["ms"], "value": out[best]["value"], "mode": best,
-            "ratio": out[best]["ratio"], "modes": out, "generation_s": gen_s}
+            "ratio": out[best]["ratio"], "modes": out, "generation_s": gen_s,
+            "per_volume": per_volume,
+            "volumes_below_1M_voxels": {"count": len(small), "ms": small_ms, "share_of_plain": small_ms / tot_ms,
+                                        "ratio_ceiling_if_free": tot_ms / (tot_ms - small_ms)}}
 
 
 def run_gpu(args):

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kGenThreads, kDdGenBlocks) k_dd_z(DdZ a) {
 
 // register-resident double-float passes (power-of-two lengths)
 template <int L, int S, int IO = 0>
-__global__ void __launch_bounds__(kDdThreads) k_ddf_y(cdd* S2, long nlines, const cdd* tw2, float2* S1) {
+__global__ void __launch_bounds__(kDdThreads, 4) k_ddf_y(cdd* S2, long nlines, const cdd* tw2, float2* S1) {
     extern __shared__ cdd smd[];
     ddf_y_tile<L, S, false, IO>(S2, nlines, tw2, blockIdx.x, smd, S1);
 }
@@ -48,6 +48,13 @@ __global__ void __launch_bounds__(512) k_ddf_z(cdd* S2, const cdd* K2, int Y, lo
                                                const cdd* tw2) {
     extern __shared__ cdd smd[];
     ddf_z_tile<L, MUL, false>(S2, K2, Y, YZ, ntiles_y, scale, tw2, blockIdx.x, smd);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kDdThreads, 3) k_ddf_z2(cdd* S2, const cdd* K2, int Y, long YZ, int ntiles_y,
+                                                         const cdd* tw2) {
+    extern __shared__ cdd smd[];
+    ddf_z2_tile<L, false>(S2, K2, Y, YZ, ntiles_y, tw2, blockIdx.x, smd);
 }
 
 template <int L>
@@ -237,6 +244,19 @@ static mvd_status ddf_z(const FftGeom& g, cdd* S2, const cdd* K2, dd scale, bool
 }
 
 mvd_status dd_z_mul(const FftGeom& g, cdd* S2, const cdd* K2, cudaStream_t st) {
+    if (g.fast && ddf_z2_length(g.Z)) {
+        mvd_status rc = MVD_ERR_UNSUPPORTED;
+        with_dd_len(g.Z, [&](auto Lc) {
+            constexpr int L = decltype(Lc)::value;
+            if constexpr (ddf_z2_length(L)) {
+                constexpr int Q = ddf_z_cols(L);
+                const int nty = (int)gen_div_up(g.Y, Q);
+                rc = launch_raw(k_ddf_z2<L>, (long)g.Xh * nty, Q * (L / kE8), ddf_z2_smem(L), st, "dd z", KC_DD_Z_MUL,
+                                S2, K2, g.Y, g.YZ, nty, g.tw2z);
+            }
+        });
+        return rc;
+    }
     if (g.fast && dd_fast_length(g.Z)) return ddf_z(g, S2, K2, dd{1.f, 0.f}, true, st);
     DdZ a = dd_z_args(g.Z, g.Y, g.YZ, g.pz, g.tw2z, S2, K2, dd{1.f, 0.f});
     return launch(k_dd_z<true>, a, dd_z_tiles(g.Z, g.Y, g.Xh), dd_z_smem(g.Z, g.Y), st, "dd z", KC_DD_Z_MUL);

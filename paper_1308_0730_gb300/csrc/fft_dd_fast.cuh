@@ -35,20 +35,33 @@ __host__ __device__ constexpr bool dd_fast_length(int L) { return L >= 32 && L <
 __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 __host__ __device__ constexpr int line_stride8(int L) { return L + L / 8 + 1; }
 
-template <int L, int S, bool WARP_LOCAL>
+// DB > 0: the exchanges alternate between the line's buffer at sm and a second
+// one at sm + DB (cdd elements), so a stage may write while slower threads of
+// the line still read the previous stage's buffer: one barrier per exchange
+// instead of two.
+// TWS: the twiddle table is a copy in shared memory at padded index pad8(m)
+// (the z tile: its Q columns share every twiddle, so a warp's reads are
+// broadcasts of few distinct words); else the global table, read-only path.
+template <int L, int S, bool WARP_LOCAL, int DB = 0, bool TWS = false>
 struct LineFFTDD {
     static constexpr int TPL = L / kE8;
     static constexpr int NST = plan8_nst(L);
 
-    __device__ __forceinline__ static void sync() {
-        if (WARP_LOCAL && TPL <= 32)
+    // WARP_LOCAL: the TPL threads of a line are contiguous, so a line longer
+    // than a warp synchronises on its own named barrier (id bar, TPL threads)
+    // instead of the whole block: the lines of a block then drift apart and
+    // their warps stop queueing on the same pipes at the same time.
+    __device__ __forceinline__ static void sync(int bar) {
+        if constexpr (WARP_LOCAL && TPL <= 32)
             __syncwarp();
+        else if constexpr (WARP_LOCAL)
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(TPL) : "memory");
         else
             __syncthreads();
     }
 
     template <int ST, int NS>
-    __device__ __forceinline__ static void stage(cdd (&v)[kE8], cdd* sm, int t, const cdd* __restrict__ tw) {
+    __device__ __forceinline__ static void stage(cdd (&v)[kE8], cdd* sm, int t, const cdd* __restrict__ tw, int bar) {
         if constexpr (ST < NST) {
             constexpr int R = plan8_radix(L, ST);
             constexpr int B = kE8 / R;
@@ -63,7 +76,16 @@ struct LineFFTDD {
                 if (NS > 1) {
                     const int step = k * (L / (NS * R));
 #pragma unroll
-                    for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle_dd<S>(tw, r * step));
+                    for (int r = 1; r < R; ++r) {
+                        cdd w;
+                        if constexpr (TWS) {
+                            w = cdd_load(tw + pad8(r * step));
+                            if (S > 0) w.im = dd{-w.im.hi, -w.im.lo};
+                        } else {
+                            w = twiddle_dd<S>(tw, r * step);
+                        }
+                        x[r] = cmul(x[r], w);
+                    }
                 }
                 DftDD<R, S>::run(x);
                 if (LAST) {
@@ -71,22 +93,26 @@ struct LineFFTDD {
                     for (int r = 0; r < R; ++r) v[m + r * B] = x[r];
                 } else {
                     const int d = (j / NS) * NS * R + k;
+                    cdd* buf = sm + ((DB > 0 && (ST & 1)) ? DB : 0);
 #pragma unroll
-                    for (int r = 0; r < R; ++r) cdd_store(sm + pad8(d + r * NS), x[r]);
+                    for (int r = 0; r < R; ++r) cdd_store(buf + pad8(d + r * NS), x[r]);
                 }
             }
             if constexpr (!LAST) {
-                sync();
+                const cdd* buf = sm + ((DB > 0 && (ST & 1)) ? DB : 0);
+                sync(bar);
 #pragma unroll
-                for (int q = 0; q < kE8; ++q) v[q] = cdd_load(sm + pad8(t + TPL * q));
-                sync();
-                stage<ST + 1, NS * R>(v, sm, t, tw);
+                for (int q = 0; q < kE8; ++q) v[q] = cdd_load(buf + pad8(t + TPL * q));
+                if constexpr (DB == 0) sync(bar);
+                stage<ST + 1, NS * R>(v, sm, t, tw, bar);
             }
         }
     }
 
-    __device__ __forceinline__ static void run(cdd (&v)[kE8], cdd* sm, int t, const cdd* __restrict__ tw) {
-        stage<0, 1>(v, sm, t, tw);
+    // bar: the line's named barrier (1 + its index in the block) when WARP_LOCAL
+    __device__ __forceinline__ static void run(cdd (&v)[kE8], cdd* sm, int t, const cdd* __restrict__ tw,
+                                               int bar = 1) {
+        stage<0, 1>(v, sm, t, tw, bar);
     }
 };
 
@@ -99,15 +125,22 @@ struct LineFFT8F {
     static constexpr int TPL = L / kE8;
     static constexpr int NST = plan8_nst(L);
 
-    __device__ __forceinline__ static void sync() {
-        if (WARP_LOCAL && TPL <= 32)
+    // WARP_LOCAL: the TPL threads of a line are contiguous, so a line longer
+    // than a warp synchronises on its own named barrier (id bar, TPL threads)
+    // instead of the whole block: the lines of a block then drift apart and
+    // their warps stop queueing on the same pipes at the same time.
+    __device__ __forceinline__ static void sync(int bar) {
+        if constexpr (WARP_LOCAL && TPL <= 32)
             __syncwarp();
+        else if constexpr (WARP_LOCAL)
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(TPL) : "memory");
         else
             __syncthreads();
     }
 
     template <int ST, int NS>
-    __device__ __forceinline__ static void stage(float2 (&v)[kE8], float2* sm, int t, const float2* __restrict__ tw) {
+    __device__ __forceinline__ static void stage(float2 (&v)[kE8], float2* sm, int t, const float2* __restrict__ tw,
+                                                 int bar) {
         if constexpr (ST < NST) {
             constexpr int R = plan8_radix(L, ST);
             constexpr int B = kE8 / R;
@@ -135,17 +168,18 @@ struct LineFFT8F {
                 }
             }
             if constexpr (!LAST) {
-                sync();
+                sync(bar);
 #pragma unroll
                 for (int q = 0; q < kE8; ++q) v[q] = sm[pad8(t + TPL * q)];
-                sync();
-                stage<ST + 1, NS * R>(v, sm, t, tw);
+                sync(bar);
+                stage<ST + 1, NS * R>(v, sm, t, tw, bar);
             }
         }
     }
 
-    __device__ __forceinline__ static void run(float2 (&v)[kE8], float2* sm, int t, const float2* __restrict__ tw) {
-        stage<0, 1>(v, sm, t, tw);
+    __device__ __forceinline__ static void run(float2 (&v)[kE8], float2* sm, int t, const float2* __restrict__ tw,
+                                               int bar = 1) {
+        stage<0, 1>(v, sm, t, tw, bar);
     }
 };
 
@@ -159,14 +193,26 @@ __host__ __device__ constexpr int ddf_z_cols(int L) {
 __host__ __device__ constexpr int half_stride8(int L) { return L / 2 + L / 16 + 1; }
 // x passes: the 2P gathered half-spectrum rows, or the P transformed lines
 // (the two phases are separated by a barrier and share the buffer)
+// x-pass strides: with two pairs per tile (L = 1024) the gather's 4 rows and
+// the unpacking's 2 lines of a quarter-warp collide on the banks at the
+// strides of one pad slot; + 2 (gathered rows) and + 3 (lines) spread them
+__host__ __device__ constexpr int x_half_stride8(int L) { return L / 2 + L / 16 + (ddf_pairs(L) == 2 ? 2 : 1); }
+__host__ __device__ constexpr int x_line_stride8(int L) { return L + L / 8 + (ddf_pairs(L) == 2 ? 3 : 1); }
 __host__ __device__ constexpr size_t ddf_x_smem(int L) {
-    return (size_t)(2 * ddf_pairs(L) * half_stride8(L) > ddf_pairs(L) * line_stride8(L)
-                        ? 2 * ddf_pairs(L) * half_stride8(L)
-                        : ddf_pairs(L) * line_stride8(L)) *
+    return (size_t)(2 * ddf_pairs(L) * x_half_stride8(L) > ddf_pairs(L) * x_line_stride8(L)
+                        ? 2 * ddf_pairs(L) * x_half_stride8(L)
+                        : ddf_pairs(L) * x_line_stride8(L)) *
            sizeof(cdd);
 }
 __host__ __device__ constexpr size_t ddf_y_smem(int L) { return (size_t)ddf_y_lines(L) * line_stride8(L) * sizeof(cdd); }
-__host__ __device__ constexpr size_t ddf_z_smem(int L) { return (size_t)ddf_z_cols(L) * line_stride8(L) * sizeof(cdd); }
+// z lines: a warp holds Q interleaved columns (q = thread % Q); with Q = 4 a
+// stride of L + L/8 + 1 puts columns q and q + 1 one bank apart, so the
+// exchanges of neighbouring threads collide (two wavefronts per quarter-warp);
+// + 2 spreads them over distinct banks
+__host__ __device__ constexpr int z_line_stride8(int L) { return L + L / 8 + (ddf_z_cols(L) == 4 ? 2 : 1); }
+__host__ __device__ constexpr size_t ddf_z_smem(int L) {
+    return (size_t)2 * ddf_z_cols(L) * z_line_stride8(L) * sizeof(cdd);
+}
 
 // 16-byte asynchronous global -> shared copy (L2 only); with !valid nothing is
 // read and the 16 bytes are zero-filled (src then only needs to be a valid
@@ -216,7 +262,7 @@ __device__ __forceinline__ void ddf_y_tile(cdd* __restrict__ S2, long nlines, co
             v[q] = ok ? ld_cdd<CO>(g + t + TPL * q) : czero_dd();
         }
     }
-    F::run(v, sm + li * line_stride8(L), t, tw2);
+    F::run(v, sm + li * line_stride8(L), t, tw2, 1 + li);
     if (ok) {
 #pragma unroll
         for (int q = 0; q < kE8; ++q) {
@@ -239,16 +285,18 @@ __device__ __forceinline__ void ddf_z_tile(cdd* __restrict__ S2, const cdd* __re
     const int y0 = (int)(tile - (long)kx * ntiles_y) * Q;
     const bool ok = y0 + q < Y;
     const long base = (long)kx * YZ + y0 + q;
-    cdd* line_sm = sm + q * line_stride8(L);
+    cdd* line_sm = sm + q * z_line_stride8(L);
     cdd v[kE8];
 #pragma unroll
     for (int i = 0; i < kE8; ++i) v[i] = ok ? ld_cdd<CO>(S2 + base + (long)(t + TPL * i) * Y) : czero_dd();
-    LineFFTDD<L, -1, false>::run(v, line_sm, t, tw2);
+    using FF = LineFFTDD<L, -1, false, Q * z_line_stride8(L)>;
+    using FI = LineFFTDD<L, +1, false, Q * z_line_stride8(L)>;
+    FF::run(v, line_sm, t, tw2);
     if (MUL) {
 #pragma unroll
         for (int i = 0; i < kE8; ++i) v[i] = cmul(v[i], ok ? cdd_load_nc(K2 + base + (long)(t + TPL * i) * Y) : czero_dd());
         __syncthreads();
-        LineFFTDD<L, +1, false>::run(v, line_sm, t, tw2);
+        FI::run(v, line_sm, t, tw2);
     } else {
 #pragma unroll
         for (int i = 0; i < kE8; ++i) v[i] = cdd{dd_mul(v[i].re, scale), dd_mul(v[i].im, scale)};
@@ -256,6 +304,65 @@ __device__ __forceinline__ void ddf_z_tile(cdd* __restrict__ S2, const cdd* __re
     if (ok) {
 #pragma unroll
         for (int i = 0; i < kE8; ++i) cdd_store(S2 + base + (long)(t + TPL * i) * Y, v[i]);
+    }
+}
+
+// z pass, forward x spectrum x inverse, with the twiddle table copied into
+// shared memory: loaded from the global table, the twiddles of the next
+// stages are hoisted above the stage barriers and held in registers (the tile
+// then needs 128), from shared memory they are not, and the tile runs 3
+// blocks of 256 threads per SM.
+__host__ __device__ constexpr bool ddf_z2_length(int L) { return L >= 128 && L <= 512 && (L & (L - 1)) == 0; }
+__host__ __device__ constexpr int z2_tw_offset(int L) { return ddf_z_cols(L) * z_line_stride8(L); }
+__host__ __device__ constexpr size_t ddf_z2_smem(int L) {
+    return (size_t)(z2_tw_offset(L) + L + L / 8) * sizeof(cdd);
+}
+
+template <int L, bool CO>
+__device__ __forceinline__ void ddf_z2_tile(cdd* __restrict__ S2, const cdd* __restrict__ K2, int Y, long YZ,
+                                            int ntiles_y, const cdd* __restrict__ tw2, long tile, cdd* sm) {
+    constexpr int TPL = L / kE8, Q = ddf_z_cols(L);
+    const int q = threadIdx.x % Q, t = threadIdx.x / Q;
+    const int kx = (int)(tile / ntiles_y);
+    const int y0 = (int)(tile - (long)kx * ntiles_y) * Q;
+    const bool ok = y0 + q < Y;
+    const long off = (long)kx * YZ + y0 + q + (long)t * Y;  // element i at off + i * TPL * Y
+    const long step = (long)TPL * Y;
+    cdd* tws = sm + z2_tw_offset(L);
+    for (int m = threadIdx.x; m < L; m += Q * TPL) cp_async16(tws + pad8(m), tw2 + m, true);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    cdd* line_sm = sm + q * z_line_stride8(L);
+    cdd v[kE8];
+    {
+        const cdd* col = S2 + off;
+#pragma unroll
+        for (int i = 0; i < kE8; ++i) v[i] = ok ? ld_cdd<CO>(col + i * step) : czero_dd();
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    LineFFTDD<L, -1, false, 0, true>::run(v, line_sm, t, tws);
+    // the kernel spectrum, four values in flight at a time (all eight would
+    // add 32 live registers); the column addresses are formed anew here and
+    // at the store, not kept across the transforms
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        long o = off;
+        asm volatile("" : "+l"(o)::"memory");
+        const cdd* kc = K2 + o;
+        cdd kv[kE8 / 2];
+#pragma unroll
+        for (int i = 0; i < kE8 / 2; ++i) kv[i] = ok ? cdd_load_nc(kc + (h * kE8 / 2 + i) * step) : czero_dd();
+#pragma unroll
+        for (int i = 0; i < kE8 / 2; ++i) v[h * kE8 / 2 + i] = cmul(v[h * kE8 / 2 + i], kv[i]);
+    }
+    __syncthreads();
+    LineFFTDD<L, +1, false, 0, true>::run(v, line_sm, t, tws);
+    if (ok) {
+        long o = off;
+        asm volatile("" : "+l"(o));
+        cdd* col = S2 + o;
+#pragma unroll
+        for (int i = 0; i < kE8; ++i) cdd_store(col + i * step, v[i]);
     }
 }
 
@@ -276,7 +383,7 @@ struct DdXFast {
 template <int L>
 __device__ __forceinline__ void ddf_store_halves(const DdXFast& a, cdd (&v)[kE8], cdd* sm, int p, int t, long rho0,
                                                  int nrows) {
-    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L), XH = L / 2 + 1;
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = x_line_stride8(L), XH = L / 2 + 1;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kE8; ++q) cdd_store(sm + p * LS + pad8(t + TPL * q), v[q]);
@@ -300,7 +407,7 @@ __device__ __forceinline__ void ddf_store_halves(const DdXFast& a, cdd (&v)[kE8]
 
 template <int L, bool CO>
 __device__ __forceinline__ void ddf_x_forward_tile(const DdXFast& a, long tile, cdd* sm) {
-    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L);
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = x_line_stride8(L);
     const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
     const long rho0 = tile * 2 * P;
     const int nrows = (int)min((long)2 * P, a.YZ - rho0);
@@ -313,7 +420,7 @@ __device__ __forceinline__ void ddf_x_forward_tile(const DdXFast& a, long tile, 
         const int n = t + TPL * q;
         v[q] = cdd{dd_from(oka ? ld1<CO>(ra + n) : 0.f), dd_from(okb ? ld1<CO>(rb + n) : 0.f)};
     }
-    LineFFTDD<L, -1, true>::run(v, sm + p * LS, t, a.tw2);
+    LineFFTDD<L, -1, true>::run(v, sm + p * LS, t, a.tw2, 1 + p);
     ddf_store_halves<L>(a, v, sm, p, t, rho0, nrows);
 }
 
@@ -322,7 +429,7 @@ __device__ __forceinline__ void ddf_x_forward_tile(const DdXFast& a, long tile, 
 // -> row P + p, at stride HS); every copy is in flight before any completes
 template <int L>
 __device__ __forceinline__ void ddf_gather_issue(const DdXFast& a, long rho0, int nrows, cdd* sm) {
-    constexpr int P = ddf_pairs(L), HS = half_stride8(L), XH = L / 2 + 1;
+    constexpr int P = ddf_pairs(L), HS = x_half_stride8(L), XH = L / 2 + 1;
     for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
         const int k = idx / (2 * P), row = idx - k * 2 * P;
         const bool ok = row < nrows;
@@ -333,7 +440,7 @@ __device__ __forceinline__ void ddf_gather_issue(const DdXFast& a, long rho0, in
 // the full spectrum of the complex line A + iB of pair p from the gathered halves
 template <int L>
 __device__ __forceinline__ void ddf_pair_line(const cdd* sm, int p, int t, cdd (&v)[kE8]) {
-    constexpr int TPL = L / kE8, P = ddf_pairs(L), HS = half_stride8(L);
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), HS = x_half_stride8(L);
 #pragma unroll
     for (int q = 0; q < kE8; ++q) {
         const int k = t + TPL * q;
@@ -358,14 +465,14 @@ __device__ __forceinline__ void ddf_gather_pair(const DdXFast& a, long rho0, int
 // double-float spectrum -> inverse x -> real rows (rounded to FP32) in dst
 template <int L, bool CO>
 __device__ __forceinline__ void ddf_x_inverse_tile(const DdXFast& a, long tile, cdd* sm) {
-    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L);
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = x_line_stride8(L);
     const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
     const long rho0 = tile * 2 * P;
     const int nrows = (int)min((long)2 * P, a.YZ - rho0);
     cdd v[kE8];
     ddf_gather_pair<L, CO>(a, rho0, nrows, p, t, sm, v);
     __syncthreads();
-    LineFFTDD<L, +1, true>::run(v, sm + p * LS, t, a.tw2);
+    LineFFTDD<L, +1, true>::run(v, sm + p * LS, t, a.tw2, 1 + p);
     const long ra = (rho0 + p) * L, rb = (rho0 + P + p) * L;
 #pragma unroll
     for (int q = 0; q < kE8; ++q) {
@@ -387,7 +494,7 @@ __host__ __device__ constexpr size_t ddf_ratio_smem(int L) {
 // register holds them across the inverse transform.
 template <int L, bool CO>
 __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cdd* sm) {
-    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = line_stride8(L), XH = L / 2 + 1;
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = x_line_stride8(L), XH = L / 2 + 1;
     const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
     const long rho0 = tile * 2 * P;
     const int nrows = (int)min((long)2 * P, a.YZ - rho0);
@@ -407,7 +514,7 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
     cdd v[kE8];
     ddf_pair_line<L>(sm, p, t, v);
     __syncthreads();
-    LineFFTDD<L, +1, true>::run(v, sm + p * LS, t, a.tw2);
+    LineFFTDD<L, +1, true>::run(v, sm + p * LS, t, a.tw2, 1 + p);
     // r - 1 of both rows as one complex FP32 line, forward x in registers (the
     // double-float inverse leaves the line in the same distribution; its last
     // shared-memory read was followed by a barrier, so the line's shared
@@ -424,7 +531,7 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
     // each FP32 line lives inside its own line's double-float region (the
     // threads of a line are the only ones touching it until the barrier)
     float2* Fp = reinterpret_cast<float2*>(sm + p * LS);
-    LineFFT8F<L, -1, true>::run(f, Fp, t, a.plan.tw);
+    LineFFT8F<L, -1, true>::run(f, Fp, t, a.plan.tw, 1 + p);
 #pragma unroll
     for (int q = 0; q < kE8; ++q) Fp[pad8(t + TPL * q)] = f[q];
     __syncthreads();

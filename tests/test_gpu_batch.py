@@ -168,3 +168,39 @@ def test_batched_volumes_of_the_48_volume_workload_match_oracle(env, cfg4_subset
     for w, p, q, want in zip(ws, plain, batched, wants):
         assert rel_err(p, want) < PARITY_TOL, f"{w.name} per volume: {err_report(p, want)}"
         assert rel_err(q, want) < PARITY_TOL, f"{w.name} batched: {err_report(q, want)}"
+
+
+@pytest.fixture(scope="module")
+def cfg4_all():
+    """All 48 volumes of the batched workload (every one has its own radix plan triple; 32
+    distinct axis lengths from 48 to 320) and the oracle's FFT leg for each, 15 iterations."""
+    import os
+
+    ws = synth.config4(workers=os.cpu_count() or 1)
+    return ws, [oracle.deconvolve_fft(w.views, w.psfs, w.n_iter)[0] for w in ws]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_all_48_batched_volumes_every_voxel(env, cfg4_all, mode):
+    """The whole 48-volume workload in one batch (15 iterations each), every voxel of every
+    volume against the oracle's FFT leg (pinned to the direct sums in tests/test_oracle_fft.py),
+    tau from each volume's maximum."""
+    torch, mvd = env
+    ws, wants = cfg4_all
+    s = torch.cuda.Stream()
+    ds = [mvd.Deconvolver(w.views, w.psfs, "efficient", path="fft", stream=s) for w in ws]
+    try:
+        b = mvd.mvd_batch_create(ds, ws[0].n_iter, mode)
+        try:
+            mvd.mvd_batch_run(b)
+            mvd.mvd_batch_wait(b)
+        finally:
+            mvd.mvd_batch_destroy(b)
+        got = [d.result() for d in ds]
+    finally:
+        for d in ds:
+            d.close()
+    worst = max((rel_err(g, want), w.name) for w, g, want in zip(ws, got, wants))
+    print(f"48-volume batch ({mode}), worst volume {worst[1]}: {worst[0]:.3e}")
+    for w, g, want in zip(ws, got, wants):
+        assert rel_err(g, want) < PARITY_TOL, f"{w.name}: {err_report(g, want)}"
