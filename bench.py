@@ -60,14 +60,16 @@ CPU_BLOCK = (128, 64, 64)
 def _kernel_bytes(X, Y, Z, precise=True):
     M = X * Y * Z
     spec = 8 * (X // 2 + 1) * Y * Z  # FP32 half spectrum; double-float is 2 * spec
-    if precise:  # the update reads the double-float spectrum
+    if precise:
+        # power-of-two x and y lengths: the ratio pass writes the FP32 spectrum of r - 1 and
+        # the back-projection's forward y reads it (FP32 in, double-float out), so the four y
+        # launches of a view update move 4, 4, 3 and 4 spec, on average 3.75
         return {
             "dd_x_forward": 4 * M + 2 * spec,       # read psi, write S2
-            "dd_y": 4 * spec,                       # read S2, write S2
+            "dd_y": 3.75 * spec,                    # read and write S2 (one launch reads FP32), mean of 4
             "dd_z_mul": 6 * spec,                   # read S2 and a double-float kernel spectrum, write S2
-            "dd_x_ratio": 4 * spec + 4 * M,         # read S2 and phi, write S2
+            "dd_x_ratio": 3 * spec + 4 * M,         # read S2 and phi, write the FP32 spectrum
             "x_update": 2 * spec + 8 * M,           # read S2, read and write psi
-            "dd_x_update_forward": 4 * spec + 8 * M,  # read S2 and psi, write psi and S2
         }
     return {
         "x_forward": 4 * M + spec,          # read psi, write S
@@ -571,6 +573,15 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, f"cuda:{local}")
     assert np.array_equal(out, psi_dev), "end-to-end result differs from the device-resident run"
+    # where an end-to-end step goes (host clock, each part synchronised)
+    parts = {}
+    for name, fn in (("load_views_h2d", lambda: d.set_views(hviews)), ("iterate", lambda: d.iterate(w.n_iter)),
+                     ("result_d2h", lambda: d.result(out))):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        fn()
+        d.synchronize()
+        parts[name] = 1e3 * (time.perf_counter() - t1)
     d.close()
     del hviews, psi_dev
 
@@ -589,7 +600,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "e2e": {"value": _job_value(ws, units_per_step, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": int(view_bytes), "d2h_bytes_per_step": int(out.nbytes),
-                    "steps": e2e_steps,
+                    "steps": e2e_steps, "breakdown_ms": parts,
                     "per_step": "time series with fixed PSFs: load the 7 views from pinned host memory "
                                 "(mvd_set_views), 10 iterations, result to pinned host memory; kernels "
                                 "precomputed once for the series"},

@@ -246,15 +246,27 @@ __device__ void run_tile(const VolDesc& d, int pass, int view, long tile, float2
             }
             break;
         }
-        default: {  // XU (in precise mode from the double-float spectrum)
-            const cdd* S2 = d.precise ? d.S2 : nullptr;
-            if (d.fx) {
-                const XFast a{nullptr, d.S, nullptr, d.psi, d.YZ, d.eps, d.px.tw, S2};
+        default: {  // XU
+            if (d.precise) {  // the double-float x inverse of the double-float spectrum
+                if (d.fx) {
+                    const DdXUpd a{d.S2, d.psi, d.YZ, d.eps, d.tw2x, nullptr, 0.f, nullptr};
+                    with_len(d.X, [&](auto Lc) {
+                        ddf_x_update_tile<decltype(Lc)::value, 1>(a, tile, reinterpret_cast<cdd*>(sm));
+                    });
+                } else {
+                    DdXU u{};
+                    u.x = dd_x_args(d.X, d.YZ, d.px, d.tw2x);
+                    u.x.S2 = d.S2;
+                    u.x.eps = d.eps;
+                    u.psi = d.psi;
+                    dd_x_update_tile<true, 1>(u, tile, reinterpret_cast<cdd*>(sm));
+                }
+            } else if (d.fx) {
+                const XFast a{nullptr, d.S, nullptr, d.psi, d.YZ, d.eps, d.px.tw};
                 with_len(d.X, [&](auto Lc) { fast_x_inverse_tile<decltype(Lc)::value, 1, true>(a, tile, sm); });
             } else {
                 GenX a = gen_x_args(d.X, d.YZ, d.px);
                 a.S = d.S;
-                a.S2in = S2;
                 a.psi = d.psi;
                 a.eps = d.eps;
                 gen_x_inverse_tile<true, 1>(a, tile, sm);
@@ -314,10 +326,11 @@ __global__ void __launch_bounds__(kGenThreads, 2) k_batch(BatchArgs a) {
 
 // tiles of one pass, and elements each tile transforms
 void pass_tiles(const VolDesc& d, int pass, long* ntiles, long* elems) {
-    if (d.precise && pass != XU) {
+    if (d.precise) {  // double-float tiles, the update's x inverse included
         switch (pass) {
             case XF:
             case XR:
+            case XU:
                 if (d.fx) {
                     *ntiles = gen_div_up(d.YZ, 2L * ddf_pairs(d.X));
                     *elems = 2L * ddf_pairs(d.X) * d.X * 4;

@@ -107,24 +107,27 @@ mvd_status fft_x_inverse_dd(const FftGeom& g, const cdd* S2, float* dst, cudaStr
 // combined update: acc *= c, c the back-projected factor of the spectrum of (r - 1) * K (+ 1)
 mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st,
                             const float* inv_s = nullptr);
-mvd_status fft_x_accumulate_dd(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st,
-                               const float* inv_s = nullptr);
-mvd_status fft_x_accumulate_generic(const FftGeom& g, const float2* S, const cdd* S2, float* acc, cudaStream_t st,
+mvd_status fft_x_accumulate_generic(const FftGeom& g, const float2* S, float* acc, cudaStream_t st,
                                     const float* inv_s = nullptr);
 mvd_status fft_x_accumulate_fast(const FftGeom& g, const float2* S, float* acc, cudaStream_t st,
                                  const float* inv_s = nullptr);
-mvd_status fft_x_accumulate_dd_fast(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st,
-                                    const float* inv_s = nullptr);
 
 // double-float forward blur (fft_dd.cu): spectrum of complex double-float
 mvd_status dd_forward_real(const FftGeom& g, const float* src, cdd* S2, cudaStream_t st);
 mvd_status dd_y(const FftGeom& g, cdd* S2, int inverse, cudaStream_t st);
-// register-resident x and y lengths: the back-projection's y passes can take
-// and hand over FP32 spectra (forward y of the FP32 r - 1 spectrum into S2;
-// inverse y of S2 rounded into the FP32 spectrum for the FP32 x inverse)
+// register-resident x and y lengths: the back-projection's forward y pass can
+// take the ratio pass's FP32 spectrum of r - 1 (exact FP32 values) into S2
 bool dd_fast_yx(const FftGeom& g);
 mvd_status dd_y_from_f32(const FftGeom& g, const float2* S1, cdd* S2, cudaStream_t st);
-mvd_status dd_y_inverse_to_f32(const FftGeom& g, cdd* S2, float2* S1, cudaStream_t st);
+// the double-float x inverse of S2 to real rows (rounded to FP32), generic lengths
+mvd_status dd_x_inverse_real_generic(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st);
+// the double-float x inverse of S2 -> the update of psi (accumulate: the combined
+// update's product), any smooth length
+mvd_status dd_x_update(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st, const float* wt,
+                       float lam, const float* inv_s, int accumulate);
+mvd_status dd_x_update_generic(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
+                               const float* wt, float lam, const float* inv_s, int accumulate);
+
 mvd_status dd_z_mul(const FftGeom& g, cdd* S2, const cdd* K2, cudaStream_t st);
 mvd_status dd_z_forward_scaled(const FftGeom& g, cdd* S2, double scale, cudaStream_t st);
 // the inverse x of b (double-float) -> r - 1 -> FP32 forward x, written to the
@@ -134,8 +137,6 @@ mvd_status dd_x_ratio(const FftGeom& g, cdd* S2, const float* phi, float eps, cu
 mvd_status dd_x_inverse_real(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st);
 bool dd_fast_x(const FftGeom& g);
 // update pass reading the double-float spectrum (rounded to FP32)
-mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                           const float* wt = nullptr, float lam = 0.f, const float* inv_s = nullptr);
 
 // register-resident variants for power-of-two lengths (fft_fast.cu)
 bool fft_fast_supported(int L);
@@ -148,8 +149,6 @@ mvd_status fft_x_ratio_fast(const FftGeom& g, float2* S, const float* phi, float
 mvd_status fft_x_update_fast(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
                              const float* wt = nullptr, float lam = 0.f, const float* inv_s = nullptr);
 mvd_status fft_inverse_real_fast(const FftGeom& g, const float2* S, float* dst, cudaStream_t st);
-mvd_status fft_x_update_dd_fast(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                                const float* wt = nullptr, float lam = 0.f, const float* inv_s = nullptr);
 
 // Direct (spatial) periodic convolution with fused epilogues.
 bool direct_supported(const int kd[3]);

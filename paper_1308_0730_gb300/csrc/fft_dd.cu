@@ -24,6 +24,12 @@ __global__ void __launch_bounds__(kGenThreads, kDdGenBlocks) k_dd_x_ratio(DdX a)
     dd_x_ratio_tile<false>(a, blockIdx.x, smd);
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(kGenThreads, kDdGenBlocks) k_dd_x_update(DdXU u) {
+    extern __shared__ cdd smd[];
+    dd_x_update_tile<false, MODE>(u, blockIdx.x, smd);
+}
+
 template <int S>
 __global__ void __launch_bounds__(kGenThreads, kDdGenBlocks) k_dd_y(DdY a) {
     extern __shared__ cdd smd[];
@@ -74,6 +80,15 @@ __global__ void __launch_bounds__(kDdThreads, 4) k_ddf_x_ratio(DdXFast a) {
     extern __shared__ cdd smd[];
     ddf_x_ratio_tile<L, false>(a, blockIdx.x, smd);
 }
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(kDdThreads, 4) k_ddf_x_update(DdXUpd a) {
+    extern __shared__ cdd smd[];
+    ddf_x_update_tile<L, MODE>(a, blockIdx.x, smd);
+}
+
+
+
 
 template <typename F>
 bool with_dd_len(int L, F&& f) {
@@ -215,17 +230,37 @@ mvd_status dd_y_from_f32(const FftGeom& g, const float2* S1, cdd* S2, cudaStream
     return rc;
 }
 
-mvd_status dd_y_inverse_to_f32(const FftGeom& g, cdd* S2, float2* S1, cudaStream_t st) {
-    if (!dd_fast_yx(g)) {
-        set_error("dd y to FP32: needs register-resident x and y lengths, got %d x %d", g.X, g.Y);
-        return MVD_ERR_UNSUPPORTED;
-    }
+mvd_status dd_x_update_generic(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
+                               const float* wt, float lam, const float* inv_s, int accumulate) {
+    DdXU u{};
+    u.x = dd_x_args(g.X, g.YZ, g.px, g.tw2x);
+    u.x.S2 = const_cast<cdd*>(S2);
+    u.x.eps = eps;
+    u.psi = psi;
+    u.wt = wt;
+    u.lam = lam;
+    u.inv_s = inv_s;
+    return launch(accumulate ? k_dd_x_update<4> : k_dd_x_update<1>, u, dd_x_tiles(g.X, g.YZ), dd_x_smem(g.X), st,
+                  "dd x update", KC_X_UPDATE);
+}
+
+mvd_status dd_x_inverse_real_generic(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st) {
+    DdXU u{};
+    u.x = dd_x_args(g.X, g.YZ, g.px, g.tw2x);
+    u.x.S2 = const_cast<cdd*>(S2);
+    u.psi = dst;
+    return launch(k_dd_x_update<0>, u, dd_x_tiles(g.X, g.YZ), dd_x_smem(g.X), st, "dd x inverse", KC_X_UPDATE);
+}
+
+mvd_status dd_x_update(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st, const float* wt,
+                       float lam, const float* inv_s, int accumulate) {
+    if (!dd_fast_x(g)) return dd_x_update_generic(g, S2, psi, eps, st, wt, lam, inv_s, accumulate);
     mvd_status rc = MVD_ERR_UNSUPPORTED;
-    const long nl = (long)g.Xh * g.Z;
-    with_dd_len(g.Y, [&](auto Lc) {
+    DdXUpd a{S2, psi, g.YZ, eps, g.tw2x, wt, lam, inv_s};
+    with_dd_len(g.X, [&](auto Lc) {
         constexpr int L = decltype(Lc)::value;
-        rc = launch_raw(k_ddf_y<L, +1, 2>, gen_div_up(nl, ddf_y_lines(L)), kDdThreads, ddf_y_smem(L), st,
-                        "dd y (FP32 out)", KC_DD_Y, S2, nl, g.tw2y, S1);
+        rc = launch_raw(accumulate ? k_ddf_x_update<L, 4> : k_ddf_x_update<L, 1>, gen_div_up(g.YZ, 2 * ddf_pairs(L)),
+                        kDdThreads, ddf_ratio_smem(L), st, "dd x update", KC_X_UPDATE, a);
     });
     return rc;
 }

@@ -100,6 +100,96 @@ __device__ void dd_x_forward_tile(const DdX& a, long tile, cdd* sm) {
 // r = phi / max(b, eps) -> FP32 forward x -> back into S2 (exact as
 // double-float), where the back-projection's y and z passes continue in
 // double-float
+// the unpacked half spectra of the P transformed complex lines in F (rows
+// p and P + p of the tile) into S2
+__device__ __forceinline__ void dd_x_unpack_store(const DdX& a, const cdd* F, long rho0, int nrows) {
+    const int P2 = 2 * a.P;
+    for (int t = threadIdx.x; t < a.Xh * P2; t += blockDim.x) {
+        const int k = t / P2, row = t - k * P2;
+        if (row >= nrows) continue;
+        const int p = row < a.P ? row : row - a.P;
+        const cdd zk = F[p * a.ls + k];
+        const cdd zm = cconj(F[p * a.ls + (k == 0 ? 0 : a.X - k)]);
+        cdd val;
+        if (row < a.P) {
+            val = chalf(cadd(zk, zm));
+        } else {  // (zk - zm) / (2i)
+            const cdd d = chalf(csub(zk, zm));
+            val = cdd{d.im, dd{-d.re.hi, -d.re.lo}};
+        }
+        cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, val);
+    }
+}
+
+// gather the half spectra of the tile's row pairs from S2 into A (rows < P)
+// and B, then form the full spectrum of each complex line A + iB in A
+template <bool CO>
+__device__ __forceinline__ void dd_x_gather_lines(const DdX& a, cdd* A, cdd* B, long rho0, int nrows) {
+    const int P2 = 2 * a.P;
+    for (int t = threadIdx.x; t < a.Xh * P2; t += blockDim.x) {
+        const int k = t / P2, row = t - k * P2;
+        cdd v = czero_dd();
+        if (row < nrows) v = CO ? cdd_load_cg(a.S2 + (long)k * a.YZ + rho0 + row) : cdd_load(a.S2 + (long)k * a.YZ + rho0 + row);
+        if (row < a.P)
+            A[row * a.ls + k] = v;
+        else
+            B[(row - a.P) * a.ls + k] = v;
+    }
+    __syncthreads();
+    const int half = (a.X + 1) / 2;
+    for (int t = threadIdx.x; t < a.P * a.Xh; t += blockDim.x) {
+        const int p = t / a.Xh, k = t - p * a.Xh;
+        const cdd av = A[p * a.ls + k], bv = B[p * a.ls + k];
+        A[p * a.ls + k] = cdd{dd_sub(av.re, bv.im), dd_add(av.im, bv.re)};
+        if (k >= 1 && k < half) A[p * a.ls + (a.X - k)] = cdd{dd_add(av.re, bv.im), dd_sub(bv.re, av.im)};
+    }
+    __syncthreads();
+}
+
+// The back-projection's last pass in double-float: inverse x of S2, the
+// result (c - 1) rounded to FP32 once, then MODE 1: psi = max(psi .
+// update_factor, eps); MODE 4: acc = acc . c . inv_s (the combined update's
+// product); MODE 0: psi = the rounded result (plain real output).
+struct DdXU {
+    DdX x;
+    float* psi;
+    const float* wt;
+    float lam;
+    const float* inv_s;
+};
+
+template <bool CO, int MODE>
+__device__ void dd_x_update_tile(const DdXU& u, long tile, cdd* sm) {
+    const DdX& a = u.x;
+    cdd* A = sm;
+    cdd* B = sm + a.P * a.ls;
+    const long rho0 = tile * 2 * a.P;
+    const int nrows = (int)min((long)2 * a.P, a.YZ - rho0);
+    dd_x_gather_lines<CO>(a, A, B, rho0, nrows);
+    const cdd* R = fft_lines_dd<+1>(A, B, a.P, a.ls, a.plan, a.tw2);
+    const int n2 = a.P * a.X;
+    for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+        const int p = t / a.X, n = t - p * a.X;
+        const cdd z = R[p * a.ls + n];
+        const float cv[2] = {z.re.hi + z.re.lo, z.im.hi + z.im.lo};  // c - 1 of rows p and P + p
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int row = p + h * a.P;
+            if (row >= nrows) continue;
+            const long i = (rho0 + row) * a.X + n;
+            if (MODE == 0) {
+                u.psi[i] = cv[h];
+                continue;
+            }
+            const float ps = u.psi[i];
+            if (MODE == 1)
+                u.psi[i] = fmaxf(ps * update_factor(cv[h], ps, u.wt, i, u.lam, u.inv_s), a.eps);
+            else
+                u.psi[i] = ps * (cv[h] + 1.f) * (u.inv_s ? __ldg(u.inv_s + i) : 1.f);
+        }
+    }
+}
+
 template <bool CO>
 __device__ void dd_x_ratio_tile(const DdX& a, long tile, cdd* sm) {
     cdd* A = sm;

@@ -234,14 +234,11 @@ __device__ __forceinline__ cdd ld_cdd(const cdd* p) {
         return cdd_load(p);
 }
 
-// IO selects where the lines come from and go to:
+// IO selects where the lines come from:
 //   0: the double-float spectrum S2, in place;
-//   1: read the FP32 spectrum S1 (each value widened exactly), write S2;
-//   2: read S2, write S1 with each value rounded to the nearest FP32 (hi + lo).
+//   1: read the FP32 spectrum S1 (each value widened exactly), write S2.
 // IO 1 takes the ratio pass's FP32 spectrum of r - 1 (exact FP32 values, so
-// nothing is lost against storing them as double-float); IO 2 hands the
-// inverse y transform to the FP32 x inverse of the update, which rounds its
-// input to FP32 in any case. Both halve the bytes of the side in FP32.
+// nothing is lost against storing them as double-float) at half the bytes.
 template <int L, int S, bool CO, int IO = 0>
 __device__ __forceinline__ void ddf_y_tile(cdd* __restrict__ S2, long nlines, const cdd* __restrict__ tw2, long tile,
                                            cdd* sm, float2* __restrict__ S1 = nullptr) {
@@ -265,12 +262,7 @@ __device__ __forceinline__ void ddf_y_tile(cdd* __restrict__ S2, long nlines, co
     F::run(v, sm + li * line_stride8(L), t, tw2, 1 + li);
     if (ok) {
 #pragma unroll
-        for (int q = 0; q < kE8; ++q) {
-            if constexpr (IO == 2)
-                g1[t + TPL * q] = make_float2(v[q].re.hi + v[q].re.lo, v[q].im.hi + v[q].im.lo);
-            else
-                cdd_store(g + t + TPL * q, v[q]);
-        }
+        for (int q = 0; q < kE8; ++q) cdd_store(g + t + TPL * q, v[q]);
     }
 }
 
@@ -553,6 +545,65 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
             a.S[(long)k * a.YZ + rho0 + row] = val;
         else
             cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, cdd{dd_from(val.x), dd_from(val.y)});
+    }
+}
+
+// The back-projection's last pass in precise mode: the double-float half
+// spectra of the tile's rows and the rows' current estimate are staged in
+// shared memory by asynchronous copies, the inverse x transform runs in
+// double-float and gives c - 1, and
+//   MODE 1: psi = max(psi . update_factor(c - 1), eps)   (weights, lambda, 1/s)
+//   MODE 4: acc = acc . c . inv_s                         (combined update)
+// (c - 1 rounded to FP32 once, at the end).
+struct DdXUpd {
+    const cdd* S2;        // double-float half spectrum S2[kx][rho]
+    float* psi;           // estimate (MODE 1) or product (MODE 4), rows of X floats
+    long YZ;
+    float eps;
+    const cdd* tw2;       // double-float twiddles of X
+    const float* wt;      // view weights or none
+    float lam;            // Tikhonov lambda
+    const float* inv_s;   // 1 / sensitivity or none
+};
+
+template <int L, int MODE>
+__device__ __forceinline__ void ddf_x_update_tile(const DdXUpd& a, long tile, cdd* sm) {
+    constexpr int TPL = L / kE8, P = ddf_pairs(L), LS = x_line_stride8(L);
+    const int p = threadIdx.x / TPL, t = threadIdx.x - p * TPL;
+    const long rho0 = tile * 2 * P;
+    const int nrows = (int)min((long)2 * P, a.YZ - rho0);
+    const bool oka = p < nrows, okb = P + p < nrows;
+    float* ps = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + ddf_x_smem(L));  // 2P rows
+    DdXFast g{};
+    g.S2 = const_cast<cdd*>(a.S2);
+    g.YZ = a.YZ;
+    ddf_gather_issue<L>(g, rho0, nrows, sm);
+    {
+        const float* src = a.psi + rho0 * L;
+        for (int c = threadIdx.x; c < 2 * P * L / 4; c += kDdThreads) {
+            const bool ok = c * 4 < nrows * L;
+            cp_async16(ps + 4 * c, ok ? src + 4 * c : a.psi, ok);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    cdd v[kE8];
+    ddf_pair_line<L>(sm, p, t, v);
+    __syncthreads();
+    LineFFTDD<L, +1, true>::run(v, sm + p * LS, t, a.tw2, 1 + p);
+    const long ra = (rho0 + p) * L, rb = (rho0 + P + p) * L;
+#pragma unroll
+    for (int q = 0; q < kE8; ++q) {
+        const int n = t + TPL * q;
+        const float ca = v[q].re.hi + v[q].re.lo, cb = v[q].im.hi + v[q].im.lo;  // c - 1
+        const float pa = ps[p * L + n], pb = ps[(P + p) * L + n];
+        if (MODE == 1) {
+            if (oka) a.psi[ra + n] = fmaxf(pa * update_factor(ca, pa, a.wt, ra + n, a.lam, a.inv_s), a.eps);
+            if (okb) a.psi[rb + n] = fmaxf(pb * update_factor(cb, pb, a.wt, rb + n, a.lam, a.inv_s), a.eps);
+        } else {
+            if (oka) a.psi[ra + n] = pa * (ca + 1.f) * (a.inv_s ? __ldg(a.inv_s + ra + n) : 1.f);
+            if (okb) a.psi[rb + n] = pb * (cb + 1.f) * (a.inv_s ? __ldg(a.inv_s + rb + n) : 1.f);
+        }
     }
 }
 

@@ -127,10 +127,10 @@ mvd_status fft_z_forward_scaled_fast(const FftGeom& g, float2* S, float scale, c
 }
 
 static mvd_status x_fast(const FftGeom& g, int mode, const float* src, float2* S, const float* phi, float* psi,
-                         float eps, cudaStream_t st, const cdd* S2 = nullptr,
-                       const float* wt = nullptr, float lam = 0.f, const float* inv_s = nullptr) {
+                         float eps, cudaStream_t st, const float* wt = nullptr, float lam = 0.f,
+                         const float* inv_s = nullptr) {
     mvd_status rc = MVD_ERR_UNSUPPORTED;
-    XFast a{src, S, phi, psi, g.YZ, eps, g.px.tw, S2, wt, lam, inv_s};
+    XFast a{src, S, phi, psi, g.YZ, eps, g.px.tw, wt, lam, inv_s};
     dispatch_len(g.X, [&](auto Lc) {
         constexpr int L = decltype(Lc)::value;
         constexpr int TPL = L / kE, P = kThreads / TPL;
@@ -175,19 +175,11 @@ mvd_status fft_x_ratio_fast(const FftGeom& g, float2* S, const float* phi, float
 }
 mvd_status fft_x_update_fast(const FftGeom& g, const float2* S, float* psi, float eps, cudaStream_t st,
                              const float* wt, float lam, const float* inv_s) {
-    return x_fast(g, 1, nullptr, const_cast<float2*>(S), nullptr, psi, eps, st, nullptr, wt, lam, inv_s);
-}
-mvd_status fft_x_update_dd_fast(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                                const float* wt, float lam, const float* inv_s) {
-    return x_fast(g, 1, nullptr, nullptr, nullptr, psi, eps, st, S2, wt, lam, inv_s);
+    return x_fast(g, 1, nullptr, const_cast<float2*>(S), nullptr, psi, eps, st, wt, lam, inv_s);
 }
 mvd_status fft_x_accumulate_fast(const FftGeom& g, const float2* S, float* acc, cudaStream_t st,
                                  const float* inv_s) {
-    return x_fast(g, 4, nullptr, const_cast<float2*>(S), nullptr, acc, 0.f, st, nullptr, nullptr, 0.f, inv_s);
-}
-mvd_status fft_x_accumulate_dd_fast(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st,
-                                    const float* inv_s) {
-    return x_fast(g, 4, nullptr, nullptr, nullptr, acc, 0.f, st, S2, nullptr, 0.f, inv_s);
+    return x_fast(g, 4, nullptr, const_cast<float2*>(S), nullptr, acc, 0.f, st, nullptr, 0.f, inv_s);
 }
 mvd_status fft_inverse_real_fast(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
     return x_fast(g, 2, nullptr, const_cast<float2*>(S), nullptr, dst, 0.f, st);

@@ -89,7 +89,6 @@ struct XFast {
     long YZ;
     float eps;
     const float2* tw;
-    const cdd* spec2;  // when set, the update reads this double-float spectrum (rounded to FP32)
     const float* wt;   // when set, the update applies the fraction wt of the change (partial overlap)
     float lam;         // Tikhonov regularisation of the update (0 = none)
     const float* inv_s;  // zero boundary: 1 / sensitivity of the update's view, or none
@@ -141,12 +140,7 @@ __device__ __forceinline__ void x_load_packed(const XFast& a, float2 (&v)[kE], f
         tmp[i] = make_float2(0.f, 0.f);
         if (idx < NTOT && row < nrows) {
             const long at = (long)k * a.YZ + rho0 + row;
-            if (a.spec2) {
-                const cdd z = CO ? cdd_load_cg(a.spec2 + at) : cdd_load(a.spec2 + at);
-                tmp[i] = make_float2(z.re.hi + z.re.lo, z.im.hi + z.im.lo);
-            } else {
-                tmp[i] = ld2<CO>(a.spec + at);
-            }
+            tmp[i] = ld2<CO>(a.spec + at);
         }
     }
 #pragma unroll

@@ -50,7 +50,6 @@ struct GenX {
     const float* phi;  // ratio epilogue
     float* psi;        // update epilogue / real output
     float eps;
-    const cdd* S2in;   // when set, the update reads this double-float spectrum (rounded to FP32)
     const float* wt;   // when set, the update applies the fraction wt of the change (partial overlap)
     float lam;         // Tikhonov regularisation of the update (0 = none)
     const float* inv_s;  // zero boundary: 1 / sensitivity of the update's view, or none
@@ -111,12 +110,7 @@ __device__ __forceinline__ void gen_load_spectrum_pairs(const GenX& a, float2* A
         float2 v = make_float2(0.f, 0.f);
         if (row < nrows) {
             const long at = (long)k * a.YZ + rho0 + row;
-            if (a.S2in) {
-                const cdd z = CO ? cdd_load_cg(a.S2in + at) : cdd_load(a.S2in + at);
-                v = make_float2(z.re.hi + z.re.lo, z.im.hi + z.im.lo);
-            } else {
-                v = ld2<CO>(a.S + at);
-            }
+            v = ld2<CO>(a.S + at);
         }
         if (row < a.P)
             A[row * a.ls + k] = v;

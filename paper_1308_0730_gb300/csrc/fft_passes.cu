@@ -95,23 +95,10 @@ mvd_status fft_x_update_generic(const FftGeom& g, const float2* S, float* psi, f
     return launch(k_x_inverse<1>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
 }
 
-mvd_status fft_x_update_dd_generic(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                                   const float* wt, float lam, const float* inv_s) {
-    GenX a = make_x(g);
-    a.S2in = S2;
-    a.psi = psi;
-    a.eps = eps;
-    a.wt = wt;
-    a.lam = lam;
-    a.inv_s = inv_s;
-    return launch(k_x_inverse<1>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x update", KC_X_UPDATE);
-}
-
-mvd_status fft_x_accumulate_generic(const FftGeom& g, const float2* S, const cdd* S2, float* acc, cudaStream_t st,
+mvd_status fft_x_accumulate_generic(const FftGeom& g, const float2* S, float* acc, cudaStream_t st,
                                     const float* inv_s) {
     GenX a = make_x(g);
     a.S = const_cast<float2*>(S);
-    a.S2in = S2;
     a.psi = acc;
     a.inv_s = inv_s;
     return launch(k_x_inverse<4>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x accumulate", KC_X_UPDATE);
@@ -126,11 +113,7 @@ mvd_status fft_inverse_real_generic(const FftGeom& g, const float2* S, float* ds
 
 mvd_status fft_x_inverse_dd(const FftGeom& g, const cdd* S2, float* dst, cudaStream_t st) {
     if (dd_fast_x(g)) return dd_x_inverse_real(g, S2, dst, st);
-    GenX a = make_x(g);
-    a.S2in = S2;
-    a.psi = dst;
-    return launch(k_x_inverse<0>, a, gen_x_tiles(g.X, g.YZ), gen_x_smem(g.X), st, "fft x inverse (double-float)",
-                  KC_X_UPDATE);
+    return dd_x_inverse_real_generic(g, S2, dst, st);
 }
 
 mvd_status fft_y_generic(const FftGeom& g, float2* S, int inverse, cudaStream_t st) {
@@ -166,18 +149,9 @@ mvd_status fft_x_update(const FftGeom& g, const float2* S, float* psi, float eps
     if (g.fast && fft_fast_supported(g.X)) return fft_x_update_fast(g, S, psi, eps, st, wt, lam, inv_s);
     return fft_x_update_generic(g, S, psi, eps, st, wt, lam, inv_s);
 }
-mvd_status fft_x_update_dd(const FftGeom& g, const cdd* S2, float* psi, float eps, cudaStream_t st,
-                           const float* wt, float lam, const float* inv_s) {
-    if (g.fast && fft_fast_supported(g.X)) return fft_x_update_dd_fast(g, S2, psi, eps, st, wt, lam, inv_s);
-    return fft_x_update_dd_generic(g, S2, psi, eps, st, wt, lam, inv_s);
-}
 mvd_status fft_x_accumulate(const FftGeom& g, const float2* S, float* acc, cudaStream_t st, const float* inv_s) {
     if (g.fast && fft_fast_supported(g.X)) return fft_x_accumulate_fast(g, S, acc, st, inv_s);
-    return fft_x_accumulate_generic(g, S, nullptr, acc, st, inv_s);
-}
-mvd_status fft_x_accumulate_dd(const FftGeom& g, const cdd* S2, float* acc, cudaStream_t st, const float* inv_s) {
-    if (g.fast && fft_fast_supported(g.X)) return fft_x_accumulate_dd_fast(g, S2, acc, st, inv_s);
-    return fft_x_accumulate_generic(g, nullptr, S2, acc, st, inv_s);
+    return fft_x_accumulate_generic(g, S, acc, st, inv_s);
 }
 mvd_status fft_inverse_real(const FftGeom& g, const float2* S, float* dst, cudaStream_t st) {
     if (g.fast && fft_fast_supported(g.X)) return fft_inverse_real_fast(g, S, dst, st);

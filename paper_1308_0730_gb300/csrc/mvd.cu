@@ -503,26 +503,24 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
             // and the back-projection runs in FP32
             MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream, c->d_S));
         } else {
-            // MVD_PRECISE: the FP32 spectrum of r - 1 is stored exactly as
-            // double-float and the back-projection's y and z passes run in
-            // double-float, so no rounding of a large |r - 1| (a count where b
-            // is near eps) spreads over the volume
+            // MVD_PRECISE: the back-projection's y, z and x-inverse passes run
+            // in double-float, so no rounding of a large |r - 1| (a count where
+            // b is near eps) spreads over the volume at FP32 level.
             const cdd* Kc2 = reinterpret_cast<const cdd*>(K4 + ns * (2 * v + 1));
-            if (dd_fast_yx(g) && !mirror) {
-                // the same arithmetic with the FP32 ends of the back-projection
-                // stored as FP32: the ratio pass's r - 1 spectrum (exact FP32
-                // values) and the inverse y output, which the FP32 x inverse of
-                // the update rounds to FP32 anyway (bit-identical results, half
-                // the bytes on those two hand-overs)
+            // The ratio pass hands r - 1 over as an FP32 spectrum when the
+            // forward y pass can widen it (exact FP32 values, half the bytes);
+            // every transform after it runs in double-float, the update's x
+            // inverse included: an FP32 x inverse there carries the rounding
+            // of a line's large values (where b is near eps) into the whole
+            // line and left up to 1.4e-4 after 15 iterations on volumes of
+            // the 48-volume batch (double-float: <= 2.6e-5).
+            if (dd_fast_yx(g)) {
                 MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream, c->d_S));
                 MVD_TRY(dd_y_from_f32(g, c->d_S, S2, c->stream));
-                MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
-                MVD_TRY(dd_y_inverse_to_f32(g, S2, c->d_S, c->stream));
-                if (prod) return fft_x_accumulate(g, c->d_S, prod, c->stream, inv_s);
-                return done(fft_x_update(g, c->d_S, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
+            } else {
+                MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream));
+                MVD_TRY(dd_y(g, S2, 0, c->stream));
             }
-            MVD_TRY(dd_x_ratio(g, S2, phi, c->eps, c->stream));
-            MVD_TRY(dd_y(g, S2, 0, c->stream));
             MVD_TRY(dd_z_mul(g, S2, Kc2, c->stream));
             MVD_TRY(dd_y(g, S2, 1, c->stream));
             if (mirror) {
@@ -531,8 +529,8 @@ mvd_status mvd::view_pass(mvd_ctx* c, int v, float* prod) {
                 if (prod) return mirror_accumulate(c, bp, 1.f, inv_s, prod, c->stream);
                 return mirror_update(c, bp, 1.f, inv_s, c->stream, wt, c->lambda);
             }
-            if (prod) return fft_x_accumulate_dd(g, S2, prod, c->stream, inv_s);
-            return done(fft_x_update_dd(g, S2, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s));
+            if (prod) return dd_x_update(g, S2, prod, 0.f, c->stream, nullptr, 0.f, inv_s, 1);
+            return done(dd_x_update(g, S2, c->d_psi, c->eps, c->stream, wt, c->lambda, inv_s, 0));
         }
     } else {
         const float2* Kp = c->d_K + ns * (2 * v);
