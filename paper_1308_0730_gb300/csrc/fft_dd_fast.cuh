@@ -118,8 +118,10 @@ struct LineFFTDD {
 
 // The same register-resident plan in FP32 (float2 elements, FP32 twiddle
 // table): used for the back-projection's forward x transform of r - 1, whose
-// input the double-float inverse leaves in exactly this distribution. A line
-// uses L/8 + L/64 + 1 float2 of shared memory at stride line_stride8(L).
+// input the double-float inverse leaves in exactly this distribution. Its
+// exchanges pad one slot per 16 float2 (128 bytes; one per 8 would put the
+// 16th element of a half-warp's load on the bank of the first); a line uses
+// L + L/16 + 1 float2 of shared memory, inside the double-float line's region.
 template <int L, int S, bool WARP_LOCAL>
 struct LineFFT8F {
     static constexpr int TPL = L / kE8;
@@ -164,13 +166,13 @@ struct LineFFT8F {
                 } else {
                     const int d = (j / NS) * NS * R + k;
 #pragma unroll
-                    for (int r = 0; r < R; ++r) sm[pad8(d + r * NS)] = x[r];
+                    for (int r = 0; r < R; ++r) sm[pad16(d + r * NS)] = x[r];
                 }
             }
             if constexpr (!LAST) {
                 sync(bar);
 #pragma unroll
-                for (int q = 0; q < kE8; ++q) v[q] = sm[pad8(t + TPL * q)];
+                for (int q = 0; q < kE8; ++q) v[q] = sm[pad16(t + TPL * q)];
                 sync(bar);
                 stage<ST + 1, NS * R>(v, sm, t, tw, bar);
             }
@@ -525,15 +527,15 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
     float2* Fp = reinterpret_cast<float2*>(sm + p * LS);
     LineFFT8F<L, -1, true>::run(f, Fp, t, a.plan.tw, 1 + p);
 #pragma unroll
-    for (int q = 0; q < kE8; ++q) Fp[pad8(t + TPL * q)] = f[q];
+    for (int q = 0; q < kE8; ++q) Fp[pad16(t + TPL * q)] = f[q];
     __syncthreads();
     for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
         const int k = idx / (2 * P), row = idx - k * 2 * P;
         if (row >= nrows) continue;
         const int pp = row < P ? row : row - P;
         const float2* F = reinterpret_cast<const float2*>(sm + pp * LS);
-        const float2 zk = F[pad8(k)];
-        const float2 zm = cconj(F[pad8(k == 0 ? 0 : L - k)]);
+        const float2 zk = F[pad16(k)];
+        const float2 zm = cconj(F[pad16(k == 0 ? 0 : L - k)]);
         float2 val;
         if (row < P) {
             val = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
