@@ -97,6 +97,18 @@ __device__ __forceinline__ void cdd_store(cdd* p, cdd a) {
     *reinterpret_cast<float4*>(p) = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only); with !valid nothing is
+// read and the 16 bytes are zero-filled (src then only needs to be a valid
+// address)
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, bool valid) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // constant (cos, S sin) pairs as double-float: hi = fl32(c), lo = fl32(c - hi)
 #define MVD_DD(c) dd{(float)(c), (float)((c) - (double)(float)(c))}
 

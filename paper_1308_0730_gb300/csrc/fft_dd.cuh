@@ -279,8 +279,18 @@ __device__ void dd_y_tile(const DdY& a, long tile, cdd* sm) {
     cdd* B = sm + a.P * a.ls;
     const long l0 = tile * a.P;
     const int nl = (int)min((long)a.P, a.nlines - l0);
-    if (a.plan.nst >= 2) {  // first stage from global memory, last stage to it
-        fft_lines_dd_io<S, true, true, CO, false>(a.S2 + l0 * a.L, a.L, 1, A, B, a.P, nl, a.ls, a.plan, a.tw2);
+    if (a.plan.nst >= 2) {
+        // the tile's lines staged by asynchronous copies, all in flight at once
+        // (lines past the end zero-filled); the last stage writes global memory
+        const cdd* src = a.S2 + l0 * a.L;
+        for (int t = threadIdx.x; t < a.P * a.L; t += blockDim.x) {
+            const int line = t / a.L, y = t - line * a.L;
+            const bool ok = line < nl;
+            cp_async16(A + line * a.ls + y, ok ? src + (long)line * a.L + y : a.S2, ok);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        fft_lines_dd_io<S, false, true, CO, false>(a.S2 + l0 * a.L, a.L, 1, A, B, a.P, nl, a.ls, a.plan, a.tw2);
         return;
     }
     for (int t = threadIdx.x; t < a.P * a.L; t += blockDim.x) {
@@ -334,7 +344,16 @@ __device__ void dd_z_tile(const DdZ& a, long tile, cdd* sm) {
     const long base = (long)kx * a.YZ + y0;
     const int n = a.Z * a.Q;
     if (MUL && a.plan.nst >= 1) {  // columns: element z of column q at base + z*Y + q; threads run along q
-        cdd* F = fft_lines_dd_io<-1, true, false, CO, true>(a.S2 + base, 1, a.Y, A, B, a.Q, nq, a.ls, a.plan, a.tw2);
+        // the tile's columns staged by asynchronous copies (consecutive copies take
+        // consecutive columns: Q * 16 contiguous bytes per z), all in flight at once
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int z = t / a.Q, q = t - z * a.Q;
+            const bool ok = q < nq;
+            cp_async16(A + q * a.ls + z, ok ? a.S2 + base + (long)z * a.Y + q : a.S2, ok);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        cdd* F = fft_lines_dd_io<-1, false, false, CO, true>(a.S2 + base, 1, a.Y, A, B, a.Q, nq, a.ls, a.plan, a.tw2);
         for (int t = threadIdx.x; t < n; t += blockDim.x) {
             const int z = t / a.Q, q = t - z * a.Q;
             if (q < nq) F[q * a.ls + z] = cmul(F[q * a.ls + z], cdd_load_nc(a.K2 + base + (long)z * a.Y + q));

@@ -216,18 +216,6 @@ __host__ __device__ constexpr size_t ddf_z_smem(int L) {
     return (size_t)2 * ddf_z_cols(L) * z_line_stride8(L) * sizeof(cdd);
 }
 
-// 16-byte asynchronous global -> shared copy (L2 only); with !valid nothing is
-// read and the 16 bytes are zero-filled (src then only needs to be a valid
-// address)
-__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, bool valid) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
-    const int n = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
 template <bool CO>
 __device__ __forceinline__ cdd ld_cdd(const cdd* p) {
     if constexpr (CO)
