@@ -5,6 +5,7 @@
 // padded shared-memory exchanges between stages).
 #pragma once
 
+#include "adf.cuh"
 #include "dd.cuh"
 #include "fft_fast.cuh"
 
@@ -35,6 +36,13 @@ __host__ __device__ constexpr bool dd_fast_length(int L) { return L >= 32 && L <
 __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 __host__ __device__ constexpr int line_stride8(int L) { return L + L / 8 + 1; }
 
+// Arithmetic: aligned double-float (adf.cuh). run() first takes the largest
+// component of the line (a reduction over its threads), puts every value on
+// the grid of that bound's quantum, and each later stage moves to a grid 16
+// times coarser (the growth bound of a radix-8 stage); butterfly sums are then
+// exact FP32 adds, and only the products (twiddles, sqrt(2)/2) are rounded
+// back onto the grid. The result is an unevaluated pair per component (hi on
+// the last stage's grid, lo the remainder).
 // DB > 0: the exchanges alternate between the line's buffer at sm and a second
 // one at sm + DB (cdd elements), so a stage may write while slower threads of
 // the line still read the previous stage's buffer: one barrier per exchange
@@ -42,7 +50,10 @@ __host__ __device__ constexpr int line_stride8(int L) { return L + L / 8 + 1; }
 // TWS: the twiddle table is a copy in shared memory at padded index pad8(m)
 // (the z tile: its Q columns share every twiddle, so a warp's reads are
 // broadcasts of few distinct words); else the global table, read-only path.
-template <int L, int S, bool WARP_LOCAL, int DB = 0, bool TWS = false>
+// QI: with !WARP_LOCAL, the block interleaves QI lines (line = thread % QI).
+// The line-bound reduction keeps its partial maxima in the line buffer's pad
+// slots (cdd index 9k + 8, which no exchange touches).
+template <int L, int S, bool WARP_LOCAL, int DB = 0, bool TWS = false, int QI = 1>
 struct LineFFTDD {
     static constexpr int TPL = L / kE8;
     static constexpr int NST = plan8_nst(L);
@@ -60,12 +71,47 @@ struct LineFFTDD {
             __syncthreads();
     }
 
+    __device__ __forceinline__ static float* red_slot(cdd* sm, int g) {
+        return reinterpret_cast<float*>(sm + 9 * (g >> 2) + 8) + (g & 3);
+    }
+
+    // largest |hi| component over the line's TPL threads
+    __device__ __forceinline__ static float line_bound(const cdd (&v)[kE8], cdd* sm, int t, int bar) {
+        float m = 0.f;
+#pragma unroll
+        for (int q = 0; q < kE8; ++q) m = adf_absmax(v[q], m);
+        if constexpr (WARP_LOCAL) {
+            constexpr int W = TPL < 32 ? TPL : 32;
+#pragma unroll
+            for (int o = 1; o < W; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if constexpr (TPL > 32) {
+                if ((t & 31) == 0) *red_slot(sm, t >> 5) = m;
+                sync(bar);
+#pragma unroll
+                for (int g = 0; g < TPL / 32; ++g) m = fmaxf(m, *red_slot(sm, g));
+            }
+        } else {
+            constexpr int LPW = QI >= 32 ? 1 : 32 / QI;  // a line's lanes in one warp
+            constexpr int G = TPL / LPW;
+            static_assert(G <= 16, "line-bound groups exceed the pad slots");
+#pragma unroll
+            for (int o = QI; o < 32; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (t % LPW == 0) *red_slot(sm, t / LPW) = m;
+            __syncthreads();
+#pragma unroll
+            for (int g = 0; g < G; ++g) m = fmaxf(m, *red_slot(sm, g));
+        }
+        return m;
+    }
+
     template <int ST, int NS>
-    __device__ __forceinline__ static void stage(cdd (&v)[kE8], cdd* sm, int t, const cdd* __restrict__ tw, int bar) {
+    __device__ __forceinline__ static void stage(cdd (&v)[kE8], cdd* sm, int t, const cdd* __restrict__ tw, int bar,
+                                                 int e0) {
         if constexpr (ST < NST) {
             constexpr int R = plan8_radix(L, ST);
             constexpr int B = kE8 / R;
             constexpr bool LAST = (ST == NST - 1);
+            const float c = adf_const_exp2(e0 + 4 * ST);  // every stage before this one is radix 8
 #pragma unroll
             for (int m = 0; m < B; ++m) {
                 cdd x[R];
@@ -75,6 +121,7 @@ struct LineFFTDD {
                 const int k = j % NS;
                 if (NS > 1) {
                     const int step = k * (L / (NS * R));
+                    x[0] = adf_calign(x[0], c);
 #pragma unroll
                     for (int r = 1; r < R; ++r) {
                         cdd w;
@@ -84,10 +131,10 @@ struct LineFFTDD {
                         } else {
                             w = twiddle_dd<S>(tw, r * step);
                         }
-                        x[r] = cmul(x[r], w);
+                        x[r] = adf_cmul(x[r], w, c);
                     }
                 }
-                DftDD<R, S>::run(x);
+                DftA<R, S>::run(x, c);
                 if (LAST) {
 #pragma unroll
                     for (int r = 0; r < R; ++r) v[m + r * B] = x[r];
@@ -104,7 +151,7 @@ struct LineFFTDD {
 #pragma unroll
                 for (int q = 0; q < kE8; ++q) v[q] = cdd_load(buf + pad8(t + TPL * q));
                 if constexpr (DB == 0) sync(bar);
-                stage<ST + 1, NS * R>(v, sm, t, tw, bar);
+                stage<ST + 1, NS * R>(v, sm, t, tw, bar, e0);
             }
         }
     }
@@ -112,7 +159,11 @@ struct LineFFTDD {
     // bar: the line's named barrier (1 + its index in the block) when WARP_LOCAL
     __device__ __forceinline__ static void run(cdd (&v)[kE8], cdd* sm, int t, const cdd* __restrict__ tw,
                                                int bar = 1) {
-        stage<0, 1>(v, sm, t, tw, bar);
+        const int e0 = adf_exp_for(line_bound(v, sm, t, bar));
+        const float c0 = adf_const_exp2(e0);
+#pragma unroll
+        for (int q = 0; q < kE8; ++q) v[q] = adf_calign(v[q], c0);
+        stage<0, 1>(v, sm, t, tw, bar, e0);
     }
 };
 
@@ -271,8 +322,8 @@ __device__ __forceinline__ void ddf_z_tile(cdd* __restrict__ S2, const cdd* __re
     cdd v[kE8];
 #pragma unroll
     for (int i = 0; i < kE8; ++i) v[i] = ok ? ld_cdd<CO>(S2 + base + (long)(t + TPL * i) * Y) : czero_dd();
-    using FF = LineFFTDD<L, -1, false, Q * z_line_stride8(L)>;
-    using FI = LineFFTDD<L, +1, false, Q * z_line_stride8(L)>;
+    using FF = LineFFTDD<L, -1, false, Q * z_line_stride8(L), false, Q>;
+    using FI = LineFFTDD<L, +1, false, Q * z_line_stride8(L), false, Q>;
     FF::run(v, line_sm, t, tw2);
     if (MUL) {
 #pragma unroll
@@ -322,7 +373,7 @@ __device__ __forceinline__ void ddf_z2_tile(cdd* __restrict__ S2, const cdd* __r
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    LineFFTDD<L, -1, false, 0, true>::run(v, line_sm, t, tws);
+    LineFFTDD<L, -1, false, 0, true, Q>::run(v, line_sm, t, tws);
     // the kernel spectrum, four values in flight at a time (all eight would
     // add 32 live registers); the column addresses are formed anew here and
     // at the store, not kept across the transforms
@@ -338,7 +389,7 @@ __device__ __forceinline__ void ddf_z2_tile(cdd* __restrict__ S2, const cdd* __r
         for (int i = 0; i < kE8 / 2; ++i) v[h * kE8 / 2 + i] = cmul(v[h * kE8 / 2 + i], kv[i]);
     }
     __syncthreads();
-    LineFFTDD<L, +1, false, 0, true>::run(v, line_sm, t, tws);
+    LineFFTDD<L, +1, false, 0, true, Q>::run(v, line_sm, t, tws);
     if (ok) {
         long o = off;
         asm volatile("" : "+l"(o));
