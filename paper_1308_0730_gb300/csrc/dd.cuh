@@ -231,159 +231,4 @@ struct DftDD<9, S> {
     __device__ __forceinline__ static void run(cdd* v) { dft9<mvd::DftDD, S>(v); }
 };
 
-// one Stockham butterfly and the multi-line driver, as in fft.cuh
-template <int R, int S>
-__device__ __forceinline__ void stockham_bfly_dd(const cdd* __restrict__ A, cdd* __restrict__ B, int j,
-                                                 const StageIdx& si, const cdd* __restrict__ tw) {
-    const int jq = small_div(j, si.inv_ns);
-    const int k = j - jq * si.Ns;
-    cdd v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = A[j + r * si.nb];
-    if (si.Ns > 1) {
-        const int step = k * si.lstep;
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle_dd<S>(tw, r * step));
-    }
-    DftDD<R, S>::run(v);
-    const int d = jq * si.Ns * R + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) B[d + r * si.Ns] = v[r];
-}
-
-template <int R, int S>
-__device__ __forceinline__ void stockham_stage_dd(const cdd* __restrict__ A, cdd* __restrict__ B, int nlines, int ls,
-                                                  int L, int Ns, const cdd* __restrict__ tw) {
-    const StageIdx si(L, R, Ns);
-    const int total = nlines * si.nb;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int line = small_div(t, si.inv_nb);
-        const int j = t - line * si.nb;
-        stockham_bfly_dd<R, S>(A + line * ls, B + line * ls, j, si, tw);
-    }
-}
-
-// A stage whose input comes straight from global memory (element e of line l
-// at g + l*gls + e*ges; lines >= nl read as zero; L2-only loads when CO)
-// and/or whose output goes straight to global memory (lines >= nl skipped);
-// the other side is the shared-memory line buffer (stride ls). LF maps
-// consecutive threads to consecutive lines (coalesced when gls = 1), else to
-// consecutive butterflies of a line (coalesced when ges = 1).
-template <int R, int S, bool GIN, bool GOUT, bool CO, bool LF>
-__device__ __forceinline__ void stockham_stage_dd_io(const cdd* __restrict__ A, cdd* __restrict__ B, const cdd* gin,
-                                                     cdd* gout, long gls, long ges, int nlines, int nl, int ls, int L,
-                                                     int Ns, const cdd* __restrict__ tw) {
-    const StageIdx si(L, R, Ns);
-    const int total = nlines * si.nb;
-    const float inv_nl = 1.0f / (float)nlines;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        int line, j;
-        if (LF) {
-            j = small_div(t, inv_nl);
-            line = t - j * nlines;
-        } else {
-            line = small_div(t, si.inv_nb);
-            j = t - line * si.nb;
-        }
-        const int jq = small_div(j, si.inv_ns);
-        const int k = j - jq * si.Ns;
-        const bool ok = line < nl;
-        cdd v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (GIN) {
-                const cdd* q = gin + (long)line * gls + (long)(j + r * si.nb) * ges;
-                v[r] = ok ? (CO ? cdd_load_cg(q) : cdd_load(q)) : czero_dd();
-            } else {
-                v[r] = A[line * ls + j + r * si.nb];
-            }
-        }
-        if (si.Ns > 1) {
-            const int step = k * si.lstep;
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle_dd<S>(tw, r * step));
-        }
-        DftDD<R, S>::run(v);
-        const int d = jq * si.Ns * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (GOUT) {
-                if (ok) cdd_store(gout + (long)line * gls + (long)(d + r * si.Ns) * ges, v[r]);
-            } else {
-                B[line * ls + d + r * si.Ns] = v[r];
-            }
-        }
-    }
-}
-
-template <int S, bool GIN, bool GOUT, bool CO, bool LF>
-__device__ __forceinline__ void stage_dd_io(int R, const cdd* A, cdd* B, const cdd* gin, cdd* gout, long gls,
-                                            long ges, int nlines, int nl, int ls, int L, int Ns, const cdd* tw) {
-    switch (R) {
-        case 8: stockham_stage_dd_io<8, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
-        case 4: stockham_stage_dd_io<4, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
-        case 2: stockham_stage_dd_io<2, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
-        case 3: stockham_stage_dd_io<3, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
-        case 6: stockham_stage_dd_io<6, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
-        case 9: stockham_stage_dd_io<9, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
-        default: stockham_stage_dd_io<5, S, GIN, GOUT, CO, LF>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw); break;
-    }
-}
-
-// Transforms nl (<= nlines) lines of length p.L. With GIN the first stage
-// reads them from global memory g (element e of line l at g + l*gls + e*ges),
-// else from the shared-memory buffer A; with GOUT the last stage writes them
-// back to g, else to shared memory. The stages between go through the
-// shared-memory buffers A/B (nlines lines at stride ls). GIN and GOUT together
-// need p.nst >= 2 (one stage would read and write the same global elements).
-// Starts and ends with the block synchronised; returns the shared buffer that
-// holds the result when !GOUT.
-template <int S, bool GIN, bool GOUT, bool CO, bool LF>
-__device__ cdd* fft_lines_dd_io(cdd* g, long gls, long ges, cdd* A, cdd* B, int nlines, int nl, int ls,
-                                const FftPlan& p, const cdd* tw) {
-    int Ns = 1;
-    for (int s = 0; s < p.nst; ++s) {
-        const int R = p.radix[s];
-        const bool first = s == 0, last = s == p.nst - 1;
-        if (GIN && first && GOUT && last)
-            stage_dd_io<S, true, true, CO, LF>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw);
-        else if (GIN && first)
-            stage_dd_io<S, true, false, CO, LF>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw);
-        else if (GOUT && last)
-            stage_dd_io<S, false, true, CO, LF>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw);
-        else
-            stage_dd_io<S, false, false, CO, LF>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw);
-        __syncthreads();
-        cdd* t = A;
-        A = B;
-        B = t;
-        Ns *= R;
-    }
-    return A;
-}
-
-// plan radices as FftPlan, twiddles from a double-float table of length L
-template <int S>
-__device__ cdd* fft_lines_dd(cdd* A, cdd* B, int nlines, int ls, const FftPlan& p, const cdd* tw) {
-    int Ns = 1;
-    for (int s = 0; s < p.nst; ++s) {
-        const int R = p.radix[s];
-        switch (R) {
-            case 8: stockham_stage_dd<8, S>(A, B, nlines, ls, p.L, Ns, tw); break;
-            case 4: stockham_stage_dd<4, S>(A, B, nlines, ls, p.L, Ns, tw); break;
-            case 2: stockham_stage_dd<2, S>(A, B, nlines, ls, p.L, Ns, tw); break;
-            case 3: stockham_stage_dd<3, S>(A, B, nlines, ls, p.L, Ns, tw); break;
-            case 6: stockham_stage_dd<6, S>(A, B, nlines, ls, p.L, Ns, tw); break;
-            case 9: stockham_stage_dd<9, S>(A, B, nlines, ls, p.L, Ns, tw); break;
-            default: stockham_stage_dd<5, S>(A, B, nlines, ls, p.L, Ns, tw); break;
-        }
-        __syncthreads();
-        cdd* t = A;
-        A = B;
-        B = t;
-        Ns *= R;
-    }
-    return A;
-}
-
 }  // namespace mvd

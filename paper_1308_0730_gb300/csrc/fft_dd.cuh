@@ -11,10 +11,225 @@
 // persistent batch kernel).
 #pragma once
 
+#include "adf.cuh"
 #include "dd.cuh"
 #include "fft_generic.cuh"
 
 namespace mvd {
+
+// One Stockham butterfly and the multi-line drivers, as in fft.cuh. The
+// first stage runs in double-float and records the largest component of its
+// outputs; the later stages run in aligned double-float (adf.cuh) on one grid
+// per tile, chosen from that bound (the tile's lines are neighbours in the
+// volume or its spectrum, and the error this leaves is absolute against the
+// tile's largest line, far inside what the convolution needs).
+template <int R, int S, bool ALN>
+__device__ __forceinline__ void dd_bfly_math(cdd (&v)[R], int k, const StageIdx& si, const cdd* __restrict__ tw,
+                                             float c, float& mx) {
+    if constexpr (ALN) {  // a later stage: Ns > 1
+        const int step = k * si.lstep;
+        v[0] = adf_calign(v[0], c);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = adf_cmul(v[r], twiddle_dd<S>(tw, r * step), c);
+        DftA<R, S>::run(v, c);
+    } else {
+        if (si.Ns > 1) {
+            const int step = k * si.lstep;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle_dd<S>(tw, r * step));
+        }
+        DftDD<R, S>::run(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) mx = adf_absmax(v[r], mx);
+    }
+}
+
+template <int R, int S, bool ALN>
+__device__ __forceinline__ void stockham_stage_dd(const cdd* __restrict__ A, cdd* __restrict__ B, int nlines, int ls,
+                                                  int L, int Ns, const cdd* __restrict__ tw, float c, float& mx) {
+    const StageIdx si(L, R, Ns);
+    const int total = nlines * si.nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int line = small_div(t, si.inv_nb);
+        const int j = t - line * si.nb;
+        const int jq = small_div(j, si.inv_ns);
+        const int k = j - jq * si.Ns;
+        const cdd* a = A + line * ls;
+        cdd* b = B + line * ls;
+        cdd v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = a[j + r * si.nb];
+        dd_bfly_math<R, S, ALN>(v, k, si, tw, c, mx);
+        const int d = jq * si.Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) b[d + r * si.Ns] = v[r];
+    }
+}
+
+// A stage whose input comes straight from global memory (element e of line l
+// at g + l*gls + e*ges; lines >= nl read as zero; L2-only loads when CO)
+// and/or whose output goes straight to global memory (lines >= nl skipped);
+// the other side is the shared-memory line buffer (stride ls). LF maps
+// consecutive threads to consecutive lines (coalesced when gls = 1), else to
+// consecutive butterflies of a line (coalesced when ges = 1).
+template <int R, int S, bool GIN, bool GOUT, bool CO, bool LF, bool ALN>
+__device__ __forceinline__ void stockham_stage_dd_io(const cdd* __restrict__ A, cdd* __restrict__ B, const cdd* gin,
+                                                     cdd* gout, long gls, long ges, int nlines, int nl, int ls, int L,
+                                                     int Ns, const cdd* __restrict__ tw, float c, float& mx) {
+    const StageIdx si(L, R, Ns);
+    const int total = nlines * si.nb;
+    const float inv_nl = 1.0f / (float)nlines;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int line, j;
+        if (LF) {
+            j = small_div(t, inv_nl);
+            line = t - j * nlines;
+        } else {
+            line = small_div(t, si.inv_nb);
+            j = t - line * si.nb;
+        }
+        const int jq = small_div(j, si.inv_ns);
+        const int k = j - jq * si.Ns;
+        const bool ok = line < nl;
+        cdd v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (GIN) {
+                const cdd* q = gin + (long)line * gls + (long)(j + r * si.nb) * ges;
+                v[r] = ok ? (CO ? cdd_load_cg(q) : cdd_load(q)) : czero_dd();
+            } else {
+                v[r] = A[line * ls + j + r * si.nb];
+            }
+        }
+        dd_bfly_math<R, S, ALN>(v, k, si, tw, c, mx);
+        const int d = jq * si.Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (GOUT) {
+                if (ok) cdd_store(gout + (long)line * gls + (long)(d + r * si.Ns) * ges, v[r]);
+            } else {
+                B[line * ls + d + r * si.Ns] = v[r];
+            }
+        }
+    }
+}
+
+template <int S, bool GIN, bool GOUT, bool CO, bool LF, bool ALN>
+__device__ __forceinline__ void stage_dd_io(int R, const cdd* A, cdd* B, const cdd* gin, cdd* gout, long gls,
+                                            long ges, int nlines, int nl, int ls, int L, int Ns, const cdd* tw,
+                                            float c, float& mx) {
+#define MVD_DD_IO(RR) \
+    stockham_stage_dd_io<RR, S, GIN, GOUT, CO, LF, ALN>(A, B, gin, gout, gls, ges, nlines, nl, ls, L, Ns, tw, c, mx)
+    switch (R) {
+        case 8: MVD_DD_IO(8); break;
+        case 4: MVD_DD_IO(4); break;
+        case 2: MVD_DD_IO(2); break;
+        case 3: MVD_DD_IO(3); break;
+        case 6: MVD_DD_IO(6); break;
+        case 9: MVD_DD_IO(9); break;
+        default: MVD_DD_IO(5); break;
+    }
+#undef MVD_DD_IO
+}
+
+// the first stage's bound: each warp's largest component into w[warp]
+__device__ __forceinline__ void dd_publish_bound(float mx, float* w) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = mx;
+}
+// grid exponent of stage s >= 1 (e: that of stage s - 1; w: the first stage's
+// warp bounds, read after the barrier that ends it). The first stage's
+// outputs are bounded by m; the twiddle products stay below sqrt(2) m.
+__device__ __forceinline__ int dd_stage_exp(int s, int e, int prev_radix, const float* w) {
+    if (s > 1) return e + adf_gen_shift(prev_radix);
+    float m = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, w[i]);
+    return adf_exp_for<18>(1.5f * m);
+}
+
+// Transforms nl (<= nlines) lines of length p.L. With GIN the first stage
+// reads them from global memory g (element e of line l at g + l*gls + e*ges),
+// else from the shared-memory buffer A; with GOUT the last stage writes them
+// back to g, else to shared memory. The stages between go through the
+// shared-memory buffers A/B (nlines lines at stride ls). GIN and GOUT together
+// need p.nst >= 2 (one stage would read and write the same global elements).
+// Starts and ends with the block synchronised; returns the shared buffer that
+// holds the result when !GOUT.
+template <int S, bool GIN, bool GOUT, bool CO, bool LF>
+__device__ cdd* fft_lines_dd_io(cdd* g, long gls, long ges, cdd* A, cdd* B, int nlines, int nl, int ls,
+                                const FftPlan& p, const cdd* tw) {
+    __shared__ float wmax[32];
+    int Ns = 1, e = 0;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.radix[s];
+        const bool first = s == 0, last = s == p.nst - 1;
+        float mx = 0.f, c = 0.f;
+        if (!first) {
+            e = dd_stage_exp(s, e, p.radix[s > 0 ? s - 1 : 0], wmax);
+            c = adf_const_exp2(e);
+        }
+        if (GIN && first && GOUT && last)
+            stage_dd_io<S, true, true, CO, LF, false>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw, c, mx);
+        else if (GIN && first)
+            stage_dd_io<S, true, false, CO, LF, false>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw, c, mx);
+        else if (first && GOUT && last)
+            stage_dd_io<S, false, true, CO, LF, false>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw, c, mx);
+        else if (first)
+            stage_dd_io<S, false, false, CO, LF, false>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw, c, mx);
+        else if (GOUT && last)
+            stage_dd_io<S, false, true, CO, LF, true>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw, c, mx);
+        else
+            stage_dd_io<S, false, false, CO, LF, true>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw, c, mx);
+        if (first) dd_publish_bound(mx, wmax);
+        __syncthreads();
+        cdd* t = A;
+        A = B;
+        B = t;
+        Ns *= R;
+    }
+    return A;
+}
+
+// plan radices as FftPlan, twiddles from a double-float table of length L
+template <int S>
+__device__ cdd* fft_lines_dd(cdd* A, cdd* B, int nlines, int ls, const FftPlan& p, const cdd* tw) {
+    __shared__ float wmax[32];
+    int Ns = 1, e = 0;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.radix[s];
+        float mx = 0.f, c = 0.f;
+        if (s > 0) {
+            e = dd_stage_exp(s, e, p.radix[s - 1], wmax);
+            c = adf_const_exp2(e);
+        }
+#define MVD_DD_ST(RR)                                                                        \
+    do {                                                                                     \
+        if (s == 0)                                                                          \
+            stockham_stage_dd<RR, S, false>(A, B, nlines, ls, p.L, Ns, tw, c, mx);           \
+        else                                                                                 \
+            stockham_stage_dd<RR, S, true>(A, B, nlines, ls, p.L, Ns, tw, c, mx);            \
+    } while (0)
+        switch (R) {
+            case 8: MVD_DD_ST(8); break;
+            case 4: MVD_DD_ST(4); break;
+            case 2: MVD_DD_ST(2); break;
+            case 3: MVD_DD_ST(3); break;
+            case 6: MVD_DD_ST(6); break;
+            case 9: MVD_DD_ST(9); break;
+            default: MVD_DD_ST(5); break;
+        }
+#undef MVD_DD_ST
+        if (s == 0) dd_publish_bound(mx, wmax);
+        __syncthreads();
+        cdd* t = A;
+        A = B;
+        B = t;
+        Ns *= R;
+    }
+    return A;
+}
+
 
 // half the lines of the FP32 tiles (elements are twice as large)
 __host__ __device__ inline int dd_x_pairs(int X) {
