@@ -64,6 +64,13 @@ __global__ void __launch_bounds__(kDdThreads, 3) k_ddf_z2(cdd* S2, const cdd* K2
 }
 
 template <int L>
+__global__ void __launch_bounds__(kDdThreads, 2) k_ddf_z2_pipe(cdd* S2, const cdd* K2, int Y, long YZ, int ntiles_y,
+                                                              const cdd* tw2, long ntiles) {
+    extern __shared__ cdd smd[];
+    ddf_z2_pipe<L>(S2, K2, Y, YZ, ntiles_y, tw2, ntiles, smd);
+}
+
+template <int L>
 __global__ void __launch_bounds__(kDdThreads) k_ddf_x_forward(DdXFast a) {
     extern __shared__ cdd smd[];
     ddf_x_forward_tile<L, false>(a, blockIdx.x, smd);
@@ -113,6 +120,21 @@ mvd_status launch_raw(K kern, long grid, int threads, size_t smem, cudaStream_t 
     prof_end(cls, st);
     count_launch();
     return check_launch(name);
+}
+
+// blocks of a persistent launch: as many as fit on every SM at once, at most one per tile
+template <typename K>
+long persistent_grid(K kern, int threads, size_t smem, long ntiles) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long g = (long)per_sm * (sms > 0 ? sms : 1);
+    return g < ntiles ? g : ntiles;
 }
 
 DdXFast ddf_args(const FftGeom& g) {
@@ -286,8 +308,10 @@ mvd_status dd_z_mul(const FftGeom& g, cdd* S2, const cdd* K2, cudaStream_t st) {
             if constexpr (ddf_z2_length(L)) {
                 constexpr int Q = ddf_z_cols(L);
                 const int nty = (int)gen_div_up(g.Y, Q);
-                rc = launch_raw(k_ddf_z2<L>, (long)g.Xh * nty, Q * (L / kE8), ddf_z2_smem(L), st, "dd z", KC_DD_Z_MUL,
-                                S2, K2, g.Y, g.YZ, nty, g.tw2z);
+                const long nt = (long)g.Xh * nty;
+                const size_t smem = ddf_z2_pipe_smem(L);
+                rc = launch_raw(k_ddf_z2_pipe<L>, persistent_grid(k_ddf_z2_pipe<L>, Q * (L / kE8), smem, nt),
+                                Q * (L / kE8), smem, st, "dd z", KC_DD_Z_MUL, S2, K2, g.Y, g.YZ, nty, g.tw2z, nt);
             }
         });
         return rc;

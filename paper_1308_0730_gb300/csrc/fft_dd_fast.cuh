@@ -399,6 +399,75 @@ __device__ __forceinline__ void ddf_z2_tile(cdd* __restrict__ S2, const cdd* __r
     }
 }
 
+// The z pass as a persistent, software-pipelined loop: each block walks the
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ... and, while it transforms one
+// tile, the next tile's columns of S2 and of the kernel spectrum are already
+// in flight into shared memory by asynchronous copies. Every thread copies
+// exactly the elements it will itself read (thread-private slots
+// i * 256 + thread), so neither the copies' completion (cp.async.wait_group
+// of its own groups) nor the reuse of the slots needs a barrier. Two blocks
+// per SM (the twiddles, the column lines and both staging areas take 110 KB
+// for L = 512); measured faster than three blocks of the unpipelined tile.
+__host__ __device__ constexpr size_t ddf_z2_pipe_smem(int L) {
+    return ddf_z2_smem(L) + (size_t)2 * kE8 * kDdThreads * sizeof(cdd);
+}
+
+template <int L>
+__device__ __forceinline__ void ddf_z2_pipe(cdd* __restrict__ S2, const cdd* __restrict__ K2, int Y, long YZ,
+                                            int ntiles_y, const cdd* __restrict__ tw2, long ntiles, cdd* sm) {
+    constexpr int TPL = L / kE8, Q = ddf_z_cols(L);
+    const int q = threadIdx.x % Q, t = threadIdx.x / Q;
+    cdd* tws = sm + z2_tw_offset(L);
+    cdd* line_sm = sm + q * z_line_stride8(L);
+    cdd* stS = sm + z2_tw_offset(L) + L + L / 8 + threadIdx.x;  // slot i at stS[i * 256]
+    cdd* stK = stS + kE8 * kDdThreads;
+    const long step = (long)TPL * Y;
+    // element i of this thread's column of tile `tile` sits at col_off(tile) + i * step
+    auto col_off = [&](long tile, bool& ok) {
+        const int kx = (int)(tile / ntiles_y);
+        const int y0 = (int)(tile - (long)kx * ntiles_y) * Q;
+        ok = y0 + q < Y;
+        return (long)kx * YZ + y0 + q + (long)t * Y;
+    };
+    auto issue = [&](cdd* slots, const cdd* src, long tile) {
+        bool ok;
+        const long off = col_off(tile, ok);
+#pragma unroll
+        for (int i = 0; i < kE8; ++i) cp_async16(slots + i * kDdThreads, ok ? src + off + i * step : src, ok);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    for (int m = threadIdx.x; m < L; m += Q * TPL) cp_async16(tws + pad8(m), tw2 + m, true);
+    long tile = blockIdx.x;
+    if (tile < ntiles) {
+        issue(stS, S2, tile);
+        issue(stK, K2, tile);
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();  // the twiddle table is shared
+    for (; tile < ntiles; tile += gridDim.x) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        const long next = tile + gridDim.x;
+        cdd v[kE8];
+#pragma unroll
+        for (int i = 0; i < kE8; ++i) v[i] = stS[i * kDdThreads];
+        if (next < ntiles) issue(stS, S2, next);
+        LineFFTDD<L, -1, false, 0, true, Q>::run(v, line_sm, t, tws);
+#pragma unroll
+        for (int i = 0; i < kE8; ++i) v[i] = cmul(v[i], stK[i * kDdThreads]);
+        if (next < ntiles) issue(stK, K2, next);
+        __syncthreads();
+        LineFFTDD<L, +1, false, 0, true, Q>::run(v, line_sm, t, tws);
+        bool ok;
+        long o = col_off(tile, ok);
+        if (ok) {
+            cdd* col = S2 + o;
+#pragma unroll
+            for (int i = 0; i < kE8; ++i) cdd_store(col + i * step, v[i]);
+        }
+        __syncthreads();  // the next forward transform reuses the column lines
+    }
+}
+
 struct DdXFast {
     const float* src;  // real rows
     cdd* S2;
