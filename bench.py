@@ -168,8 +168,10 @@ WORKLOADS = {
     "specimen-x1024": (1024, 64, 64),
     "specimen-y1024": (64, 1024, 64),
     "specimen-z512": (64, 64, 512),
-    # the specimen's three transform lengths on a slab whose spectra exceed the L2 (per-kernel captures)
+    # slabs with one of the specimen's transform lengths whose spectra exceed the L2 (per-kernel captures)
     "specimen-1024x256x128": (1024, 256, 128),
+    "specimen-256x1024x128": (256, 1024, 128),
+    "specimen-256x128x512": (256, 128, 512),
 }
 
 

@@ -32,6 +32,21 @@ __host__ __device__ constexpr int plan8_radix(int L, int s) {
 __host__ __device__ constexpr int plan8_nst(int L) { return plan8_n(L) + (plan8_rem(L) > 1 ? 1 : 0); }
 __host__ __device__ constexpr bool dd_fast_length(int L) { return L >= 32 && L <= 1024 && (L & (L - 1)) == 0; }
 
+// Twiddles in stage order: the natural table of a length L (w^m, m < L) is
+// followed by the stage-ordered one, where stage s >= 1 (NS points combined
+// before it, radix R) keeps w^(r k L / (NS R)) at tw_stage_off(L, s) +
+// (r - 1) NS + k: a warp's consecutive k read consecutive entries (in natural
+// order they would sit L / (NS R) entries apart).
+__host__ __device__ constexpr int tw_stage_off(int L, int ST) {
+    int off = 0, ns = 1;
+    for (int s = 0; s < ST; ++s) {
+        const int R = plan8_radix(L, s);
+        if (s > 0) off += (R - 1) * ns;
+        ns *= R;
+    }
+    return off;
+}
+
 // padded index: one pad slot per 8 elements; line stride shifts lines across banks
 __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 __host__ __device__ constexpr int line_stride8(int L) { return L + L / 8 + 1; }
@@ -47,9 +62,10 @@ __host__ __device__ constexpr int line_stride8(int L) { return L + L / 8 + 1; }
 // one at sm + DB (cdd elements), so a stage may write while slower threads of
 // the line still read the previous stage's buffer: one barrier per exchange
 // instead of two.
-// TWS: the twiddle table is a copy in shared memory at padded index pad8(m)
-// (the z tile: its Q columns share every twiddle, so a warp's reads are
-// broadcasts of few distinct words); else the global table, read-only path.
+// TWS: the stage-ordered twiddles are a copy in shared memory at padded index
+// pad8(i) (the z tile: its Q columns share every twiddle, so a warp's reads
+// are broadcasts of few distinct words); else tw is the global natural table,
+// followed by the stage-ordered one (read-only path).
 // QI: with !WARP_LOCAL, the block interleaves QI lines (line = thread % QI).
 // The line-bound reduction keeps its partial maxima in the line buffer's pad
 // slots (cdd index 9k + 8, which no exchange touches).
@@ -120,16 +136,16 @@ struct LineFFTDD {
                 const int j = t + TPL * m;
                 const int k = j % NS;
                 if (NS > 1) {
-                    const int step = k * (L / (NS * R));
+                    constexpr int OFF = tw_stage_off(L, ST);
                     x[0] = adf_calign(x[0], c);
 #pragma unroll
                     for (int r = 1; r < R; ++r) {
                         cdd w;
                         if constexpr (TWS) {
-                            w = cdd_load(tw + pad8(r * step));
+                            w = cdd_load(tw + pad8(OFF + (r - 1) * NS + k));
                             if (S > 0) w.im = dd{-w.im.hi, -w.im.lo};
                         } else {
-                            w = twiddle_dd<S>(tw, r * step);
+                            w = twiddle_dd<S>(tw + L, OFF + (r - 1) * NS + k);
                         }
                         x[r] = adf_cmul(x[r], w, c);
                     }
@@ -242,14 +258,16 @@ __host__ __device__ constexpr int ddf_y_lines(int L) { return kDdThreads / (L / 
 __host__ __device__ constexpr int ddf_z_cols(int L) {
     return (kDdThreads / (L / kE8)) >= 4 ? kDdThreads / (L / kE8) : 4;
 }
-// half-spectrum rows (XH = L/2 + 1 padded values) of the x-pass gather
-__host__ __device__ constexpr int half_stride8(int L) { return L / 2 + L / 16 + 1; }
-// x passes: the 2P gathered half-spectrum rows, or the P transformed lines
-// (the two phases are separated by a barrier and share the buffer)
-// x-pass strides: with two pairs per tile (L = 1024) the gather's 4 rows and
-// the unpacking's 2 lines of a quarter-warp collide on the banks at the
-// strides of one pad slot; + 2 (gathered rows) and + 3 (lines) spread them
-__host__ __device__ constexpr int x_half_stride8(int L) { return L / 2 + L / 16 + (ddf_pairs(L) == 2 ? 2 : 1); }
+// half-spectrum rows (XH = L/2 + 1 values) of the x-pass gather, unpadded:
+// the pair line reads them in ascending runs (k <= L/2) and descending runs
+// (L - k), and a padded row would split a quarter-warp's descending run over
+// a pad slot (two wavefronts). The gather's quarter-warp writes 8 rows of one
+// k (odd stride: distinct banks) or, with two pairs, 4 rows of k and k + 1
+// (stride 2 mod 8). The x passes' 2P gathered rows and their P transformed
+// lines share the buffer (the two phases are separated by a barrier). With two
+// pairs per tile (L = 1024) the unpacking's 2 lines of a quarter-warp collide
+// on the banks at a line stride of one pad slot; + 3 spreads them.
+__host__ __device__ constexpr int x_half_stride8(int L) { return L / 2 + 1 + (ddf_pairs(L) == 2 ? 1 : 0); }
 __host__ __device__ constexpr int x_line_stride8(int L) { return L + L / 8 + (ddf_pairs(L) == 2 ? 3 : 1); }
 __host__ __device__ constexpr size_t ddf_x_smem(int L) {
     return (size_t)(2 * ddf_pairs(L) * x_half_stride8(L) > ddf_pairs(L) * x_line_stride8(L)
@@ -362,7 +380,7 @@ __device__ __forceinline__ void ddf_z2_tile(cdd* __restrict__ S2, const cdd* __r
     const long off = (long)kx * YZ + y0 + q + (long)t * Y;  // element i at off + i * TPL * Y
     const long step = (long)TPL * Y;
     cdd* tws = sm + z2_tw_offset(L);
-    for (int m = threadIdx.x; m < L; m += Q * TPL) cp_async16(tws + pad8(m), tw2 + m, true);
+    for (int m = threadIdx.x; m < L; m += Q * TPL) cp_async16(tws + pad8(m), tw2 + L + m, true);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     cdd* line_sm = sm + q * z_line_stride8(L);
     cdd v[kE8];
@@ -436,7 +454,7 @@ __device__ __forceinline__ void ddf_z2_pipe(cdd* __restrict__ S2, const cdd* __r
         for (int i = 0; i < kE8; ++i) cp_async16(slots + i * kDdThreads, ok ? src + off + i * step : src, ok);
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    for (int m = threadIdx.x; m < L; m += Q * TPL) cp_async16(tws + pad8(m), tw2 + m, true);
+    for (int m = threadIdx.x; m < L; m += Q * TPL) cp_async16(tws + pad8(m), tw2 + L + m, true);
     long tile = blockIdx.x;
     if (tile < ntiles) {
         issue(stS, S2, tile);
@@ -535,7 +553,7 @@ __device__ __forceinline__ void ddf_gather_issue(const DdXFast& a, long rho0, in
     for (int idx = threadIdx.x; idx < XH * 2 * P; idx += kDdThreads) {
         const int k = idx / (2 * P), row = idx - k * 2 * P;
         const bool ok = row < nrows;
-        cp_async16(sm + row * HS + pad8(k), ok ? a.S2 + (long)k * a.YZ + rho0 + row : a.S2, ok);
+        cp_async16(sm + row * HS + k, ok ? a.S2 + (long)k * a.YZ + rho0 + row : a.S2, ok);
     }
 }
 
@@ -547,7 +565,7 @@ __device__ __forceinline__ void ddf_pair_line(const cdd* sm, int p, int t, cdd (
     for (int q = 0; q < kE8; ++q) {
         const int k = t + TPL * q;
         const int kk = k <= L / 2 ? k : L - k;
-        const cdd A = cdd_load(sm + p * HS + pad8(kk)), B = cdd_load(sm + (P + p) * HS + pad8(kk));
+        const cdd A = cdd_load(sm + p * HS + kk), B = cdd_load(sm + (P + p) * HS + kk);
         v[q] = k <= L / 2 ? cdd{dd_sub(A.re, B.im), dd_add(A.im, B.re)}    // A + iB
                           : cdd{dd_add(A.re, B.im), dd_sub(B.re, A.im)};   // conj(A) + i conj(B)
     }

@@ -305,24 +305,52 @@ mvd_status setup_fft(mvd_ctx* c) {
     if (c->precise != 1) MVD_TRY(dev_alloc(&c->d_K, ns * (c->precise ? 1 : 2) * c->nv, "kernel spectra"));
     const float inv_m = (float)(1.0 / (double)c->M);
     if (c->precise) {
-        // double-float twiddles: hi = fl32(w), lo = fl32(w - hi), w in FP64
-        std::vector<float4> tw2((size_t)g.X + g.Y + g.Z);
+        // double-float twiddles w^m = exp(-2 pi i m / L): hi = fl32(w), lo =
+        // fl32(w - hi), w in FP64. Per axis the table in natural order (m =
+        // 0..L-1), then, for the register-resident passes of a power-of-two L,
+        // the same values in stage order: stage s >= 1 of the radix-8 plan
+        // (NS points combined before it, radix R) holds w^(r k L / (NS R)) at
+        // (r - 1) NS + k, so that a warp's threads (consecutive k) read
+        // consecutive entries.
+        auto twv = [](long m, int L) {
+            const double ang = -2.0 * M_PI * (double)m / (double)L;
+            const double cr = std::cos(ang), ci = std::sin(ang);
+            const float rh = (float)cr, ih = (float)ci;
+            return make_float4(rh, (float)(cr - rh), ih, (float)(ci - ih));
+        };
+        std::vector<float4> tw2(2 * ((size_t)g.X + g.Y + g.Z), make_float4(0.f, 0.f, 0.f, 0.f));
         size_t o = 0;
         for (int a = 0; a < 3; ++a) {
-            for (int m = 0; m < Ls[a]; ++m) {
-                const double ang = -2.0 * M_PI * (double)m / (double)Ls[a];
-                const double cr = std::cos(ang), ci = std::sin(ang);
-                const float rh = (float)cr, ih = (float)ci;
-                tw2[o + m] = make_float4(rh, (float)(cr - rh), ih, (float)(ci - ih));
+            const int L = Ls[a];
+            for (int m = 0; m < L; ++m) tw2[o + m] = twv(m, L);
+            if (L >= 32 && L <= 1024 && (L & (L - 1)) == 0) {
+                std::vector<int> radix;
+                int rem = L;
+                while (rem % 8 == 0 && rem >= 8) {
+                    radix.push_back(8);
+                    rem /= 8;
+                }
+                if (rem > 1) radix.push_back(rem);
+                int ns = 1, off = 0;
+                for (size_t st = 0; st < radix.size(); ++st) {
+                    const int R = radix[st];
+                    if (st > 0) {
+                        for (int r = 1; r < R; ++r)
+                            for (int k = 0; k < ns; ++k)
+                                tw2[o + L + off + (size_t)(r - 1) * ns + k] = twv((long)r * k * (L / (ns * R)), L);
+                        off += (R - 1) * ns;
+                    }
+                    ns *= R;
+                }
             }
-            o += Ls[a];
+            o += 2 * (size_t)L;
         }
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_tw2), tw2.size(), "double-float twiddle tables"));
         MVD_CUDA(cudaMemcpyAsync(c->d_tw2, tw2.data(), tw2.size() * sizeof(float4), cudaMemcpyHostToDevice,
                                  c->stream));
         g.tw2x = c->d_tw2;
-        g.tw2y = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + g.X);
-        g.tw2z = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + g.X + g.Y);
+        g.tw2y = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + 2 * g.X);
+        g.tw2z = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + 2 * (g.X + g.Y));
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_S2), ns, "double-float work spectrum"));
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_KP2), ns * 2 * c->nv, "double-float kernel spectra"));
     }
