@@ -183,8 +183,9 @@ struct LineFFTDD {
     }
 };
 
-// The same register-resident plan in FP32 (float2 elements, FP32 twiddle
-// table): used for the back-projection's forward x transform of r - 1, whose
+// The same register-resident plan in FP32 (float2 elements; tw is the FP32
+// natural table of L, followed by its radix-8 stage-ordered copy): used for
+// the back-projection's forward x transform of r - 1, whose
 // input the double-float inverse leaves in exactly this distribution. Its
 // exchanges pad one slot per 16 float2 (128 bytes; one per 8 would put the
 // 16th element of a half-warp's load on the bank of the first); a line uses
@@ -222,9 +223,9 @@ struct LineFFT8F {
                 const int j = t + TPL * m;
                 const int k = j % NS;
                 if (NS > 1) {
-                    const int step = k * (L / (NS * R));
+                    constexpr int OFF = tw_stage_off(L, ST);
 #pragma unroll
-                    for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<S>(tw, r * step));
+                    for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<S>(tw + L, OFF + (r - 1) * NS + k));
                 }
                 Dft<R, S>::run(x);
                 if (LAST) {

@@ -76,6 +76,22 @@ __host__ __device__ constexpr bool fast_length(int L) {
     return L >= 16 && L <= 4096 && (L & (L - 1)) == 0;
 }
 
+// Twiddles in stage order: the FP32 natural table of a length L (w^m, m < L)
+// is followed by its radix-8 stage-ordered copy (the 8-point-per-thread
+// lines) and then its radix-16 one (these lines), where stage s >= 1 (NS
+// points combined before it, radix R) keeps w^(r k L / (NS R)) at
+// tw_stage_off16(L, s) + (r - 1) NS + k: a warp's consecutive k read
+// consecutive entries.
+__host__ __device__ constexpr int tw_stage_off16(int L, int ST) {
+    int off = 0, ns = 1;
+    for (int s = 0; s < ST; ++s) {
+        const int R = plan_radix(L, s);
+        if (s > 0) off += (R - 1) * ns;
+        ns *= R;
+    }
+    return off;
+}
+
 // padded shared-memory index of element i of a line: one pad slot per 16
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 // line stride in float2: L + L/16 (+1 to shift lines across banks)
@@ -107,9 +123,9 @@ struct LineFFT {
                 const int j = t + TPL * m;
                 const int k = j % NS;
                 if (NS > 1) {
-                    const int step = k * (L / (NS * R));
+                    constexpr int OFF = tw_stage_off16(L, ST);
 #pragma unroll
-                    for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<S>(tw, r * step));
+                    for (int r = 1; r < R; ++r) x[r] = cmul(x[r], twiddle<S>(tw + 2 * L, OFF + (r - 1) * NS + k));
                 }
                 Dft<R, S>::run(x);
                 if (LAST) {

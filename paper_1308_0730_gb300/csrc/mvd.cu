@@ -44,6 +44,7 @@ mvd_status check_launch(const char* what) {
 // per-kernel event timing
 // ---------------------------------------------------------------------------
 namespace {
+
 struct ProfRec {
     int cls;
     cudaEvent_t a, b;
@@ -179,6 +180,34 @@ using namespace mvd;
 
 namespace {
 
+// Stage order of the twiddles of a register-resident line of power-of-two
+// length L whose stages are radix P (the last one L's remainder): stage
+// s >= 1, with NS points combined before it and radix R, needs w^m for
+// m = r k L / (NS R) (r = 1..R-1, k = 0..NS-1); put(i, m) stores it at
+// i = (earlier stages' entries) + (r - 1) NS + k.
+template <typename F>
+void stage_ordered_twiddles(int L, int P, F&& put) {
+    std::vector<int> radix;
+    int rem = L;
+    while (rem % P == 0 && rem >= P) {
+        radix.push_back(P);
+        rem /= P;
+    }
+    if (rem > 1) radix.push_back(rem);
+    int ns = 1;
+    size_t off = 0;
+    for (size_t st = 0; st < radix.size(); ++st) {
+        const int R = radix[st];
+        if (st > 0) {
+            for (int r = 1; r < R; ++r)
+                for (int k = 0; k < ns; ++k) put(off + (size_t)(r - 1) * ns + k, (long)r * k * (L / (ns * R)));
+            off += (size_t)(R - 1) * ns;
+        }
+        ns *= R;
+    }
+}
+
+
 struct DeviceGuard {
     int prev = -1;
     bool ok = true;
@@ -286,20 +315,30 @@ mvd_status setup_fft(mvd_ctx* c) {
         return MVD_ERR_UNSUPPORTED;
     }
     const int Ls[3] = {g.X, g.Y, g.Z};
-    std::vector<float2> tw((size_t)g.X + g.Y + g.Z);
+    // FP32 twiddles w^m = exp(-2 pi i m / L), per axis: the natural table
+    // (m = 0..L-1), then the same values in the stage order of the
+    // register-resident lines of a power-of-two L, for their radix-8 plan
+    // (8 points per thread) and their radix-16 plan (16 points per thread)
+    std::vector<float2> tw(3 * ((size_t)g.X + g.Y + g.Z), make_float2(0.f, 0.f));
     size_t off = 0;
     for (int a = 0; a < 3; ++a) {
-        for (int m = 0; m < Ls[a]; ++m) {
-            const double ang = -2.0 * M_PI * (double)m / (double)Ls[a];
-            tw[off + m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        const int L = Ls[a];
+        auto w32 = [L](long m) {
+            const double ang = -2.0 * M_PI * (double)m / (double)L;
+            return make_float2((float)std::cos(ang), (float)std::sin(ang));
+        };
+        for (int m = 0; m < L; ++m) tw[off + m] = w32(m);
+        if (L >= 16 && L <= 4096 && (L & (L - 1)) == 0) {
+            stage_ordered_twiddles(L, 8, [&](size_t i, long m) { tw[off + L + i] = w32(m); });
+            stage_ordered_twiddles(L, 16, [&](size_t i, long m) { tw[off + 2 * (size_t)L + i] = w32(m); });
         }
-        off += Ls[a];
+        off += 3 * (size_t)L;
     }
     MVD_TRY(dev_alloc(&c->d_tw, tw.size(), "twiddle tables"));
     MVD_CUDA(cudaMemcpyAsync(c->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
     g.px.tw = c->d_tw;
-    g.py.tw = c->d_tw + g.X;
-    g.pz.tw = c->d_tw + g.X + g.Y;
+    g.py.tw = c->d_tw + 3 * g.X;
+    g.pz.tw = c->d_tw + 3 * (g.X + g.Y);
     const size_t ns = (size_t)g.Xh * g.YZ;
     MVD_TRY(dev_alloc(&c->d_S, ns, "work spectrum"));
     if (c->precise != 1) MVD_TRY(dev_alloc(&c->d_K, ns * (c->precise ? 1 : 2) * c->nv, "kernel spectra"));
@@ -323,26 +362,8 @@ mvd_status setup_fft(mvd_ctx* c) {
         for (int a = 0; a < 3; ++a) {
             const int L = Ls[a];
             for (int m = 0; m < L; ++m) tw2[o + m] = twv(m, L);
-            if (L >= 32 && L <= 1024 && (L & (L - 1)) == 0) {
-                std::vector<int> radix;
-                int rem = L;
-                while (rem % 8 == 0 && rem >= 8) {
-                    radix.push_back(8);
-                    rem /= 8;
-                }
-                if (rem > 1) radix.push_back(rem);
-                int ns = 1, off = 0;
-                for (size_t st = 0; st < radix.size(); ++st) {
-                    const int R = radix[st];
-                    if (st > 0) {
-                        for (int r = 1; r < R; ++r)
-                            for (int k = 0; k < ns; ++k)
-                                tw2[o + L + off + (size_t)(r - 1) * ns + k] = twv((long)r * k * (L / (ns * R)), L);
-                        off += (R - 1) * ns;
-                    }
-                    ns *= R;
-                }
-            }
+            if (L >= 32 && L <= 1024 && (L & (L - 1)) == 0)
+                stage_ordered_twiddles(L, 8, [&](size_t i, long m) { tw2[o + L + i] = twv(m, L); });
             o += 2 * (size_t)L;
         }
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_tw2), tw2.size(), "double-float twiddle tables"));
