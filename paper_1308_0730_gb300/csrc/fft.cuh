@@ -235,12 +235,12 @@ struct Dft<9, S> {
 __device__ __forceinline__ int small_div(int n, float inv) { return __float2int_rz(((float)n + 0.5f) * inv); }
 
 // Per-stage constants of the Stockham indexing: nb = L / R butterflies per
-// line, Ns combined so far, lstep = L / (Ns R) the twiddle index stride.
+// line, Ns combined so far.
 struct StageIdx {
-    int nb, Ns, lstep;
+    int nb, Ns;
     float inv_nb, inv_ns;
     __device__ __forceinline__ StageIdx(int L, int R, int ns)
-        : nb(L / R), Ns(ns), lstep(L / (ns * R)), inv_nb(1.0f / (float)(L / R)), inv_ns(1.0f / (float)ns) {}
+        : nb(L / R), Ns(ns), inv_nb(1.0f / (float)(L / R)), inv_ns(1.0f / (float)ns) {}
 };
 
 template <int R, int S>
@@ -252,9 +252,8 @@ __device__ __forceinline__ void stockham_bfly(const float2* __restrict__ A, floa
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = A[j + r * si.nb];
     if (si.Ns > 1) {
-        const int step = k * si.lstep;
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<S>(tw, r * step));
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle<S>(tw, (r - 1) * si.Ns + k));
     }
     Dft<R, S>::run(v);
     const int d = jq * si.Ns * R + k;
@@ -280,21 +279,28 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ A, flo
 // ls >= L), using B (same shape) as the ping-pong buffer. All threads of the
 // block take part; the call begins and ends with the data synchronised.
 // Returns the buffer (A or B) that holds the result.
+// Twiddles: p.tw is the axis's natural table (w^m, m < L), followed by its
+// radix-8 and radix-16 stage-ordered copies and then by its copy in the
+// stage order of this plan (p.tw + 3L): stage s >= 1 (Ns combined before it,
+// radix R) keeps w^(r k L / (Ns R)) at (earlier stages' entries) +
+// (r - 1) Ns + k, so consecutive butterflies read consecutive entries.
 template <int S>
 __device__ float2* fft_lines(float2* A, float2* B, int nlines, int ls, const FftPlan& p) {
     int Ns = 1;
+    const float2* tw = p.tw + 3 * p.L;
     for (int s = 0; s < p.nst; ++s) {
         const int R = p.radix[s];
         switch (R) {
-            case 8: stockham_stage<8, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
-            case 4: stockham_stage<4, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
-            case 2: stockham_stage<2, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
-            case 3: stockham_stage<3, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
-            case 6: stockham_stage<6, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
-            case 9: stockham_stage<9, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
-            case 10: stockham_stage<10, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
-            default: stockham_stage<5, S>(A, B, nlines, ls, p.L, Ns, p.tw); break;
+            case 8: stockham_stage<8, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 4: stockham_stage<4, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 2: stockham_stage<2, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 3: stockham_stage<3, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 6: stockham_stage<6, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 9: stockham_stage<9, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            case 10: stockham_stage<10, S>(A, B, nlines, ls, p.L, Ns, tw); break;
+            default: stockham_stage<5, S>(A, B, nlines, ls, p.L, Ns, tw); break;
         }
+        if (s > 0) tw += (R - 1) * Ns;
         __syncthreads();
         float2* t = A;
         A = B;

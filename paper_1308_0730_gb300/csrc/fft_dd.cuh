@@ -17,7 +17,9 @@
 
 namespace mvd {
 
-// One Stockham butterfly and the multi-line drivers, as in fft.cuh. The
+// One Stockham butterfly and the multi-line drivers, as in fft.cuh (tw: the
+// axis's natural double-float table, followed by its radix-8 and its
+// plan-ordered copies; the drivers read the plan-ordered one). The
 // first stage runs in double-float and records the largest component of its
 // outputs; the later stages run in aligned double-float (adf.cuh) on one grid
 // per tile, chosen from that bound (the tile's lines are neighbours in the
@@ -27,16 +29,14 @@ template <int R, int S, bool ALN>
 __device__ __forceinline__ void dd_bfly_math(cdd (&v)[R], int k, const StageIdx& si, const cdd* __restrict__ tw,
                                              float c, float& mx) {
     if constexpr (ALN) {  // a later stage: Ns > 1
-        const int step = k * si.lstep;
         v[0] = adf_calign(v[0], c);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = adf_cmul(v[r], twiddle_dd<S>(tw, r * step), c);
+        for (int r = 1; r < R; ++r) v[r] = adf_cmul(v[r], twiddle_dd<S>(tw, (r - 1) * si.Ns + k), c);
         DftA<R, S>::run(v, c);
     } else {
         if (si.Ns > 1) {
-            const int step = k * si.lstep;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle_dd<S>(tw, r * step));
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle_dd<S>(tw, (r - 1) * si.Ns + k));
         }
         DftDD<R, S>::run(v);
 #pragma unroll
@@ -161,6 +161,7 @@ __device__ cdd* fft_lines_dd_io(cdd* g, long gls, long ges, cdd* A, cdd* B, int 
                                 const FftPlan& p, const cdd* tw) {
     __shared__ float wmax[32];
     int Ns = 1, e = 0;
+    tw += 2 * p.L;  // the stage-ordered copy for this plan
     for (int s = 0; s < p.nst; ++s) {
         const int R = p.radix[s];
         const bool first = s == 0, last = s == p.nst - 1;
@@ -182,6 +183,7 @@ __device__ cdd* fft_lines_dd_io(cdd* g, long gls, long ges, cdd* A, cdd* B, int 
         else
             stage_dd_io<S, false, false, CO, LF, true>(R, A, B, g, g, gls, ges, nlines, nl, ls, p.L, Ns, tw, c, mx);
         if (first) dd_publish_bound(mx, wmax);
+        if (!first) tw += (R - 1) * Ns;
         __syncthreads();
         cdd* t = A;
         A = B;
@@ -196,6 +198,7 @@ template <int S>
 __device__ cdd* fft_lines_dd(cdd* A, cdd* B, int nlines, int ls, const FftPlan& p, const cdd* tw) {
     __shared__ float wmax[32];
     int Ns = 1, e = 0;
+    tw += 2 * p.L;  // the stage-ordered copy for this plan
     for (int s = 0; s < p.nst; ++s) {
         const int R = p.radix[s];
         float mx = 0.f, c = 0.f;
@@ -221,6 +224,7 @@ __device__ cdd* fft_lines_dd(cdd* A, cdd* B, int nlines, int ls, const FftPlan& 
         }
 #undef MVD_DD_ST
         if (s == 0) dd_publish_bound(mx, wmax);
+        if (s > 0) tw += (R - 1) * Ns;
         __syncthreads();
         cdd* t = A;
         A = B;

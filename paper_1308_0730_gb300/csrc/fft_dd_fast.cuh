@@ -513,13 +513,15 @@ __device__ __forceinline__ void ddf_store_halves(const DdXFast& a, cdd (&v)[kE8]
         const int k = idx / (2 * P), row = idx - k * 2 * P;
         if (row >= nrows) continue;
         const int pp = row < P ? row : row - P;
+        // zk and zm are outputs of one aligned line (one grid, below 2^23 q):
+        // their sums and differences are exact FP32 adds
         const cdd zk = cdd_load(sm + pp * LS + pad8(k));
         const cdd zm = cconj(cdd_load(sm + pp * LS + pad8(k == 0 ? 0 : L - k)));
         cdd val;
         if (row < P) {
-            val = chalf(cadd(zk, zm));
+            val = chalf(adf_cadd(zk, zm));
         } else {
-            const cdd d = chalf(csub(zk, zm));
+            const cdd d = chalf(adf_csub(zk, zm));
             val = cdd{d.im, dd{-d.re.hi, -d.re.lo}};
         }
         cdd_store(a.S2 + (long)k * a.YZ + rho0 + row, val);
@@ -644,9 +646,13 @@ __device__ __forceinline__ void ddf_x_ratio_tile(const DdXFast& a, long tile, cd
 #pragma unroll
     for (int q = 0; q < kE8; ++q) {
         const int n = t + TPL * q;
-        const float ba = v[q].re.hi + v[q].re.lo, bb = v[q].im.hi + v[q].im.lo;
-        const float xa = oka ? phs[p * L + n] / fmaxf(ba, a.eps) - 1.f : 0.f;
-        const float xb = okb ? phs[(P + p) * L + n] / fmaxf(bb, a.eps) - 1.f : 0.f;
+        // r - 1 = (phi - b') / b' with b' = max(b, eps): the difference is
+        // exact where phi and b' are within a factor 2 (Sterbenz), so r - 1
+        // keeps its relative precision as r approaches 1; the quotient is the
+        // fast division intrinsic (2 ulp, b' far inside its range)
+        const float ba = fmaxf(v[q].re.hi + v[q].re.lo, a.eps), bb = fmaxf(v[q].im.hi + v[q].im.lo, a.eps);
+        const float xa = oka ? __fdividef(phs[p * L + n] - ba, ba) : 0.f;
+        const float xb = okb ? __fdividef(phs[(P + p) * L + n] - bb, bb) : 0.f;
         f[q] = make_float2(xa, xb);
     }
     // each FP32 line lives inside its own line's double-float region (the

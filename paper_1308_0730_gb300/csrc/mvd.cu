@@ -180,20 +180,13 @@ using namespace mvd;
 
 namespace {
 
-// Stage order of the twiddles of a register-resident line of power-of-two
-// length L whose stages are radix P (the last one L's remainder): stage
-// s >= 1, with NS points combined before it and radix R, needs w^m for
-// m = r k L / (NS R) (r = 1..R-1, k = 0..NS-1); put(i, m) stores it at
-// i = (earlier stages' entries) + (r - 1) NS + k.
+// Stage order of the twiddles of a line transform whose stages have the
+// radices radix[0..n-1]: stage s >= 1, with NS points combined before it and
+// radix R, needs w^m for m = r k L / (NS R) (r = 1..R-1, k = 0..NS-1);
+// put(i, m) stores it at i = (earlier stages' entries) + (r - 1) NS + k, so
+// that consecutive butterflies (consecutive k) read consecutive entries.
 template <typename F>
-void stage_ordered_twiddles(int L, int P, F&& put) {
-    std::vector<int> radix;
-    int rem = L;
-    while (rem % P == 0 && rem >= P) {
-        radix.push_back(P);
-        rem /= P;
-    }
-    if (rem > 1) radix.push_back(rem);
+void stage_ordered_twiddles(int L, const std::vector<int>& radix, F&& put) {
     int ns = 1;
     size_t off = 0;
     for (size_t st = 0; st < radix.size(); ++st) {
@@ -206,6 +199,20 @@ void stage_ordered_twiddles(int L, int P, F&& put) {
         ns *= R;
     }
 }
+
+// the register-resident lines' plan: radix P stages, then L's remainder
+std::vector<int> pow_plan(int L, int P) {
+    std::vector<int> radix;
+    int rem = L;
+    while (rem % P == 0 && rem >= P) {
+        radix.push_back(P);
+        rem /= P;
+    }
+    if (rem > 1) radix.push_back(rem);
+    return radix;
+}
+
+std::vector<int> plan_radices(const FftPlan& p) { return std::vector<int>(p.radix, p.radix + p.nst); }
 
 
 struct DeviceGuard {
@@ -318,8 +325,10 @@ mvd_status setup_fft(mvd_ctx* c) {
     // FP32 twiddles w^m = exp(-2 pi i m / L), per axis: the natural table
     // (m = 0..L-1), then the same values in the stage order of the
     // register-resident lines of a power-of-two L, for their radix-8 plan
-    // (8 points per thread) and their radix-16 plan (16 points per thread)
-    std::vector<float2> tw(3 * ((size_t)g.X + g.Y + g.Z), make_float2(0.f, 0.f));
+    // (8 points per thread) and their radix-16 plan (16 points per thread),
+    // then in the stage order of the axis's mixed-radix plan
+    const FftPlan* plans[3] = {&g.px, &g.py, &g.pz};
+    std::vector<float2> tw(4 * ((size_t)g.X + g.Y + g.Z), make_float2(0.f, 0.f));
     size_t off = 0;
     for (int a = 0; a < 3; ++a) {
         const int L = Ls[a];
@@ -329,16 +338,17 @@ mvd_status setup_fft(mvd_ctx* c) {
         };
         for (int m = 0; m < L; ++m) tw[off + m] = w32(m);
         if (L >= 16 && L <= 4096 && (L & (L - 1)) == 0) {
-            stage_ordered_twiddles(L, 8, [&](size_t i, long m) { tw[off + L + i] = w32(m); });
-            stage_ordered_twiddles(L, 16, [&](size_t i, long m) { tw[off + 2 * (size_t)L + i] = w32(m); });
+            stage_ordered_twiddles(L, pow_plan(L, 8), [&](size_t i, long m) { tw[off + L + i] = w32(m); });
+            stage_ordered_twiddles(L, pow_plan(L, 16), [&](size_t i, long m) { tw[off + 2 * (size_t)L + i] = w32(m); });
         }
-        off += 3 * (size_t)L;
+        stage_ordered_twiddles(L, plan_radices(*plans[a]), [&](size_t i, long m) { tw[off + 3 * (size_t)L + i] = w32(m); });
+        off += 4 * (size_t)L;
     }
     MVD_TRY(dev_alloc(&c->d_tw, tw.size(), "twiddle tables"));
     MVD_CUDA(cudaMemcpyAsync(c->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
     g.px.tw = c->d_tw;
-    g.py.tw = c->d_tw + 3 * g.X;
-    g.pz.tw = c->d_tw + 3 * (g.X + g.Y);
+    g.py.tw = c->d_tw + 4 * g.X;
+    g.pz.tw = c->d_tw + 4 * (g.X + g.Y);
     const size_t ns = (size_t)g.Xh * g.YZ;
     MVD_TRY(dev_alloc(&c->d_S, ns, "work spectrum"));
     if (c->precise != 1) MVD_TRY(dev_alloc(&c->d_K, ns * (c->precise ? 1 : 2) * c->nv, "kernel spectra"));
@@ -347,31 +357,31 @@ mvd_status setup_fft(mvd_ctx* c) {
         // double-float twiddles w^m = exp(-2 pi i m / L): hi = fl32(w), lo =
         // fl32(w - hi), w in FP64. Per axis the table in natural order (m =
         // 0..L-1), then, for the register-resident passes of a power-of-two L,
-        // the same values in stage order: stage s >= 1 of the radix-8 plan
-        // (NS points combined before it, radix R) holds w^(r k L / (NS R)) at
-        // (r - 1) NS + k, so that a warp's threads (consecutive k) read
-        // consecutive entries.
+        // the same values in the stage order of their radix-8 plan, then in
+        // the stage order of the axis's mixed-radix plan.
         auto twv = [](long m, int L) {
             const double ang = -2.0 * M_PI * (double)m / (double)L;
             const double cr = std::cos(ang), ci = std::sin(ang);
             const float rh = (float)cr, ih = (float)ci;
             return make_float4(rh, (float)(cr - rh), ih, (float)(ci - ih));
         };
-        std::vector<float4> tw2(2 * ((size_t)g.X + g.Y + g.Z), make_float4(0.f, 0.f, 0.f, 0.f));
+        std::vector<float4> tw2(3 * ((size_t)g.X + g.Y + g.Z), make_float4(0.f, 0.f, 0.f, 0.f));
         size_t o = 0;
         for (int a = 0; a < 3; ++a) {
             const int L = Ls[a];
             for (int m = 0; m < L; ++m) tw2[o + m] = twv(m, L);
             if (L >= 32 && L <= 1024 && (L & (L - 1)) == 0)
-                stage_ordered_twiddles(L, 8, [&](size_t i, long m) { tw2[o + L + i] = twv(m, L); });
-            o += 2 * (size_t)L;
+                stage_ordered_twiddles(L, pow_plan(L, 8), [&](size_t i, long m) { tw2[o + L + i] = twv(m, L); });
+            stage_ordered_twiddles(L, plan_radices(*plans[a]),
+                                   [&](size_t i, long m) { tw2[o + 2 * (size_t)L + i] = twv(m, L); });
+            o += 3 * (size_t)L;
         }
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_tw2), tw2.size(), "double-float twiddle tables"));
         MVD_CUDA(cudaMemcpyAsync(c->d_tw2, tw2.data(), tw2.size() * sizeof(float4), cudaMemcpyHostToDevice,
                                  c->stream));
         g.tw2x = c->d_tw2;
-        g.tw2y = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + 2 * g.X);
-        g.tw2z = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + 2 * (g.X + g.Y));
+        g.tw2y = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + 3 * g.X);
+        g.tw2z = reinterpret_cast<const cdd*>(reinterpret_cast<const float4*>(c->d_tw2) + 3 * (g.X + g.Y));
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_S2), ns, "double-float work spectrum"));
         MVD_TRY(dev_alloc(reinterpret_cast<float4**>(&c->d_KP2), ns * 2 * c->nv, "double-float kernel spectra"));
     }
