@@ -72,6 +72,25 @@ __device__ __forceinline__ dd dd_dot2(dd x, dd y, dd z, dd w) {
 __device__ __forceinline__ cdd cmul(cdd a, cdd b) {
     return {dd_dot2<-1>(a.re, b.re, a.im, b.im), dd_dot2<+1>(a.re, b.im, a.im, b.re)};
 }
+// x.y + sg * z.w as an unevaluated pair, without the final renormalisation
+// (16 ops): hi the rounded sum of the high products, lo its TwoSum error
+// plus the products' exact errors and cross terms. For a consumer that
+// re-aligns its input anyway (the aligned line transforms).
+template <int SG>
+__device__ __forceinline__ dd dd_dot2_pair(dd x, dd y, dd z, dd w) {
+    const float p = x.hi * y.hi, q = z.hi * w.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    float f = fmaf(z.hi, w.hi, -q);
+    f = fmaf(z.hi, w.lo, f);
+    f = fmaf(z.lo, w.hi, f);
+    const dd t = dd_two_sum(p, SG > 0 ? q : -q);
+    return {t.hi, t.lo + (SG > 0 ? e + f : e - f)};
+}
+__device__ __forceinline__ cdd cmul_pair(cdd a, cdd b) {
+    return {dd_dot2_pair<-1>(a.re, b.re, a.im, b.im), dd_dot2_pair<+1>(a.re, b.im, a.im, b.re)};
+}
 __device__ __forceinline__ cdd cconj(cdd a) { return {a.re, dd{-a.im.hi, -a.im.lo}}; }
 __device__ __forceinline__ cdd chalf(cdd a) {  // exact
     return {dd{0.5f * a.re.hi, 0.5f * a.re.lo}, dd{0.5f * a.im.hi, 0.5f * a.im.lo}};

@@ -472,9 +472,11 @@ __device__ __forceinline__ void ddf_z2_pipe(cdd* __restrict__ S2, const cdd* __r
         if (next < ntiles) issue(stS, S2, next);
         LineFFTDD<L, -1, false, 0, true, Q>::run(v, line_sm, t, tws);
 #pragma unroll
-        for (int i = 0; i < kE8; ++i) v[i] = cmul(v[i], stK[i * kDdThreads]);
+        for (int i = 0; i < kE8; ++i) v[i] = cmul_pair(v[i], stK[i * kDdThreads]);
         if (next < ntiles) issue(stK, K2, next);
-        __syncthreads();
+        // no barrier here nor at the loop's end: the next transform writes the
+        // column lines only after its bound reduction's block barrier, which
+        // every thread reaches after its last read of the previous transform
         LineFFTDD<L, +1, false, 0, true, Q>::run(v, line_sm, t, tws);
         bool ok;
         long o = col_off(tile, ok);
@@ -483,7 +485,6 @@ __device__ __forceinline__ void ddf_z2_pipe(cdd* __restrict__ S2, const cdd* __r
 #pragma unroll
             for (int i = 0; i < kE8; ++i) cdd_store(col + i * step, v[i]);
         }
-        __syncthreads();  // the next forward transform reuses the column lines
     }
 }
 
