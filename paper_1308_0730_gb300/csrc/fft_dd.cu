@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kDdThreads, 2) k_ddf_z2_pipe(cdd* S2, const cd
 }
 
 template <int L>
-__global__ void __launch_bounds__(kDdThreads) k_ddf_x_forward(DdXFast a) {
+__global__ void __launch_bounds__(kDdThreads, 4) k_ddf_x_forward(DdXFast a) {
     extern __shared__ cdd smd[];
     ddf_x_forward_tile<L, false>(a, blockIdx.x, smd);
 }
