@@ -57,13 +57,6 @@ __global__ void __launch_bounds__(512) k_ddf_z(cdd* S2, const cdd* K2, int Y, lo
 }
 
 template <int L>
-__global__ void __launch_bounds__(kDdThreads, 3) k_ddf_z2(cdd* S2, const cdd* K2, int Y, long YZ, int ntiles_y,
-                                                         const cdd* tw2) {
-    extern __shared__ cdd smd[];
-    ddf_z2_tile<L, false>(S2, K2, Y, YZ, ntiles_y, tw2, blockIdx.x, smd);
-}
-
-template <int L>
 __global__ void __launch_bounds__(kDdThreads, 2) k_ddf_z2_pipe(cdd* S2, const cdd* K2, int Y, long YZ, int ntiles_y,
                                                               const cdd* tw2, long ntiles) {
     extern __shared__ cdd smd[];

@@ -359,63 +359,14 @@ __device__ __forceinline__ void ddf_z_tile(cdd* __restrict__ S2, const cdd* __re
     }
 }
 
-// z pass, forward x spectrum x inverse, with the twiddle table copied into
-// shared memory: loaded from the global table, the twiddles of the next
-// stages are hoisted above the stage barriers and held in registers (the tile
-// then needs 128), from shared memory they are not, and the tile runs 3
-// blocks of 256 threads per SM.
+// z pass (forward x spectrum x inverse) with the twiddles in shared memory:
+// the Q column lines, then the stage-ordered twiddle table at pad8(i) (loaded
+// from the global table, the compiler hoists later stages' twiddles above the
+// stage barriers and holds them in registers).
 __host__ __device__ constexpr bool ddf_z2_length(int L) { return L >= 128 && L <= 512 && (L & (L - 1)) == 0; }
 __host__ __device__ constexpr int z2_tw_offset(int L) { return ddf_z_cols(L) * z_line_stride8(L); }
 __host__ __device__ constexpr size_t ddf_z2_smem(int L) {
     return (size_t)(z2_tw_offset(L) + L + L / 8) * sizeof(cdd);
-}
-
-template <int L, bool CO>
-__device__ __forceinline__ void ddf_z2_tile(cdd* __restrict__ S2, const cdd* __restrict__ K2, int Y, long YZ,
-                                            int ntiles_y, const cdd* __restrict__ tw2, long tile, cdd* sm) {
-    constexpr int TPL = L / kE8, Q = ddf_z_cols(L);
-    const int q = threadIdx.x % Q, t = threadIdx.x / Q;
-    const int kx = (int)(tile / ntiles_y);
-    const int y0 = (int)(tile - (long)kx * ntiles_y) * Q;
-    const bool ok = y0 + q < Y;
-    const long off = (long)kx * YZ + y0 + q + (long)t * Y;  // element i at off + i * TPL * Y
-    const long step = (long)TPL * Y;
-    cdd* tws = sm + z2_tw_offset(L);
-    for (int m = threadIdx.x; m < L; m += Q * TPL) cp_async16(tws + pad8(m), tw2 + L + m, true);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    cdd* line_sm = sm + q * z_line_stride8(L);
-    cdd v[kE8];
-    {
-        const cdd* col = S2 + off;
-#pragma unroll
-        for (int i = 0; i < kE8; ++i) v[i] = ok ? ld_cdd<CO>(col + i * step) : czero_dd();
-    }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-    LineFFTDD<L, -1, false, 0, true, Q>::run(v, line_sm, t, tws);
-    // the kernel spectrum, four values in flight at a time (all eight would
-    // add 32 live registers); the column addresses are formed anew here and
-    // at the store, not kept across the transforms
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        long o = off;
-        asm volatile("" : "+l"(o)::"memory");
-        const cdd* kc = K2 + o;
-        cdd kv[kE8 / 2];
-#pragma unroll
-        for (int i = 0; i < kE8 / 2; ++i) kv[i] = ok ? cdd_load_nc(kc + (h * kE8 / 2 + i) * step) : czero_dd();
-#pragma unroll
-        for (int i = 0; i < kE8 / 2; ++i) v[h * kE8 / 2 + i] = cmul(v[h * kE8 / 2 + i], kv[i]);
-    }
-    __syncthreads();
-    LineFFTDD<L, +1, false, 0, true, Q>::run(v, line_sm, t, tws);
-    if (ok) {
-        long o = off;
-        asm volatile("" : "+l"(o));
-        cdd* col = S2 + o;
-#pragma unroll
-        for (int i = 0; i < kE8; ++i) cdd_store(col + i * step, v[i]);
-    }
 }
 
 // The z pass as a persistent, software-pipelined loop: each block walks the
