@@ -71,9 +71,10 @@ typedef enum {
 typedef enum { MVD_PATH_AUTO = 0, MVD_PATH_DIRECT = 1, MVD_PATH_FFT = 2 } mvd_path;
 
 /* Arithmetic of the FFT engine.
- *   MVD_PRECISE: double-float (pairs of FP32, about 48 significant bits) for
- *     the whole forward blur b = psi * P_v and for the back-projection's y, z
- *     and inverse x passes; the back-projection's forward x pass transforms
+ *   MVD_PRECISE: double-float (pairs of FP32; inside the FFT lines every
+ *     high part sits on one power-of-two grid per line, which keeps the error
+ *     near 2^-43 of the line's largest value) for the whole forward blur
+ *     b = psi * P_v and for the back-projection's y, z and inverse x passes; the back-projection's forward x pass transforms
  *     r - 1 in FP32 (c = (r - 1) * K + 1 holds because K sums to 1, and r - 1
  *     is small where the estimate fits). FP32 FFT rounding is absolute (it
  *     scales with the whole volume's norm), so in FP32 the dim voxels of b
